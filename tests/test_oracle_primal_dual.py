@@ -1,0 +1,131 @@
+"""Pins of the oracle's Algorithm 1/2 against convergence theory and the constraint set."""
+import numpy as np
+import pytest
+
+from oracle import measurement as meas
+from oracle import primal_dual as pd
+from oracle import prox
+from oracle import wavelets as wav
+from paper_1801_02417_gb300 import inputs
+
+
+def _problem(n=16, M=200, levels=2, nblocks=2, seed=1, snr=30.0, omega=2.0):
+    W = inputs.Workload("tiny", n, M, 6, 40, levels, nblocks, 0, 0, snr, 0, seed)
+    uv = inputs.uv_coverage(W, omega_max=omega)
+    w = inputs.visibility_weights(M, seed, 0.3)
+    Strue = inputs.stokes_source(n, seed)
+    Yc = meas.phi(Strue, uv, w)
+    sig = inputs.sigma_for_snr(Yc, snr)
+    Y = Yc + inputs.complex_noise(M, sig, seed)
+    off = inputs.block_offsets(M, nblocks)
+    eps = np.array([meas.chi2_epsilon(int(off[b + 1] - off[b]), sig) for b in range(nblocks)])
+    return pd.Problem(n, levels, uv, w, Y, off, eps), Strue
+
+
+def _metric_sequence(prob, p, mode, T, iters, st=None, iteration=pd.pd_iteration):
+    st = st or pd.zero_state(prob.n, prob.Y.shape[0])
+    out = []
+    for _ in range(iters):
+        st2 = iteration(st, prob, T, p, mode)
+        out.append(pd.metric_sq(*(st2[k] - st[k] for k in "SZABCD"), prob, p, mode))
+        st = st2
+    return np.array(out), st
+
+
+@pytest.mark.parametrize("mode", [pd.POLARIZED, pd.NO_CONSTRAINT, pd.NNLS])
+def test_fixed_point_residual_non_increasing(mode):
+    """Algorithm 1 is a proximal-point step in the metric M, so ||z_{k+1} - z_k||_M never grows."""
+    prob, _ = _problem()
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    p = pd.step_sizes(on, mode)
+    T = 2e-3 * np.ones((4, 9, prob.n, prob.n))
+    ds, _ = _metric_sequence(prob, p, mode, T, 40)
+    assert ds[0] > 0
+    # Rounding floor: once converged to machine precision the metric is noise.
+    assert np.all(np.diff(ds) <= 1e-10 * ds[:-1] + 1e-24 * ds[0]), ds
+
+
+def test_planted_sign_error_breaks_monotonicity():
+    """A wrong sign on C in step 3 must be caught by the metric pin above."""
+    prob, _ = _problem()
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    p = pd.step_sizes(on, pd.POLARIZED)
+    T = 2e-3 * np.ones((4, 9, prob.n, prob.n))
+
+    def wrong(st, prob, T, p, mode):
+        st = dict(st)
+        st["C"] = -st["C"]
+        out = pd.pd_iteration(st, prob, T, p, mode)
+        return out
+    rng = np.random.default_rng(0)
+    st0 = pd.zero_state(prob.n, prob.Y.shape[0])
+    st0["C"] = rng.normal(size=st0["C"].shape)
+    ds, _ = _metric_sequence(prob, p, pd.POLARIZED, T, 30, st=st0, iteration=wrong)
+    assert np.any(np.diff(ds) > 1e-6 * ds[:-1])
+
+
+def test_polarized_solution_is_feasible_and_fits_data():
+    """At convergence: ||phi S - Y||_b <= (1 + theta) eps_b and S in P (Section 5.5 stop rules)."""
+    prob, Strue = _problem(n=16, M=300, levels=2, nblocks=1, seed=3)
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    T = 1e-2 * np.ones((4, 9, prob.n, prob.n))
+    st = pd.run(pd.zero_state(prob.n, 300), prob, T, pd.step_sizes(on, pd.POLARIZED), 2500)
+    res = pd.residual_norms(st["S"], prob)
+    assert np.all(res <= 1.005 * prob.eps), (res, prob.eps)
+    pv = -st["S"][0] + np.sqrt(np.sum(st["S"][1:] ** 2, axis=0))
+    assert pv.max() <= 1e-4 * st["S"][0].max()
+    # The dual variables of the epigraph sit on the polar cones at the fixed point.
+    assert np.all(st["C"][0] + st["D"][0] <= 1e-9)
+
+
+def test_gamma_only_rescales_duals():
+    """gamma only affects convergence speed (Section 4.2): two gammas reach the same minimum of ||Psi^dag S||_W,1."""
+    prob, _ = _problem(n=8, M=120, levels=1, nblocks=1, seed=5)
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    Wt = np.ones((4, 9, 8, 8))
+    vals = []
+    for gamma in (3e-2, 1e-1):
+        st = pd.run(pd.zero_state(8, 120), prob, gamma * Wt, pd.step_sizes(on, pd.POLARIZED), 6000)
+        vals.append(float(np.sum(np.abs(wav.psi_adjoint(st["S"], 1)))))
+        assert np.all(pd.residual_norms(st["S"], prob) <= 1.01 * prob.eps)
+    assert abs(vals[0] - vals[1]) <= 5e-3 * vals[0], vals
+
+
+def test_soft_threshold_step_keeps_dual_in_box():
+    """After step 6, |A| <= gamma W element-wise (clamp identity of the soft-threshold step)."""
+    prob, _ = _problem()
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    p = pd.step_sizes(on, pd.POLARIZED)
+    rng = np.random.default_rng(9)
+    T = np.abs(rng.normal(size=(4, 9, 16, 16))) * 1e-2
+    st = pd.run(pd.zero_state(16, 200), prob, T, p, 5)
+    assert np.all(np.abs(st["A"]) <= T * (1 + 1e-12))
+
+
+def test_nnls_mode_keeps_other_variables_zero_and_I_nonnegative():
+    prob, _ = _problem()
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    st = pd.run(pd.zero_state(16, 200), prob, np.zeros((4, 9, 16, 16)), pd.step_sizes(on, pd.NNLS), 20, pd.NNLS)
+    for k in "ZACD":
+        assert not np.any(st[k])
+    assert st["S"][0].min() >= 0.0
+
+
+def test_reweight_formula_bounds():
+    rng = np.random.default_rng(4)
+    S = rng.normal(size=(4, 16, 16))
+    W = pd.reweight(S, 2, 0.5)
+    assert W.shape == (4, 9, 16, 16)
+    assert np.all((W > 0) & (W <= 1.0))
+    c = np.abs(wav.psi_adjoint(S, 2))
+    assert np.allclose(W * (0.5 + c), 0.5)
+
+
+def test_stats_helpers():
+    prob, Strue = _problem()
+    assert pd.violation_count(Strue, 0.0) == 0
+    bad = Strue.copy()
+    bad[1, 3, 3] = bad[0, 3, 3] + 1.0
+    assert pd.violation_count(bad, 1e-3) == 1
+    rc = pd.relative_change(Strue * 1.1, Strue)
+    assert np.allclose(rc, 0.1)
