@@ -1,0 +1,401 @@
+"""Throughput of the Polarized SARA primal-dual iteration on GB300.
+
+One step = one iteration of Algorithm 1 (every hot-path stage: primal/epigraph
+sweep, SARA analysis + soft-threshold dual, SARA synthesis, NUFFT forward +
+degrid + l2-ball dual, gridding + adjoint NUFFT) on the 1024x1024 4-Stokes,
+2,000,000-visibility, 32-block, 6-level workload, with inputs resident in HBM.
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle instead (the
+reference arm of this benchmark), on bounded samples of the same workload.
+Multi-GPU: independent replicas, one per rank (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1801_02417_gb300 import inputs  # noqa: E402
+
+METRIC = "PD iters/s at 1024² 4-Stokes 2M vis"
+WORKLOAD = "img1024_m2m"
+
+
+def chi2_epsilon(M_b: int, sigma: float) -> float:
+    """eps^2 = (8M + 2 sqrt(16M)) sigma^2 / 2 (Section 5.1)."""
+    dof = 8.0 * M_b
+    return math.sqrt((dof + 2.0 * math.sqrt(2.0 * dof)) * sigma * sigma / 2.0)
+
+
+def make_inputs(wl):
+    uv = inputs.uv_coverage(wl)
+    w = inputs.visibility_weights(wl.M, wl.seed, 0.0).astype(np.float32)
+    truth = inputs.stokes_source(wl.n, wl.seed, wl.n_compact).astype(np.float32)
+    off = inputs.block_offsets(wl.M, wl.nblocks)
+    return uv, w, truth, off
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline model
+def stage_bytes(n: int, L: int, M: int, Wd: int) -> dict:
+    """Algorithmic DRAM bytes of each stage of one iteration (each array read/written once)."""
+    N = n * n
+    approx = sum(32 * 4 * (N >> (2 * l)) for l in range(1, L))       # 32 (map, basis) approximations
+    return {
+        "primal": 192 * N,                          # S,C (16+16), Z,D (8+8), PsiA, Adj, A0, T0 read; S,Xb,Z,C,D,A0 written
+        "analysis": 16 * N + 12 * 32 * N + 2 * approx,   # Xb read; A r/w + T read; approximations w/r
+        "synthesis": 4 * 32 * N + 16 * N + 16 * N + 2 * approx,   # A read, A0 read, PsiA written
+        "fwd_fft": 16 * N + 2 * 16 * n * Wd + 16 * Wd * Wd,
+        "degrid": M * (16 + 32 + 32 + 32) + 16 * Wd * Wd,   # rec, R r/w, Y; spectrum window once
+        "ball": 0,
+        "grid": M * (16 + 32) + 2 * 32 * Wd * Wd,      # rec, R; accumulator clear + write
+        "adj_fft": 32 * Wd * Wd + 2 * 16 * n * Wd + 16 * N,
+    }
+
+
+def window_side(uv: np.ndarray, n: int, W: int = 7) -> int:
+    K = 2 * n
+    c = np.floor(np.abs(uv) * K / (2 * np.pi) + 0.5).max() if len(uv) else 0
+    R = int(c) + W // 2 + 1
+    return 2 * R + 1 if 2 * R + 1 <= K else K
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(n: int, L: int, uv: np.ndarray, w: np.ndarray, M: int, budget_s: float, seed: int = 0) -> dict:
+    """Seconds per full oracle iteration of Algorithm 1 at (n, L, M), extrapolated from samples.
+
+    Times, as the oracle runs them: the per-pixel steps on the full maps (once);
+    the analysis + synthesis of a few (map, basis) pairs (each of the 32 pairs
+    costs the same); phi + phi^dagger on a subset of rows (cost linear in rows).
+    """
+    from oracle import measurement as meas
+    from oracle import prox
+    from oracle import wavelets as wav
+
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    S = rng.normal(size=(4, n, n))
+    Z = rng.normal(size=(2, n, n))
+    C = rng.normal(size=(4, n, n))
+    D = rng.normal(size=(2, n, n))
+    A0 = rng.normal(size=(4, n, n))
+    # Per-pixel part (steps 3-4, 9-12, Dirac of 5-6).
+    t = time.perf_counter()
+    X = S - 0.33 * (A0 + C)
+    Z1 = prox.proj_V(Z - 0.33 * D)
+    Sb, Zb = 2 * X - S, 2 * Z1 - Z
+    Ct, Dt = C + Sb, D + Zb
+    prox.proj_E1(Ct[0], Dt[0])
+    prox.proj_E2(Ct[1:4], Dt[1])
+    prox.soft_threshold(A0 + Sb / 3, np.abs(A0))
+    t_pix = time.perf_counter() - t
+    # Wavelet pairs.
+    pairs = []
+    x = rng.normal(size=(n, n))
+    b = 1
+    while True:
+        t = time.perf_counter()
+        c = wav.dwt2(x, wav.FILTERS[b], L)
+        wav.idwt2(c, wav.FILTERS[b], L)
+        prox.soft_threshold(c, np.abs(c))
+        pairs.append(time.perf_counter() - t)
+        b = b % 8 + 1
+        if len(pairs) >= 8 or time.perf_counter() - t0 > 0.6 * budget_s:
+            break
+    t_pairs = 32 * statistics.mean(pairs)
+    # phi + phi^dagger on a row subset.
+    rows = 64
+    sub = rng.choice(len(uv), size=min(rows, len(uv)), replace=False)
+    Sm = rng.normal(size=(4, n, n))
+    t = time.perf_counter()
+    Bv = meas.phi(Sm, uv[sub], w[sub])
+    meas.phi_adjoint(Bv, uv[sub], w[sub], n)
+    t_rows = time.perf_counter() - t
+    t_vis = t_rows * M / len(sub)
+    total = t_pix + t_pairs + t_vis
+    return {"seconds_per_iter": total, "t_pixels": t_pix, "t_wavelets": t_pairs, "t_phi": t_vis,
+            "pairs_timed": len(pairs), "rows_timed": int(len(sub)), "wall": time.perf_counter() - t0}
+
+
+def cpu_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ arms
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args) -> None:
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    wl = inputs.WORKLOADS[args.workload]
+    uv, w, truth, off = make_inputs(wl)
+    per_step_budget = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(wl.n, wl.levels, uv, w.astype(np.float64), wl.M, per_step_budget, seed=i)
+        if i >= args.warmup:
+            samples.append(r["seconds_per_iter"])
+    sec = statistics.mean(samples)
+    value = 1.0 / sec
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "M": wl.M, "blocks": wl.nblocks, "levels": wl.levels},
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: FP64 oracle per-pixel steps on full 1024^2 maps, analysis+synthesis "
+                                   "of sampled (map, basis) pairs x32, phi+phi^dagger on 64 rows scaled to 2M"},
+        "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_own(args) -> None:
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1801_02417_gb300 import _build
+    from paper_1801_02417_gb300 import binding as B
+    from paper_1801_02417_gb300.solver import PolarizedSARA
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build_library()
+    if world > 1:
+        dist.barrier()
+    B.lib()
+
+    wl = inputs.WORKLOADS[args.workload]
+    n, L, M = wl.n, wl.levels, wl.M
+    uv, w, truth, off = make_inputs(wl)
+    # A dedicated stream: the handle launches on it and the CUDA events below are
+    # recorded on it (torch's default stream would be handle 0 = "create your own").
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = PolarizedSARA(n, L, stream=stream.cuda_stream)
+    # Clean visibilities from the library's own phi, then noise at the input SNR.
+    zeros = np.zeros((M, 4), np.complex64)
+    eps1 = np.ones(wl.nblocks)
+    s.set_measurements(uv, zeros, w, off, eps1)
+    clean = np.empty((M, 4), np.complex64)
+    B.ps_apply_phi(s.h, truth, clean)
+    sigma = inputs.sigma_for_snr(clean, wl.snr_db)
+    Y = (clean + inputs.complex_noise(M, sigma, wl.seed)).astype(np.complex64)
+    eps = np.array([chi2_epsilon(int(off[b + 1] - off[b]), sigma) for b in range(wl.nblocks)])
+    s.set_measurements(uv, Y, w, off, eps)
+    dirty = np.empty((4, n, n), np.float32)
+    B.ps_apply_phi_adjoint(s.h, Y, dirty)
+    gamma = 1e-3 * float(np.max(np.abs(s.psi_adjoint(dirty))))
+    s.set_sara_weights(None, gamma)
+    s.set_mode(B.PS_POLARIZED)
+
+    # Warm-up, then exactly K timed steps between barriers.
+    s.pd_iterate(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()        # ncu --profile-from-start off captures only this region
+    ev0.record(stream)
+    s.pd_iterate(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+    launches = B.ps_kernels_per_iteration(s.h) * args.steps
+
+    # Stage timing (CUDA events between stages, same launch configuration, eager).
+    prof_iters = min(args.steps, 20)
+    stages = B.ps_profile_stages(s.h, prof_iters)
+    Wd = window_side(uv, n)
+    sbytes = stage_bytes(n, L, M, Wd)
+    dom = max(stages, key=stages.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = sbytes[dom] / (stages[dom] * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get(dom)
+        except Exception:
+            traffic = None
+    total_bytes = sum(sbytes.values())
+
+    # End to end through the C ABI with host buffers (pinned): upload of the
+    # measurements, then per step one iteration and a read-back of the Stokes maps.
+    e2e = None
+    if rank == 0:
+        uv_p = torch.from_numpy(uv).pin_memory()
+        Y_p = torch.from_numpy(Y.view(np.float32)).pin_memory()
+        w_p = torch.from_numpy(w).pin_memory()
+        out_p = torch.empty((4, n, n), dtype=torch.float32).pin_memory()
+        ke = max(1, args.steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.ps_set_measurements(s.h, uv_p, Y_p, w_p, off, eps)
+        s.set_sara_weights(None, gamma)
+        for _ in range(ke):
+            s.pd_iterate(1)
+            B.ps_get_stokes(s.h, out_p)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = uv.nbytes + Y.nbytes + w.nbytes
+        e2e = {"value": ke / te, "unit": "iter/s", "h2d_bytes_per_step": int(h2d / ke),
+               "d2h_bytes_per_step": int(out_p.numel() * 4),
+               "note": "host->device measurements (sort, power iteration) once, then per step one iteration + Stokes read-back"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(n, L, uv, w.astype(np.float64), M, budget_s=20.0)
+        cpu = {"value": 1.0 / r["seconds_per_iter"], "unit": "iter/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": (f"FP64 oracle: per-pixel steps on full {n}^2 maps ({r['t_pixels']:.2f}s), "
+                          f"{r['pairs_timed']} (map,basis) analysis+synthesis pairs x32/{r['pairs_timed']} "
+                          f"({r['t_wavelets']:.1f}s), phi+phi^dagger on {r['rows_timed']} rows x{M // r['rows_timed']} "
+                          f"({r['t_phi']:.1f}s); extrapolated per-iteration time {r['seconds_per_iter']:.1f}s")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "n": n, "stokes": 4, "M": M, "blocks": wl.nblocks, "levels": L,
+                       "kernel_width": 7, "oversampling": 2, "grid_window": Wd,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "no flush: per-iteration working set ~%.0f MB > 126 MB L2" % (total_bytes / 1e6),
+                       "vis_iters_per_s": value * M},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src, "algorithmic_bytes": sbytes[dom], "stage_ms": stages[dom]},
+            "iteration_roofline": {"algorithmic_bytes": total_bytes,
+                                   "achieved_gbs": total_bytes / (ms_per_step * 1e-3) / 1e9,
+                                   "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+            "stages_ms": stages,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_own(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * polsara.h - C ABI of the GB300 Polarized SARA primal-dual imager.
+ *
+ * Polarized SARA (Birdi, Repetti & Wiaux, arXiv:1801.02417) recovers the four
+ * Stokes maps S = [I, Q, U, V] (N = n*n pixels each) from full-polarization
+ * visibilities Y = phi(S) + E (Section 2.1, Eq. RIME_disc) by solving
+ *   min_S,Z  f(phi(S)) + i_U(S) + gamma ||Psi^dagger S||_{W,1} + i_V(Z)
+ *            + i_E1(S_:,1, Z_:,1) + i_E2(S_:,2:4, Z_:,2)          (Eq. min_gen2)
+ * with the primal-dual iteration of Algorithm 1, reweighted by Algorithm 2.
+ * Every step of the iteration runs in this library's CUDA kernels.
+ *
+ * Conventions shared by every call
+ *   - Stokes maps: float32, 4 planes of n*n in the order I, Q, U, V; each plane is
+ *     row-major, pixel (p, q) at centred coordinates x = q - n/2, y = p - n/2.
+ *   - Visibilities: complex64 interleaved (re, im), M rows of 4 correlations in the
+ *     paper's order RR, RL, LR, LL (Section 2.1: S^T L = [I+Q, U+iV, U-iV, I-Q]).
+ *   - Frequencies: float64, M rows of (omega_u, omega_v) in radians per pixel
+ *     (|omega| < pi); phi uses the phase exp(-i (omega_u x + omega_v y)) of Eq. RIME.
+ *   - SARA coefficients: float32, 4 maps x 9 bases x n*n; basis 0 is Dirac, basis b
+ *     (1..8) the periodic orthonormal Daubechies db_b Mallat transform with
+ *     `levels` levels; the concatenation is scaled by 1/3 (tight frame).
+ *     Mallat layout of one n*n basis array at level l (m = n >> (l-1), h = m/2):
+ *     rows [0,h) cols [h,m) x-high/y-low, rows [h,m) cols [0,h) x-low/y-high,
+ *     rows [h,m) cols [h,m) x-high/y-high; the coarsest approximation fills the
+ *     top-left (n >> levels)^2 block.
+ *   - `device_ptrs` = 1: pointers are CUDA device pointers read/written on the
+ *     handle's stream; 0: host pointers (the call then synchronises the stream).
+ *   - Ownership: inputs are copied; outputs go to caller-allocated buffers; the
+ *     handle owns all its device state until ps_destroy.
+ *   - Errors: every call returns a ps_status; ps_last_error() holds a message.
+ *     No call aborts the process. A CUDA error leaves the handle unusable
+ *     (PS_ECUDA); an invalid argument leaves it unchanged (PS_EINVAL).
+ */
+#ifndef POLSARA_H
+#define POLSARA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ps_handle ps_handle;
+
+typedef enum {
+  PS_OK = 0,
+  PS_EINVAL = 1,      /* invalid argument (size, pointer, mode) */
+  PS_ENOMEM = 2,      /* device allocation failed */
+  PS_ECUDA = 3,       /* a CUDA runtime call or kernel failed */
+  PS_ETIMEOUT = 4,    /* a bounded device wait gave up */
+  PS_ENONFINITE = 5,  /* a NaN/Inf was detected in the state */
+  PS_ESTATE = 6       /* call out of order (e.g. iterate before set_measurements) */
+} ps_status;
+
+/* Problem variants (Section 4.2, Section 4.3.4, Section 5.2). */
+enum {
+  PS_POLARIZED = 0,      /* Algorithm 1 in full: S, Z, A, B, C, D */
+  PS_NO_CONSTRAINT = 1,  /* S, A, B only, with P_U' (Stokes I >= 0) */
+  PS_NNLS = 2            /* S, B only, with P_U' and g = 0: the initialisation of Alg. 2 */
+};
+
+typedef struct {
+  int32_t n;             /* image side: power of two, 16 <= n <= 2048 */
+  int32_t levels;        /* wavelet levels, 1 <= levels, n divisible by 2^levels */
+  int32_t mode;          /* PS_POLARIZED | PS_NO_CONSTRAINT | PS_NNLS */
+  int32_t literal_ball;  /* 0: l2-ball radius eps (Moreau reading of Alg. 1 step 8);
+                            1: the printed radius eps / rho2 */
+  int32_t kernel_width;  /* NUFFT interpolation width W: 5, 7 or 9; 0 => 7 */
+  int32_t reserved;
+  double tau, rho1, rho2, rho3;  /* step sizes; 0 => default of Section 4.3.3:
+                                    rho1 = rho3 = 1, rho2 = 1/||phi||^2,
+                                    tau = 0.99 / (sum of rho_i ||K_i||^2 in the mode) */
+} ps_config;
+
+typedef struct {
+  int32_t nblocks;          /* number of l2 blocks the next fields describe */
+  int32_t reserved;
+  double* block_residual;   /* out, nblocks entries (may be NULL): ||phi(S) - Y||_2 per block */
+  double rel_change[4];     /* ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| of the last iteration (Eq. stop_crit) */
+  double zeta;              /* violation threshold used (Section 5.2) */
+  int64_t violations;       /* pixels with -I + ||(Q,U,V)|| > zeta */
+  int64_t violations_raw;   /* pixels with -I + ||(Q,U,V)|| > 0 */
+  double weighted_l1;       /* sum |T .* Psi^dagger S| (gamma ||Psi^dagger S||_{W,1}) */
+  int64_t iterations;       /* iterations run on this handle */
+} ps_stats;
+
+/* Primal and dual state of Algorithm 1 (the warm start Algorithm 2 passes on).
+ * Each pointer may be NULL to skip that array. Sizes: S, C: 4N floats; Z, D: 2N
+ * floats; A: 36N floats; B: M x 4 complex64 (8M floats), rows in the caller's
+ * visibility order. */
+typedef struct {
+  float* S; float* Z; float* A; float* B; float* C; float* D;
+  int32_t device_ptrs;
+  int32_t reserved;
+} ps_state_view;
+
+/* Create a handle for one imaging problem (Section 4). `cuda_stream` is a
+ * cudaStream_t the handle launches on (NULL: the handle creates its own).
+ * Validates cfg (n power of two, levels, mode). */
+ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out);
+
+/* Release every device buffer of the handle. NULL is accepted. */
+void ps_destroy(ps_handle* h);
+
+/* Message of the last failed call on `h` (or of the last failed ps_create when
+ * h is NULL). Valid until the next call on the handle. */
+const char* ps_last_error(const ps_handle* h);
+
+/* Measurements of the data model Y = phi(S) + E (Section 2.1, Eq. RIME_disc) and
+ * the l2 balls of the data-fidelity term (Eq. f_diff), one per block.
+ *   M              rows (0 allowed: no data term)
+ *   uv             M x 2 float64, radians per pixel, |omega| < pi
+ *   vis            M x 4 complex64 (RR, RL, LR, LL)
+ *   weights        M float32 per-row weights w_m >= 0 (phi = diag(w) F ...), NULL = 1
+ *   nblocks        number of l2 blocks (>= 1 when M > 0)
+ *   block_offsets  nblocks+1 int64, increasing, [0] = 0, [nblocks] = M
+ *   eps            nblocks float64 radii eps_b > 0 (e.g. the chi^2 bound of Section 5.1)
+ *   device_ptrs    for uv, vis, weights (block_offsets and eps are host arrays)
+ * Sorts the rows by interpolation tile, estimates ||phi||^2 by power iteration
+ * (FP64 reductions on the device), sets the default step sizes, and resets the
+ * state to zero. */
+ps_status ps_set_measurements(ps_handle* h, int64_t M, const double* uv, const float* vis,
+                              const float* weights, int32_t nblocks, const int64_t* block_offsets,
+                              const double* eps, int32_t device_ptrs);
+
+/* Soft-threshold sizes gamma W of Algorithm 1 step 6 (W >= 0: 4 x 9 x N floats in
+ * the coefficient layout; NULL = all ones). gamma > 0. */
+ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_t device_ptrs);
+
+/* Current soft-threshold sizes gamma W (4 x 9 x N floats, coefficient layout). */
+ps_status ps_get_sara_weights(ps_handle* h, float* out, int32_t device_ptrs);
+
+/* Run n_iter iterations of Algorithm 1 (steps 3-12) in the handle's mode.
+ * Asynchronous on the handle's stream (a CUDA graph of one iteration is replayed). */
+ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter);
+
+/* Reweighting of Algorithm 2 (Eq. weights): W = delta / (delta + |Psi^dagger S|),
+ * thresholds gamma W with the gamma of the last ps_set_sara_weights. All primal and
+ * dual state is kept (warm start). delta > 0. */
+ps_status ps_reweight(ps_handle* h, double delta);
+
+/* Switch the problem variant (PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS) keeping the
+ * state; step sizes that were defaulted are recomputed for the new mode. */
+ps_status ps_set_mode(ps_handle* h, int32_t mode);
+
+/* Current Stokes maps S (4 x N floats). */
+ps_status ps_get_stokes(ps_handle* h, float* out, int32_t device_ptrs);
+
+/* Read or overwrite the primal/dual state (Algorithm 2 warm start). */
+ps_status ps_get_state(ps_handle* h, const ps_state_view* view);
+ps_status ps_set_state(ps_handle* h, const ps_state_view* view);
+
+/* Step sizes and the power-iteration estimate of ||phi||_sp^2 (Section 4.3.3). */
+ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, double* rho3,
+                        double* opnorm_sq);
+
+/* Stopping-rule statistics of Section 5.5 for the current S: per-block residual
+ * norms, relative change of the last iteration, violation count N_p with
+ * zeta = zeta_sigma * rms(Stokes I residual image) / PSF peak (Section 5.2),
+ * and the weighted l1 objective. Synchronises the stream. */
+ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out);
+
+/* Operators of the method on caller data, using the handle's measurement set:
+ *   ps_apply_phi          S (4 x N) -> Y = phi(S) (M x 4 complex64)    [Eq. meas_op]
+ *   ps_apply_phi_adjoint  Y -> phi^dagger(Y) = Re(Phi^H Y L^H) (4 x N) [Alg. 1 step 3]
+ *   ps_apply_psi_adjoint  S (4 x N) -> Psi^dagger S (4 x 9 x N)        [Section 4.1]
+ *   ps_apply_psi          A (4 x 9 x N) -> Psi A (4 x N)               [Section 4.1]
+ * Inputs and outputs may not alias. */
+ps_status ps_apply_phi(ps_handle* h, const float* S, float* Y, int32_t device_ptrs);
+ps_status ps_apply_phi_adjoint(ps_handle* h, const float* Y, float* S, int32_t device_ptrs);
+ps_status ps_apply_psi_adjoint(ps_handle* h, const float* S, float* A, int32_t device_ptrs);
+ps_status ps_apply_psi(ps_handle* h, const float* A, float* S, int32_t device_ptrs);
+
+/* The Daubechies scaling filters db1..db8 the library uses (Section 4.1), built
+ * on the host by spectral factorisation: out[8][16], row b-1 holds db_b's 2b taps
+ * (zero padded). Needs no device. */
+ps_status ps_wavelet_filters(double* out);
+
+/* Stages of one iteration, in launch order (index into ps_profile_stages' output). */
+enum {
+  PS_STAGE_PRIMAL = 0,     /* k_primal: steps 3-4, 9-12, Dirac part of 5-6 */
+  PS_STAGE_ANALYSIS = 1,   /* k_analysis x levels: steps 5-6 */
+  PS_STAGE_SYNTHESIS = 2,  /* k_synthesis x levels: Psi A for the next step 3 */
+  PS_STAGE_FWD_FFT = 3,    /* k_fwd_rows + k_fwd_cols: F Z of step 7 */
+  PS_STAGE_DEGRID = 4,     /* k_degrid: G, mixing, B~ and block-norm partials (step 7) */
+  PS_STAGE_BALL = 5,       /* k_block_scale: step 8 */
+  PS_STAGE_GRID = 6,       /* accumulator clear + k_grid: G^T of phi^dagger */
+  PS_STAGE_ADJ_FFT = 7,    /* k_adj_cols + k_adj_rows: Z^T F^H of phi^dagger */
+  PS_NSTAGES = 8
+};
+
+/* Run n_iter iterations launched one kernel at a time (no graph) with CUDA events
+ * between the stages on the handle's stream, and write the mean milliseconds of
+ * each stage to stage_ms[PS_NSTAGES]. The iterations advance the state like
+ * ps_pd_iterate. Synchronises the stream. */
+ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms);
+
+/* Number of kernel launches in one iteration of the handle's current mode. */
+int32_t ps_kernels_per_iteration(const ps_handle* h);
+
+/* Synchronise the handle's stream; reports a pending CUDA error. */
+ps_status ps_synchronize(ps_handle* h);
+
+/* Device bytes held by the handle (for admission control by memory footprint). */
+int64_t ps_device_bytes(const ps_handle* h);
+
+/* Estimate of the device bytes a handle would hold for (n, levels, M) before it is
+ * created; 0 on invalid sizes. */
+int64_t ps_estimate_bytes(int32_t n, int32_t levels, int64_t M);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLSARA_H */

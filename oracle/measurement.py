@@ -42,6 +42,10 @@ def _phase_tables(uv: np.ndarray, n: int):
     return eu, ev
 
 
+def _chunk(n: int) -> int:
+    return max(64, min(_CHUNK, (1 << 24) // (4 * n)))
+
+
 def Phi(x: np.ndarray, uv: np.ndarray, w: np.ndarray) -> np.ndarray:
     """Phi applied to a stack of maps x (k, n, n) -> (M, k) complex (Eq. meas_op, direct DFT)."""
     x = np.asarray(x)
@@ -50,12 +54,13 @@ def Phi(x: np.ndarray, uv: np.ndarray, w: np.ndarray) -> np.ndarray:
     k, n, _ = x.shape
     M = uv.shape[0]
     out = np.empty((M, k), dtype=np.complex128)
-    for m0 in range(0, M, _CHUNK):
-        m1 = min(M, m0 + _CHUNK)
+    ch = _chunk(n)
+    for m0 in range(0, M, ch):
+        m1 = min(M, m0 + ch)
         eu, ev = _phase_tables(uv[m0:m1], n)
-        # T[j, p, m] = sum_q x[j, p, q] eu[m, q]; then sum_p ev[m, p] T[j, p, m].
-        T = np.einsum("jpq,mq->jpm", x, eu, optimize=True)
-        out[m0:m1] = np.einsum("mp,jpm->mj", ev, T, optimize=True) * w[m0:m1, None]
+        # T[j, p, m] = sum_q x[j, p, q] eu[m, q]  (a matrix product), then sum_p ev[m, p] T[j, p, m].
+        T = np.tensordot(x, eu, axes=([2], [1]))
+        out[m0:m1] = np.sum(ev.T[None, :, :] * T, axis=1).T * w[m0:m1, None]
     return out
 
 
@@ -66,12 +71,14 @@ def Phi_adjoint(y: np.ndarray, uv: np.ndarray, w: np.ndarray, n: int) -> np.ndar
         return Phi_adjoint(y[:, None], uv, w, n)[0]
     M, k = y.shape
     out = np.zeros((k, n, n), dtype=np.complex128)
-    for m0 in range(0, M, _CHUNK):
-        m1 = min(M, m0 + _CHUNK)
+    ch = _chunk(n)
+    for m0 in range(0, M, ch):
+        m1 = min(M, m0 + ch)
         eu, ev = _phase_tables(uv[m0:m1], n)
         wy = y[m0:m1] * w[m0:m1, None]
-        # out[j, p, q] = sum_m conj(ev[m, p]) wy[m, j] conj(eu[m, q])
-        out += np.einsum("mp,mj,mq->jpq", np.conj(ev), wy, np.conj(eu), optimize=True)
+        # out[j, p, q] = sum_m conj(ev[m, p]) wy[m, j] conj(eu[m, q])  (a matrix product per j)
+        for j in range(k):
+            out[j] += np.conj(ev).T @ (wy[:, j:j + 1] * np.conj(eu))
     return out
 
 
@@ -119,6 +126,24 @@ def op_norm_sq(uv: np.ndarray, w: np.ndarray, n: int, iters: int = 200, tol: flo
             break
         lam = lam_new
     return lam
+
+
+def op_norm_sq_lanczos(uv: np.ndarray, w: np.ndarray, n: int, tol: float = 1e-12) -> float:
+    """||phi||_sp^2 as the largest eigenvalue of phi^dagger phi by Lanczos (scipy eigsh).
+
+    Same quantity as op_norm_sq; Lanczos converges even when the top eigenvalues
+    of the PSF-like operator phi^dagger phi are nearly degenerate.
+    """
+    from scipy.sparse.linalg import LinearOperator, eigsh
+
+    N4 = 4 * n * n
+
+    def mv(v):
+        x = np.asarray(v, dtype=np.float64).reshape(4, n, n)
+        return phi_adjoint(phi(x, uv, w), uv, w, n).ravel()
+    op = LinearOperator((N4, N4), matvec=mv, dtype=np.float64)
+    v0 = np.random.default_rng(0).normal(size=N4)
+    return float(eigsh(op, k=1, which="LA", tol=tol, v0=v0, return_eigenvectors=False)[0])
 
 
 def chi2_epsilon(M_b: int, sigma: float) -> float:

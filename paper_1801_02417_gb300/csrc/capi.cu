@@ -1,0 +1,901 @@
+// C ABI of the Polarized SARA imager (declared in include/polsara.h).
+//
+// One handle = one imaging problem resident on the device. ps_pd_iterate replays
+// a CUDA graph of one iteration of Algorithm 1:
+//   k_primal                    steps 3, 4, 9-12 and the Dirac part of 5-6
+//   k_analysis x levels         steps 5-6 (Psi^dagger of 2S'-S, soft-threshold dual)
+//   k_synthesis x levels        Psi A^(k+1) for the next step 3
+//   k_fwd_rows, k_fwd_cols      F Z of phi(2S'-S)                  (step 7)
+//   k_degrid                    G, mixing by L, B~ and ||B~/rho2 - Y||^2 partials
+//   k_block_scale               step 8 (l2-ball factor per block)
+//   k_grid, k_adj_cols, k_adj_rows   phi^dagger B^(k+1) for the next step 3
+// B is kept as R = B~/rho2 - Y with a per-block factor: B = c_b R, c_b =
+// rho2 (1 - min(1, eps_b / ||R_b||)), which is the step-8 result written out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using ps::Handle;
+
+struct ps_handle : public Handle {};
+
+namespace ps {
+cudaError_t configure_kernels();
+}
+
+static std::string g_create_error;
+
+static ps_status fail(Handle* h, ps_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CK(h, x)                                                                               \
+  do {                                                                                         \
+    cudaError_t _e = (x);                                                                      \
+    if (_e != cudaSuccess)                                                                     \
+      return fail((h), _e == cudaErrorMemoryAllocation ? PS_ENOMEM : PS_ECUDA,                 \
+                  std::string(#x) + ": " + cudaGetErrorString(_e));                          \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(Handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) h->bytes += (int64_t)(count * sizeof(T));
+  return e;
+}
+
+template <typename T>
+static void dfree(Handle* h, T*& p, size_t count) {
+  if (p) {
+    cudaFree(p);
+    h->bytes -= (int64_t)(count * sizeof(T));
+  }
+  p = nullptr;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int sweep_blocks_host(int N) { return (N + 1023) / 1024; }
+
+static void free_vis(Handle* h) {
+  const size_t M = h->M;
+  dfree(h, h->R, 4 * M);
+  dfree(h, h->Y, 4 * M);
+  dfree(h, h->vtmp, 4 * M);
+  dfree(h, h->rec, M);
+  dfree(h, h->perm, M);
+  dfree(h, h->eps, (size_t)h->nblocks);
+  dfree(h, h->cb, (size_t)h->nblocks);
+  dfree(h, h->chunk_start, (size_t)h->nchunks + 1);
+  dfree(h, h->chunk_block, (size_t)h->nchunks);
+  dfree(h, h->chunk_part, (size_t)h->nchunks);
+  dfree(h, h->block_chunk, (size_t)h->nblocks + 1);
+  dfree(h, h->items, (size_t)h->nitems);
+  dfree(h, h->gchunks, (size_t)h->ngchunks);
+  dfree(h, h->gperm, M);
+  dfree(h, h->gblk, M);
+  const size_t Wd = h->g.Wd;
+  dfree(h, h->T1, (size_t)h->n * Wd);
+  dfree(h, h->G, Wd * Wd);
+  dfree(h, h->Acc, 2 * Wd * Wd);
+  dfree(h, h->T2, (size_t)h->n * Wd);
+  dfree(h, h->tw, (size_t)h->g.K / 2);
+  dfree(h, h->corr, (size_t)h->n);
+  h->M = h->nblocks = h->nchunks = h->nitems = h->ngchunks = 0;
+  h->g = ps::GridGeom{};
+}
+
+static void drop_graph(Handle* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_mode = -1;
+}
+
+static void set_default_steps(Handle* h) {
+  const ps_config& c = h->cfg;
+  h->rho1 = c.rho1 > 0 ? c.rho1 : 1.0;
+  h->rho3 = c.rho3 > 0 ? c.rho3 : 1.0;
+  const double on = h->opnorm_sq > 0 ? h->opnorm_sq : 0.0;
+  h->rho2 = c.rho2 > 0 ? c.rho2 : (on > 0 ? 1.0 / on : 1.0);
+  double denom = h->rho2 * on;
+  if (h->mode != PS_NNLS) denom += h->rho1;
+  if (h->mode == PS_POLARIZED) denom += h->rho3;
+  h->tau = c.tau > 0 ? c.tau : (denom > 0 ? 0.99 / denom : 0.99);
+}
+
+static ps_status reset_state(Handle* h) {
+  const size_t N = h->N;
+  CK(h, cudaMemsetAsync(h->S, 0, 4 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->Z, 0, 2 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->C, 0, 4 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->D, 0, 2 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->A, 0, 36 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->PsiA, 0, 4 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->Adj, 0, 4 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->Xb, 0, 4 * N * sizeof(float), h->stream));
+  CK(h, cudaMemsetAsync(h->red, 0, (size_t)h->red_cap * sizeof(double), h->stream));
+  if (h->M > 0) {
+    CK(h, cudaMemsetAsync(h->R, 0, 4 * (size_t)h->M * sizeof(float2), h->stream));
+    CK(h, cudaMemsetAsync(h->cb, 0, (size_t)h->nblocks * sizeof(float), h->stream));
+  }
+  h->derived_valid = true;   // Psi 0 = 0, phi^dagger 0 = 0
+  h->iterations = 0;
+  return PS_OK;
+}
+
+// Psi A and phi^dagger(c_b R) of the current state.
+static ps_status compute_derived(Handle* h) {
+  CK(h, ps::sara_synthesis(h, h->A, h->PsiA));
+  if (h->M > 0) {
+    CK(h, ps::nufft_grid(h, h->R, 1));
+    CK(h, ps::nufft_adjoint_image(h, h->Adj));
+  } else {
+    CK(h, cudaMemsetAsync(h->Adj, 0, 4 * (size_t)h->N * sizeof(float), h->stream));
+  }
+  h->derived_valid = true;
+  return PS_OK;
+}
+
+// One iteration of Algorithm 1. With `ev` (PS_NSTAGES + 1 events) the stage
+// boundaries are recorded on the stream for ps_profile_stages.
+static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], h->stream) : cudaSuccess; };
+  cudaError_t e;
+  if ((e = mark(PS_STAGE_PRIMAL)) != cudaSuccess) return e;
+  if ((e = ps::primal_sweep(h)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_ANALYSIS)) != cudaSuccess) return e;
+  if (h->mode != PS_NNLS) {
+    e = ps::sara_analysis(h, h->Xb, h->A, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f);
+    if (e != cudaSuccess) return e;
+  }
+  if ((e = mark(PS_STAGE_SYNTHESIS)) != cudaSuccess) return e;
+  if (h->mode != PS_NNLS) {
+    e = ps::sara_synthesis(h, h->A, h->PsiA);
+    if (e != cudaSuccess) return e;
+  }
+  if ((e = mark(PS_STAGE_FWD_FFT)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_forward_grid(h, h->Xb)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_DEGRID)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_degrid(h, ps::DEG_DUAL, nullptr)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_BALL)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::block_scales(h)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_GRID)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_grid(h, h->R, 1)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_ADJ_FFT)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_adjoint_image(h, h->Adj)) != cudaSuccess) return e;
+  return mark(PS_NSTAGES);
+}
+
+static ps_status build_graph(Handle* h) {
+  drop_graph(h);
+  cudaGraph_t graph = nullptr;
+  CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = one_iteration(h);
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(h, PS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&h->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(h, PS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  h->graph_mode = h->mode;
+  return PS_OK;
+}
+
+#pragma GCC visibility push(default)
+extern "C" {
+
+const char* ps_last_error(const ps_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t ps_estimate_bytes(int32_t n, int32_t levels, int64_t M) {
+  if (n < 16 || n > 2048 || !is_pow2(n) || levels < 1 || (n % (1 << levels)) != 0 || M < 0) return 0;
+  const int64_t N = (int64_t)n * n, K = 2 * (int64_t)n;
+  const int64_t img = (28 + 72 + 16) * N * 4 + (8 * (int64_t)sweep_blocks_host((int)N) + 1024) * 8;
+  const int64_t vis = M * (3 * 32 + 16 + 4) + (M / ps::kChunk + 64) * 24;
+  const int64_t grid = 2 * (int64_t)n * K * 16 + 48 * K * K + K * 12 + (int64_t)n * 4;
+  return img + vis + grid;
+}
+
+int64_t ps_device_bytes(const ps_handle* h) { return h ? h->bytes : 0; }
+
+ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
+  if (!cfg || !out) return fail(nullptr, PS_EINVAL, "ps_create: null argument");
+  *out = nullptr;
+  const int n = cfg->n, L = cfg->levels;
+  if (n < 16 || n > 2048 || !is_pow2(n))
+    return fail(nullptr, PS_EINVAL, "ps_create: n must be a power of two in [16, 2048]");
+  if (L < 1 || (n % (1 << L)) != 0 || (n >> L) < 1)
+    return fail(nullptr, PS_EINVAL, "ps_create: levels must satisfy 1 <= levels and n divisible by 2^levels");
+  if (cfg->mode < PS_POLARIZED || cfg->mode > PS_NNLS) return fail(nullptr, PS_EINVAL, "ps_create: bad mode");
+  const int W = cfg->kernel_width == 0 ? 7 : cfg->kernel_width;
+  if (W != 5 && W != 7 && W != 9) return fail(nullptr, PS_EINVAL, "ps_create: kernel_width must be 5, 7 or 9");
+  if (cfg->tau < 0 || cfg->rho1 < 0 || cfg->rho2 < 0 || cfg->rho3 < 0)
+    return fail(nullptr, PS_EINVAL, "ps_create: step sizes must be >= 0");
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+    return fail(nullptr, PS_ECUDA, "ps_create: no CUDA device");
+
+  ps_handle* h = new ps_handle();
+  h->cfg = *cfg;
+  h->cfg.kernel_width = W;
+  h->n = n;
+  h->N = n * n;
+  h->L = L;
+  h->mode = cfg->mode;
+  auto bail = [&](ps_status st) {
+    g_create_error = h->err;
+    ps_destroy(h);
+    return st;
+  };
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      h->err = "ps_create: cudaStreamCreate failed";
+      return bail(PS_ECUDA);
+    }
+    h->own_stream = true;
+  }
+  cudaError_t e = ps::configure_kernels();
+  if (e != cudaSuccess) {
+    h->err = std::string("configure kernels: ") + cudaGetErrorString(e);
+    return bail(PS_ECUDA);
+  }
+  double filt[ps::kDb][ps::kMaxTaps];
+  ps::daubechies_filters(filt);
+  if ((e = ps::upload_filters(filt)) != cudaSuccess) {
+    h->err = std::string("upload filters: ") + cudaGetErrorString(e);
+    return bail(PS_ECUDA);
+  }
+  const size_t N = h->N;
+  h->red_cap = 8 * sweep_blocks_host((int)N) + 1024;
+  bool ok = dalloc(h, &h->S, 4 * N) == cudaSuccess && dalloc(h, &h->Z, 2 * N) == cudaSuccess &&
+            dalloc(h, &h->C, 4 * N) == cudaSuccess && dalloc(h, &h->D, 2 * N) == cudaSuccess &&
+            dalloc(h, &h->Xb, 4 * N) == cudaSuccess && dalloc(h, &h->PsiA, 4 * N) == cudaSuccess &&
+            dalloc(h, &h->Adj, 4 * N) == cudaSuccess && dalloc(h, &h->tmp4, 4 * N) == cudaSuccess &&
+            dalloc(h, &h->A, 36 * N) == cudaSuccess && dalloc(h, &h->T, 36 * N) == cudaSuccess &&
+            dalloc(h, &h->approx, 16 * N) == cudaSuccess && dalloc(h, &h->red, (size_t)h->red_cap) == cudaSuccess &&
+            cudaMallocHost((void**)&h->red_host, 1024 * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    h->err = "ps_create: device allocation failed";
+    return bail(PS_ENOMEM);
+  }
+  if (reset_state(h) != PS_OK) return bail(PS_ECUDA);
+  // Thresholds default to 1 (gamma = 1, W = 1).
+  std::vector<float> ones(36 * N, 1.0f);
+  if (cudaMemcpyAsync(h->T, ones.data(), ones.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    h->err = "ps_create: initialisation failed";
+    return bail(PS_ECUDA);
+  }
+  set_default_steps(h);
+  *out = h;
+  return PS_OK;
+}
+
+void ps_destroy(ps_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  free_vis(h);
+  const size_t N = h->N;
+  dfree(h, h->S, 4 * N);
+  dfree(h, h->Z, 2 * N);
+  dfree(h, h->C, 4 * N);
+  dfree(h, h->D, 2 * N);
+  dfree(h, h->Xb, 4 * N);
+  dfree(h, h->PsiA, 4 * N);
+  dfree(h, h->Adj, 4 * N);
+  dfree(h, h->tmp4, 4 * N);
+  dfree(h, h->tmp36, 36 * N);
+  dfree(h, h->A, 36 * N);
+  dfree(h, h->T, 36 * N);
+  dfree(h, h->approx, 16 * N);
+  dfree(h, h->red, (size_t)h->red_cap);
+  if (h->red_host) cudaFreeHost(h->red_host);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+ps_status ps_synchronize(ps_handle* h) {
+  if (!h) return PS_EINVAL;
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaGetLastError());
+  return PS_OK;
+}
+
+// Copy `bytes` from a caller pointer into device memory `dst` (or alias when on device).
+static ps_status stage_in(Handle* h, const void* src, size_t bytes, int device_ptrs, void* dst) {
+  CK(h, cudaMemcpyAsync(dst, src, bytes, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  return PS_OK;
+}
+
+static ps_status power_iteration(Handle* h);
+}  // extern "C"
+
+static __global__ void k_fill(float* p, int n, float v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+extern "C" {
+
+ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const float* vis, const float* weights,
+                              int32_t nblocks, const int64_t* block_offsets, const double* eps, int32_t device_ptrs) {
+  if (!h) return PS_EINVAL;
+  if (M64 < 0 || M64 > (int64_t)1 << 30) return fail(h, PS_EINVAL, "set_measurements: M out of range");
+  const int M = (int)M64;
+  if (M > 0 && (!uv || !vis || !block_offsets || !eps || nblocks < 1 || nblocks > 2047))
+    return fail(h, PS_EINVAL, "set_measurements: need uv, vis, block_offsets, eps and 1 <= nblocks <= 2047");
+  if (M > 0) {
+    if (block_offsets[0] != 0 || block_offsets[nblocks] != M64)
+      return fail(h, PS_EINVAL, "set_measurements: block_offsets must start at 0 and end at M");
+    for (int b = 0; b < nblocks; ++b) {
+      if (block_offsets[b + 1] < block_offsets[b]) return fail(h, PS_EINVAL, "set_measurements: offsets decrease");
+      if (!(eps[b] > 0) || !std::isfinite(eps[b])) return fail(h, PS_EINVAL, "set_measurements: eps must be > 0");
+    }
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  free_vis(h);
+  h->have_meas = false;
+
+  // Host copies of the measurement rows.
+  std::vector<double> uvh(2 * (size_t)M);
+  std::vector<float> wh(M, 1.0f);
+  if (M > 0) {
+    CK(h, cudaMemcpy(uvh.data(), uv, uvh.size() * sizeof(double),
+                     device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    if (weights)
+      CK(h, cudaMemcpy(wh.data(), weights, wh.size() * sizeof(float),
+                       device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  }
+  for (int m = 0; m < M; ++m) {
+    if (!std::isfinite(uvh[2 * m]) || !std::isfinite(uvh[2 * m + 1]) || std::fabs(uvh[2 * m]) >= M_PI ||
+        std::fabs(uvh[2 * m + 1]) >= M_PI)
+      return fail(h, PS_EINVAL, "set_measurements: |omega| must be < pi (radians per pixel)");
+    if (!(wh[m] >= 0.f) || !std::isfinite(wh[m])) return fail(h, PS_EINVAL, "set_measurements: weights must be >= 0");
+  }
+
+  // Grid geometry: tap centres c = floor(u + 1/2), u = omega K / (2 pi).
+  ps::GridGeom& g = h->g;
+  g.K = 2 * h->n;
+  g.logK = 0;
+  while ((1 << g.logK) < g.K) ++g.logK;
+  g.W = h->cfg.kernel_width;
+  g.beta = (float)ps::es_beta(g.W);
+  const int hw = g.W / 2;
+  std::vector<int> cx(M), cy(M);
+  std::vector<float> fx(M), fy(M);
+  int cmax = 0;
+  for (int m = 0; m < M; ++m) {
+    const double u = uvh[2 * m] * g.K / (2.0 * M_PI), v = uvh[2 * m + 1] * g.K / (2.0 * M_PI);
+    const double cu = std::floor(u + 0.5), cv = std::floor(v + 0.5);
+    cx[m] = (int)cu;
+    cy[m] = (int)cv;
+    fx[m] = (float)(u - cu);
+    fy[m] = (float)(v - cv);
+    cmax = std::max(cmax, std::max(std::abs(cx[m]), std::abs(cy[m])));
+  }
+  g.R = cmax + hw;
+  if (2 * g.R + 1 <= g.K) {
+    g.full = 0;
+    g.Wd = 2 * g.R + 1;
+    g.off = g.R;
+  } else {
+    g.full = 1;
+    g.Wd = g.K;
+    g.off = 0;
+  }
+  g.tilesX = (g.Wd + ps::kGridTile - 1) / ps::kGridTile;
+  auto gi = [&](int k) { return g.full ? (k & (g.K - 1)) : k + g.off; };
+
+  // Sort rows by gridding tile within each block (blocks stay contiguous).
+  std::vector<int32_t> perm(M);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<int64_t> key(M);
+  for (int m = 0; m < M; ++m) {
+    const int gy = gi(cy[m]), gx = gi(cx[m]);
+    const int64_t tile = (int64_t)(gy / ps::kGridTile) * g.tilesX + gx / ps::kGridTile;
+    key[m] = (tile << 26) | ((int64_t)gy << 13) | gx;
+  }
+  std::vector<int32_t> cstart, cblock, bchunk;
+  if (M > 0) h->offsets_host.assign(block_offsets, block_offsets + nblocks + 1);
+  else h->offsets_host.assign(1, 0);
+  std::vector<uint16_t> blk_of(M);
+  for (int b = 0; b < (M > 0 ? nblocks : 0); ++b) {
+    const int s = (int)block_offsets[b], e = (int)block_offsets[b + 1];
+    std::stable_sort(perm.begin() + s, perm.begin() + e, [&](int32_t a, int32_t c) { return key[a] < key[c]; });
+    bchunk.push_back((int32_t)cblock.size());
+    for (int c0 = s; c0 < e; c0 += ps::kChunk) {
+      cstart.push_back(c0);
+      cblock.push_back(b);
+    }
+    for (int i = s; i < e; ++i) blk_of[i] = (uint16_t)b;
+  }
+  if (M > 0) {
+    bchunk.push_back((int32_t)cblock.size());
+    cstart.push_back(M);
+  }
+  // Gridding order: every storage row sorted by tap-centre cell (tile-major).
+  std::vector<int32_t> gperm(M);
+  std::iota(gperm.begin(), gperm.end(), 0);
+  std::stable_sort(gperm.begin(), gperm.end(), [&](int32_t a, int32_t c) { return key[perm[a]] < key[perm[c]]; });
+  std::vector<uint16_t> gblk(M);
+  for (int j = 0; j < M; ++j) gblk[j] = blk_of[gperm[j]];
+  std::vector<ps::GridItem> items;
+  std::vector<int32_t> gchunks;
+  {
+    int j0 = 0;
+    while (j0 < M) {
+      const int64_t tile = key[perm[gperm[j0]]] >> 26;
+      int j1 = j0;
+      while (j1 < M && j1 - j0 < ps::kGridItem && (key[perm[gperm[j1]]] >> 26) == tile) ++j1;
+      ps::GridItem it{};
+      it.ty = (int32_t)(tile / g.tilesX);
+      it.tx = (int32_t)(tile % g.tilesX);
+      it.vstart = j0;
+      it.vend = j1;
+      it.cstart = (int32_t)gchunks.size();
+      int c0 = j0;
+      while (c0 < j1) {
+        const int64_t cell = key[perm[gperm[c0]]] & ((1LL << 26) - 1);
+        int c1 = c0;
+        while (c1 < j1 && c1 - c0 < ps::kBinChunk && (key[perm[gperm[c1]]] & ((1LL << 26) - 1)) == cell) ++c1;
+        const int gy = (int)(cell >> 13), gx = (int)(cell & 8191);
+        const int ly = gy - it.ty * ps::kGridTile, lx = gx - it.tx * ps::kGridTile;
+        gchunks.push_back((c0 - j0) | ((c1 - c0) << 10) | (ly << 16) | (lx << 24));
+        c0 = c1;
+      }
+      it.cend = (int32_t)gchunks.size();
+      items.push_back(it);
+      j0 = j1;
+    }
+  }
+  h->M = M;
+  h->nblocks = M > 0 ? nblocks : 0;
+  h->nchunks = (int)cblock.size();
+  h->nitems = (int)items.size();
+  h->ngchunks = (int)gchunks.size();
+  if (M > 0) h->eps_host.assign(eps, eps + h->nblocks);
+  else h->eps_host.clear();
+  h->block_chunk_host = bchunk;
+
+  std::vector<float4> rech(M);
+  double psf = 0.0;
+  for (int i = 0; i < M; ++i) {
+    const int m = perm[i];
+    const int packed = (cx[m] & 0xFFFF) | (cy[m] << 16);
+    float pf;
+    std::memcpy(&pf, &packed, sizeof(pf));
+    rech[i] = make_float4(fx[m], fy[m], wh[m], pf);
+    psf += 2.0 * (double)wh[m] * wh[m];
+  }
+  h->psf_peak = psf;
+
+  // Device buffers for the visibility domain and the grid.
+  const size_t Wd = g.Wd;
+  bool ok = dalloc(h, &h->R, 4 * (size_t)M) == cudaSuccess && dalloc(h, &h->Y, 4 * (size_t)M) == cudaSuccess &&
+            dalloc(h, &h->vtmp, 4 * (size_t)M) == cudaSuccess && dalloc(h, &h->rec, (size_t)M) == cudaSuccess &&
+            dalloc(h, &h->perm, (size_t)M) == cudaSuccess && dalloc(h, &h->eps, (size_t)h->nblocks) == cudaSuccess &&
+            dalloc(h, &h->cb, (size_t)h->nblocks) == cudaSuccess &&
+            dalloc(h, &h->chunk_start, cstart.size()) == cudaSuccess &&
+            dalloc(h, &h->chunk_block, cblock.size()) == cudaSuccess &&
+            dalloc(h, &h->chunk_part, cblock.size()) == cudaSuccess &&
+            dalloc(h, &h->block_chunk, bchunk.size()) == cudaSuccess && dalloc(h, &h->items, items.size()) == cudaSuccess &&
+            dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess && dalloc(h, &h->gperm, (size_t)M) == cudaSuccess &&
+            dalloc(h, &h->gblk, (size_t)M) == cudaSuccess &&
+            dalloc(h, &h->T1, (size_t)h->n * Wd) == cudaSuccess && dalloc(h, &h->G, Wd * Wd) == cudaSuccess &&
+            dalloc(h, &h->Acc, 2 * Wd * Wd) == cudaSuccess && dalloc(h, &h->T2, (size_t)h->n * Wd) == cudaSuccess &&
+            dalloc(h, &h->tw, (size_t)g.K / 2) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_vis(h);
+    return fail(h, PS_ENOMEM, "set_measurements: device allocation failed");
+  }
+  std::vector<float2> twh(g.K / 2);
+  for (int k = 0; k < g.K / 2; ++k) {
+    const double a = -2.0 * M_PI * k / g.K;
+    twh[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  std::vector<float> corrh(h->n);
+  for (int q = 0; q < h->n; ++q)
+    corrh[q] = (float)(1.0 / ps::es_fourier(2.0 * M_PI * (q - h->n / 2) / g.K, g.W, g.beta));
+  CK(h, cudaMemcpy(h->tw, twh.data(), twh.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->corr, corrh.data(), corrh.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (M > 0) {
+    CK(h, cudaMemcpy(h->rec, rech.data(), rech.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->eps, eps, h->nblocks * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->chunk_start, cstart.data(), cstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->chunk_block, cblock.data(), cblock.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->block_chunk, bchunk.data(), bchunk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->items, items.data(), items.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->gchunks, gchunks.data(), gchunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->gperm, gperm.data(), gperm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->gblk, gblk.data(), gblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    // Measurements into sorted order.
+    ps_status st = stage_in(h, vis, 4 * (size_t)M * sizeof(float2), device_ptrs, h->vtmp);
+    if (st != PS_OK) return st;
+    CK(h, ps::gather_vis(h, h->vtmp, h->Y));
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->have_meas = true;
+  ps_status st = power_iteration(h);
+  if (st != PS_OK) return st;
+  set_default_steps(h);
+  return reset_state(h);
+}
+
+static ps_status power_iteration(Handle* h) {
+  h->opnorm_sq = 0.0;
+  if (h->M == 0) return PS_OK;
+  const size_t N4 = 4 * (size_t)h->N;
+  std::vector<float> x(N4);
+  uint64_t s = 0x9E3779B97F4A7C15ull;
+  double nrm = 0.0;
+  for (size_t i = 0; i < N4; ++i) {
+    s = s * 6364136223846793005ull + 1442695040888963407ull;
+    x[i] = (float)((double)(s >> 11) / 9007199254740992.0 - 0.5);
+    nrm += (double)x[i] * x[i];
+  }
+  const float inv = (float)(1.0 / std::sqrt(nrm));
+  for (auto& v : x) v *= inv;
+  CK(h, cudaMemcpy(h->tmp4, x.data(), N4 * sizeof(float), cudaMemcpyHostToDevice));
+  double* dres = h->red + (size_t)h->red_cap - 600;
+  double lam = 0.0;
+  for (int it = 0; it < 1000; ++it) {
+    CK(h, ps::nufft_forward_grid(h, h->tmp4));
+    CK(h, ps::nufft_degrid(h, ps::DEG_APPLY, h->vtmp));
+    CK(h, ps::nufft_grid(h, h->vtmp, 0));
+    CK(h, ps::nufft_adjoint_image(h, h->Adj));
+    CK(h, ps::reduce_dot(h, h->tmp4, h->Adj, N4, dres));
+    CK(h, ps::reduce_dot(h, h->Adj, h->Adj, N4, dres + 1));
+    CK(h, cudaMemcpyAsync(h->red_host, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double lam_new = h->red_host[0], ny = std::sqrt(h->red_host[1]);
+    if (!(ny > 0) || !std::isfinite(ny)) return fail(h, PS_ENONFINITE, "power iteration: zero or non-finite phi^dagger phi x");
+    CK(h, ps::scale_copy(h, h->Adj, h->tmp4, N4, 1.0 / ny));
+    const bool done = it > 4 && std::fabs(lam_new - lam) <= 1e-7 * lam_new;
+    lam = lam_new;
+    if (done) break;
+  }
+  h->opnorm_sq = lam;
+  return PS_OK;
+}
+
+ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_t device_ptrs) {
+  if (!h) return PS_EINVAL;
+  if (!(gamma > 0) || !std::isfinite(gamma)) return fail(h, PS_EINVAL, "set_sara_weights: gamma must be > 0");
+  const size_t len = 36 * (size_t)h->N;
+  if (W) {
+    ps_status st = stage_in(h, W, len * sizeof(float), device_ptrs, h->T);
+    if (st != PS_OK) return st;
+    CK(h, ps::scale_copy(h, h->T, h->T, len, gamma));
+  } else {
+    std::vector<float> v(len, (float)gamma);
+    CK(h, cudaMemcpyAsync(h->T, v.data(), len * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  h->gamma = gamma;
+  if (!device_ptrs) CK(h, cudaStreamSynchronize(h->stream));
+  return PS_OK;
+}
+
+ps_status ps_set_mode(ps_handle* h, int32_t mode) {
+  if (!h) return PS_EINVAL;
+  if (mode < PS_POLARIZED || mode > PS_NNLS) return fail(h, PS_EINVAL, "set_mode: bad mode");
+  h->mode = mode;
+  h->cfg.mode = mode;
+  set_default_steps(h);
+  drop_graph(h);
+  return PS_OK;
+}
+
+ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter) {
+  if (!h) return PS_EINVAL;
+  if (n_iter < 0) return fail(h, PS_EINVAL, "pd_iterate: n_iter < 0");
+  if (!h->have_meas) return fail(h, PS_ESTATE, "pd_iterate: call ps_set_measurements first");
+  if (n_iter == 0) return PS_OK;
+  if (!h->derived_valid) {
+    ps_status st = compute_derived(h);
+    if (st != PS_OK) return st;
+  }
+  if (!h->graph || h->graph_mode != h->mode) {
+    ps_status st = build_graph(h);
+    if (st != PS_OK) return st;
+  }
+  for (int i = 0; i < n_iter; ++i) CK(h, cudaGraphLaunch(h->graph, h->stream));
+  h->iterations += n_iter;
+  return PS_OK;
+}
+
+ps_status ps_reweight(ps_handle* h, double delta) {
+  if (!h) return PS_EINVAL;
+  if (!(delta > 0) || !std::isfinite(delta)) return fail(h, PS_EINVAL, "reweight: delta must be > 0");
+  CK(h, ps::dirac_apply(h, h->S, nullptr, h->T, ps::SARA_REWEIGHT, 1.0f / 3.0f, (float)h->gamma, (float)delta));
+  CK(h, ps::sara_analysis(h, h->S, nullptr, h->T, ps::SARA_REWEIGHT, 1.0f / 3.0f, (float)h->gamma, (float)delta));
+  return PS_OK;
+}
+
+static ps_status copy_out(Handle* h, const void* dsrc, void* dst, size_t bytes, int device_ptrs) {
+  CK(h, cudaMemcpyAsync(dst, dsrc, bytes, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  if (!device_ptrs) CK(h, cudaStreamSynchronize(h->stream));
+  return PS_OK;
+}
+
+ps_status ps_get_stokes(ps_handle* h, float* out, int32_t device_ptrs) {
+  if (!h || !out) return h ? fail(h, PS_EINVAL, "get_stokes: null output") : PS_EINVAL;
+  return copy_out(h, h->S, out, 4 * (size_t)h->N * sizeof(float), device_ptrs);
+}
+
+ps_status ps_get_sara_weights(ps_handle* h, float* out, int32_t device_ptrs) {
+  if (!h || !out) return h ? fail(h, PS_EINVAL, "get_sara_weights: null output") : PS_EINVAL;
+  return copy_out(h, h->T, out, 36 * (size_t)h->N * sizeof(float), device_ptrs);
+}
+
+ps_status ps_get_state(ps_handle* h, const ps_state_view* v) {
+  if (!h || !v) return PS_EINVAL;
+  const size_t N = h->N;
+  const int dp = v->device_ptrs;
+  ps_status st;
+  if (v->S && (st = copy_out(h, h->S, v->S, 4 * N * sizeof(float), dp)) != PS_OK) return st;
+  if (v->Z && (st = copy_out(h, h->Z, v->Z, 2 * N * sizeof(float), dp)) != PS_OK) return st;
+  if (v->A && (st = copy_out(h, h->A, v->A, 36 * N * sizeof(float), dp)) != PS_OK) return st;
+  if (v->C && (st = copy_out(h, h->C, v->C, 4 * N * sizeof(float), dp)) != PS_OK) return st;
+  if (v->D && (st = copy_out(h, h->D, v->D, 2 * N * sizeof(float), dp)) != PS_OK) return st;
+  if (v->B && h->M > 0) {
+    float2* tmp = nullptr;
+    CK(h, dalloc(h, &tmp, 4 * (size_t)h->M));
+    cudaError_t e = cudaMemcpyAsync(h->vtmp, h->R, 4 * (size_t)h->M * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = ps::scale_vis(h, h->vtmp);
+    if (e == cudaSuccess) e = ps::scatter_vis(h, h->vtmp, tmp);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(v->B, tmp, 4 * (size_t)h->M * sizeof(float2),
+                          dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dfree(h, tmp, 4 * (size_t)h->M);
+    CK(h, e);
+  }
+  return PS_OK;
+}
+
+ps_status ps_set_state(ps_handle* h, const ps_state_view* v) {
+  if (!h || !v) return PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "set_state: call ps_set_measurements first");
+  const size_t N = h->N;
+  const int dp = v->device_ptrs;
+  ps_status st;
+  if (v->S && (st = stage_in(h, v->S, 4 * N * sizeof(float), dp, h->S)) != PS_OK) return st;
+  if (v->Z && (st = stage_in(h, v->Z, 2 * N * sizeof(float), dp, h->Z)) != PS_OK) return st;
+  if (v->A && (st = stage_in(h, v->A, 36 * N * sizeof(float), dp, h->A)) != PS_OK) return st;
+  if (v->C && (st = stage_in(h, v->C, 4 * N * sizeof(float), dp, h->C)) != PS_OK) return st;
+  if (v->D && (st = stage_in(h, v->D, 2 * N * sizeof(float), dp, h->D)) != PS_OK) return st;
+  if (v->B && h->M > 0) {
+    if ((st = stage_in(h, v->B, 4 * (size_t)h->M * sizeof(float2), dp, h->vtmp)) != PS_OK) return st;
+    CK(h, ps::gather_vis(h, h->vtmp, h->R));
+    k_fill<<<(h->nblocks + 127) / 128, 128, 0, h->stream>>>(h->cb, h->nblocks, 1.0f);
+    CK(h, cudaGetLastError());
+  }
+  if (!dp) CK(h, cudaStreamSynchronize(h->stream));
+  h->derived_valid = false;
+  return PS_OK;
+}
+
+ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, double* rho3, double* opnorm_sq) {
+  if (!h) return PS_EINVAL;
+  if (tau) *tau = h->tau;
+  if (rho1) *rho1 = h->rho1;
+  if (rho2) *rho2 = h->rho2;
+  if (rho3) *rho3 = h->rho3;
+  if (opnorm_sq) *opnorm_sq = h->opnorm_sq;
+  return PS_OK;
+}
+
+static ps_status ensure_tmp36(Handle* h) {
+  if (!h->tmp36) CK(h, dalloc(h, &h->tmp36, 36 * (size_t)h->N));
+  return PS_OK;
+}
+
+ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
+  if (!h || !out) return PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "compute_stats: call ps_set_measurements first");
+  const size_t N = h->N;
+  double* dres = h->red + (size_t)h->red_cap - 600;
+  // Relative change of the last iteration (partials written by k_primal).
+  const int nb = sweep_blocks_host((int)N);
+  std::vector<double> part(8 * (size_t)nb);
+  CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  // Residual Y - phi(S) per block, and the residual image.
+  std::vector<double> chunk(h->nchunks);
+  double rms = 0.0;
+  if (h->M > 0) {
+    CK(h, ps::nufft_forward_grid(h, h->S));
+    CK(h, ps::nufft_degrid(h, ps::DEG_RESID, h->vtmp));
+    CK(h, cudaMemcpyAsync(chunk.data(), h->chunk_part, chunk.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, ps::nufft_grid(h, h->vtmp, 0));
+    CK(h, ps::nufft_adjoint_image(h, h->tmp4));
+    CK(h, ps::reduce_dot(h, h->tmp4, h->tmp4, N, dres));
+    CK(h, cudaMemcpyAsync(h->red_host, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    rms = std::sqrt(h->red_host[0] / (double)N);
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < 4; ++c) {
+    double num = 0, den = 0;
+    for (int b = 0; b < nb; ++b) {
+      num += part[8 * (size_t)b + c];
+      den += part[8 * (size_t)b + 4 + c];
+    }
+    out->rel_change[c] = den > 0 ? std::sqrt(num / den) : INFINITY;
+  }
+  if (out->block_residual) {
+    for (int b = 0; b < std::min(out->nblocks, h->nblocks); ++b) {
+      double s = 0;
+      for (int c = h->block_chunk_host[b]; c < h->block_chunk_host[b + 1]; ++c) s += chunk[c];
+      out->block_residual[b] = std::sqrt(s);
+    }
+  }
+  out->zeta = h->psf_peak > 0 ? zeta_sigma * rms / h->psf_peak : 0.0;
+  CK(h, ps::violation_count(h, h->S, out->zeta, dres + 2));
+  ps_status st = ensure_tmp36(h);
+  if (st != PS_OK) return st;
+  CK(h, ps::dirac_apply(h, h->S, h->tmp36, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+  CK(h, ps::sara_analysis(h, h->S, h->tmp36, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+  CK(h, ps::weighted_l1(h, h->tmp36, h->T, dres + 4));
+  CK(h, cudaMemcpyAsync(h->red_host, dres, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  out->violations = (int64_t)h->red_host[2];
+  out->violations_raw = (int64_t)h->red_host[3];
+  out->weighted_l1 = h->red_host[4];
+  out->iterations = h->iterations;
+  return PS_OK;
+}
+
+ps_status ps_apply_phi(ps_handle* h, const float* S, float* Y, int32_t device_ptrs) {
+  if (!h || !S || !Y) return h ? fail(h, PS_EINVAL, "apply_phi: null pointer") : PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "apply_phi: call ps_set_measurements first");
+  if (h->M == 0) return PS_OK;
+  const size_t N4 = 4 * (size_t)h->N, V = 4 * (size_t)h->M;
+  const float* X = S;
+  if (!device_ptrs) {
+    CK(h, cudaMemcpyAsync(h->tmp4, S, N4 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    X = h->tmp4;
+  }
+  CK(h, ps::nufft_forward_grid(h, X));
+  CK(h, ps::nufft_degrid(h, ps::DEG_APPLY, h->vtmp));
+  if (device_ptrs) {
+    CK(h, ps::scatter_vis(h, h->vtmp, (float2*)Y));
+    return PS_OK;
+  }
+  float2* tmp = nullptr;
+  CK(h, dalloc(h, &tmp, V));
+  cudaError_t e = ps::scatter_vis(h, h->vtmp, tmp);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Y, tmp, V * sizeof(float2), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, V);
+  CK(h, e);
+  return PS_OK;
+}
+
+ps_status ps_apply_phi_adjoint(ps_handle* h, const float* Yin, float* S, int32_t device_ptrs) {
+  if (!h || !Yin || !S) return h ? fail(h, PS_EINVAL, "apply_phi_adjoint: null pointer") : PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "apply_phi_adjoint: call ps_set_measurements first");
+  const size_t N4 = 4 * (size_t)h->N, V = 4 * (size_t)h->M;
+  float* out = device_ptrs ? S : h->tmp4;
+  if (h->M == 0) {
+    CK(h, cudaMemsetAsync(out, 0, N4 * sizeof(float), h->stream));
+  } else if (device_ptrs) {
+    CK(h, ps::gather_vis(h, (const float2*)Yin, h->vtmp));
+  } else {
+    float2* tmp = nullptr;
+    CK(h, dalloc(h, &tmp, V));
+    cudaError_t e = cudaMemcpyAsync(tmp, Yin, V * sizeof(float2), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = ps::gather_vis(h, tmp, h->vtmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dfree(h, tmp, V);
+    CK(h, e);
+  }
+  if (h->M > 0) {
+    CK(h, ps::nufft_grid(h, h->vtmp, 0));
+    CK(h, ps::nufft_adjoint_image(h, out));
+  }
+  if (!device_ptrs) return copy_out(h, h->tmp4, S, N4 * sizeof(float), 0);
+  return PS_OK;
+}
+
+ps_status ps_apply_psi_adjoint(ps_handle* h, const float* S, float* A, int32_t device_ptrs) {
+  if (!h || !S || !A) return h ? fail(h, PS_EINVAL, "apply_psi_adjoint: null pointer") : PS_EINVAL;
+  const size_t N4 = 4 * (size_t)h->N;
+  const float* X = S;
+  float* coef = A;
+  if (!device_ptrs) {
+    ps_status st = ensure_tmp36(h);
+    if (st != PS_OK) return st;
+    CK(h, cudaMemcpyAsync(h->tmp4, S, N4 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    X = h->tmp4;
+    coef = h->tmp36;
+  }
+  CK(h, ps::dirac_apply(h, X, coef, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+  CK(h, ps::sara_analysis(h, X, coef, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+  if (!device_ptrs) return copy_out(h, h->tmp36, A, 36 * (size_t)h->N * sizeof(float), 0);
+  return PS_OK;
+}
+
+ps_status ps_apply_psi(ps_handle* h, const float* A, float* S, int32_t device_ptrs) {
+  if (!h || !A || !S) return h ? fail(h, PS_EINVAL, "apply_psi: null pointer") : PS_EINVAL;
+  const float* coef = A;
+  float* out = S;
+  if (!device_ptrs) {
+    ps_status st = ensure_tmp36(h);
+    if (st != PS_OK) return st;
+    CK(h, cudaMemcpyAsync(h->tmp36, A, 36 * (size_t)h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    coef = h->tmp36;
+    out = h->tmp4;
+  }
+  CK(h, ps::sara_synthesis(h, coef, out));
+  if (!device_ptrs) return copy_out(h, h->tmp4, S, 4 * (size_t)h->N * sizeof(float), 0);
+  return PS_OK;
+}
+
+ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms) {
+  if (!h || !stage_ms || n_iter < 1) return h ? fail(h, PS_EINVAL, "profile_stages: bad arguments") : PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "profile_stages: call ps_set_measurements first");
+  if (!h->derived_valid) {
+    ps_status st = compute_derived(h);
+    if (st != PS_OK) return st;
+  }
+  cudaEvent_t ev[PS_NSTAGES + 1];
+  for (int i = 0; i <= PS_NSTAGES; ++i) CK(h, cudaEventCreate(&ev[i]));
+  std::vector<double> acc(PS_NSTAGES, 0.0);
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+    e = one_iteration(h, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[PS_NSTAGES]);
+    for (int s = 0; s < PS_NSTAGES && e == cudaSuccess; ++s) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+      acc[s] += ms;
+    }
+  }
+  for (int i = 0; i <= PS_NSTAGES; ++i) cudaEventDestroy(ev[i]);
+  CK(h, e);
+  h->iterations += n_iter;
+  for (int s = 0; s < PS_NSTAGES; ++s) stage_ms[s] = acc[s] / n_iter;
+  return PS_OK;
+}
+
+int32_t ps_kernels_per_iteration(const ps_handle* h) {
+  if (!h) return 0;
+  int k = 1;                                   // k_primal
+  if (h->mode != PS_NNLS) k += 2 * h->L;       // analysis + synthesis levels
+  if (h->M > 0) k += 2 + 1 + 1 + 1 + 2;        // fwd rows/cols, degrid, block scale, grid, adj cols/rows
+  return k;
+}
+
+ps_status ps_wavelet_filters(double* out) {
+  if (!out) return PS_EINVAL;
+  double h[ps::kDb][ps::kMaxTaps];
+  ps::daubechies_filters(h);
+  std::memcpy(out, h, sizeof(h));
+  return PS_OK;
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

@@ -1,0 +1,144 @@
+// Internal declarations of the Polarized SARA CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "polsara.h"
+
+namespace ps {
+
+constexpr int kBases = 9;        // Dirac + db1..db8
+constexpr int kDb = 8;           // Daubechies bases
+constexpr int kMaxTaps = 16;     // db8 filter length
+constexpr int kGridTile = 16;    // gridding tile side (cells)
+constexpr int kChunk = 1024;     // visibilities per reduction chunk
+constexpr int kGridItem = 512;   // visibilities per gridding work item
+constexpr int kBinChunk = 32;    // visibilities per same-cell accumulation chunk
+
+// Analysis / synthesis kernel modes.
+enum { SARA_DUAL = 0, SARA_APPLY = 1, SARA_REWEIGHT = 2 };
+// Degridding modes.
+enum { DEG_DUAL = 0, DEG_APPLY = 1, DEG_RESID = 2 };
+
+struct GridItem {      // one gridding CTA: gridding-order rows [vstart, vend), centres in tile (ty, tx),
+  int32_t ty, tx;      // same-cell chunks [cstart, cend)
+  int32_t vstart, vend, cstart, cend;
+  int32_t pad0, pad1;
+};
+
+// Geometry of the NUFFT grid: the K x K oversampled spectrum is kept only on a
+// window of frequencies [-R, R]^2 covering every interpolation tap (window
+// mode), or whole (full mode, indices modulo K).
+struct GridGeom {
+  int K = 0, logK = 0;   // oversampled FFT length (2n)
+  int W = 7;             // interpolation kernel width
+  int R = 0;             // window half-width (cells)
+  int Wd = 0;            // stored grid side: 2R+1 (window) or K (full)
+  int full = 0;          // 1: full grid, indices wrap modulo K
+  int off = 0;           // grid index of frequency k: (k + off) [& (K-1) if full]
+  int tilesX = 0;        // gridding tiles per side
+  float beta = 0.f;      // ES kernel shape
+};
+
+struct Handle {
+  ps_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int n = 0, N = 0, L = 0, mode = PS_POLARIZED;
+  double tau = 0, rho1 = 1, rho2 = 1, rho3 = 1, opnorm_sq = 0, gamma = 1;
+  bool have_meas = false;
+  bool derived_valid = false;     // PsiA and Adj hold Psi A and phi^dagger B of the current state
+  int64_t iterations = 0;
+  int64_t bytes = 0;
+
+  // Image-domain state (float32 planes).
+  float *S = nullptr, *Z = nullptr, *C = nullptr, *D = nullptr;
+  float *Xb = nullptr;        // 2 S^(k+1) - S^(k)
+  float *PsiA = nullptr;      // Psi A
+  float *Adj = nullptr;       // phi^dagger B
+  float *tmp4 = nullptr;      // 4N scratch for operators
+  float *A = nullptr, *T = nullptr;   // 36N coefficients and thresholds gamma W
+  float *approx = nullptr;    // 2 ping-pong buffers of 32 * (N/4) approximations
+  double *red = nullptr;      // reduction partials
+  int red_cap = 0;
+  double *red_host = nullptr; // pinned
+
+  // Visibility-domain state, rows sorted by tile within each block.
+  int M = 0, nblocks = 0;
+  float2 *R = nullptr;        // residual form of B: B = c_b R  (M x 4)
+  float2 *Y = nullptr;        // measurements (M x 4)
+  float4 *rec = nullptr;      // (fx, fy, w, packed (cx, cy))
+  int32_t *perm = nullptr;    // sorted row -> caller row
+  float2 *vtmp = nullptr;     // M x 4 scratch
+  double *eps = nullptr;      // per block radius (device)
+  float *cb = nullptr;        // per block scale c_b (device)
+  int nchunks = 0;
+  int32_t *chunk_start = nullptr;  // nchunks+1 (device)
+  int32_t *chunk_block = nullptr;  // nchunks
+  double *chunk_part = nullptr;    // nchunks partial sums
+  int32_t *block_chunk = nullptr;  // nblocks+1 first chunk of each block
+  int nitems = 0, ngchunks = 0;
+  GridItem *items = nullptr;       // gridding work items
+  int32_t *gchunks = nullptr;      // packed (start, count, ly, lx) of same-cell chunks
+  int32_t *gperm = nullptr;        // gridding order -> storage row
+  uint16_t *gblk = nullptr;        // block of each gridding-order row
+  std::vector<double> eps_host;
+  std::vector<int32_t> block_chunk_host;
+  double psf_peak = 0.0;      // 2 sum w_m^2: peak of the Stokes-I PSF
+  float *tmp36 = nullptr;     // 36N scratch for operator calls (allocated on first use)
+  std::vector<int64_t> offsets_host;
+
+  // NUFFT buffers.
+  GridGeom g;
+  float4 *T1 = nullptr;       // n x Wd row spectra (forward)
+  float4 *G = nullptr;        // Wd x Wd packed spectra (I+iQ, U+iV)
+  float4 *Acc = nullptr;      // Wd x Wd x 2 gridding accumulators (xI, xQ | xU, xV)
+  float4 *T2 = nullptr;       // n x Wd column-transformed adjoint
+  float2 *tw = nullptr;       // K/2 twiddles exp(-2 pi i k / K)
+  float *corr = nullptr;      // n de-apodisation factors 1 / phihat(2 pi x / K)
+
+  // CUDA graph of one iteration.
+  cudaGraphExec_t graph = nullptr;
+  int graph_mode = -1;
+};
+
+// Host-side constants.
+void daubechies_filters(double h[kDb][kMaxTaps]);          // db1..db8 scaling filters
+double es_beta(int W);
+double es_kernel(double t, int W, double beta);            // ES kernel value at offset t (cells)
+double es_fourier(double xi, int W, double beta);          // its Fourier transform at xi
+
+// Kernel launchers (return cudaGetLastError()).
+cudaError_t upload_filters(const double h[kDb][kMaxTaps]);
+
+// NUFFT pieces (nufft.cu).
+cudaError_t nufft_forward_grid(Handle* h, const float* X);                 // X (4 planes) -> G
+cudaError_t nufft_degrid(Handle* h, int mode, float2* out);                // G -> visibilities
+cudaError_t nufft_grid(Handle* h, const float2* in, int use_block_scale);  // visibilities -> Acc
+cudaError_t nufft_adjoint_image(Handle* h, float* out);                    // Acc -> 4 planes
+cudaError_t block_scales(Handle* h);                                        // chunk partials -> c_b
+
+// SARA pieces (sara.cu).
+cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, int mode,
+                          float scale, float gamma, float delta);
+cudaError_t sara_synthesis(Handle* h, const float* coef, float* out);
+
+// Elementwise / reductions (prox.cu).
+cudaError_t primal_sweep(Handle* h);
+cudaError_t dirac_apply(Handle* h, const float* X, float* coef, float* thr, int mode,
+                        float scale, float gamma, float delta);
+cudaError_t reduce_dot(Handle* h, const float* a, const float* b, size_t len, double* dev_out);
+cudaError_t violation_count(Handle* h, const float* S, double zeta, double* dev_out);
+cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* dev_out);
+cudaError_t vis_norms(Handle* h, const float2* v, double* dev_out);
+cudaError_t scale_copy(Handle* h, const float* x, float* y, size_t len, double s);
+cudaError_t gather_vis(Handle* h, const float2* user, float2* sorted);
+cudaError_t scatter_vis(Handle* h, const float2* sorted, float2* user);
+cudaError_t scale_vis(Handle* h, float2* v);   // v = c_b v per block (state readout)
+
+}  // namespace ps

@@ -1,0 +1,511 @@
+// Measurement operator phi = Phi S L and its adjoint (Section 5.1, Eq. meas_op;
+// Algorithm 1 steps 3 and 7), as a non-uniform FFT on the GPU.
+//
+// Phi = G F Z: Z de-apodises and zero-pads each map to the K = 2n grid, F is the
+// K x K FFT, G interpolates the spectrum at each sampled frequency with a W x W
+// "exponential of semicircle" kernel. The four real Stokes maps travel as two
+// complex images, I + iQ and U + iV, so two complex FFTs serve four maps; the
+// correlations are recovered from the spectrum at +u and -u (Hermitian
+// symmetry of real maps) and mixed by L of Section 2.1 inside the degridding
+// kernel. The spectrum is stored only on the window of frequencies the
+// interpolation touches ([-R, R]^2), which prunes the column FFTs and the grid.
+//
+// Kernels (one launch each):
+//   k_fwd_rows    row FFTs of the de-apodised, zero-padded rows     (n CTAs)
+//   k_fwd_cols    column FFTs, kept on the window                    (Wd CTAs)
+//   k_degrid      interpolation + Stokes->correlation mixing + dual update of B
+//                 and per-chunk FP64 partial of ||B~/rho2 - Y||^2     (1 CTA / chunk)
+//   k_block_scale per-block l2-ball projection factor (FP64)
+//   k_grid        mixing by conj(L) + tile-privatised gridding in shared memory
+//   k_adj_cols    Hermitian symmetrisation + inverse column FFTs     (R+1 CTAs)
+//   k_adj_rows    inverse row FFTs + crop + de-apodisation -> phi^dagger planes
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace ps {
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 f4sub(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 f4scale(float4 a, float s) {
+  return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+}
+__device__ __forceinline__ float4 f4fma(float s, float4 a, float4 acc) {
+  return make_float4(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y), fmaf(s, a.z, acc.z), fmaf(s, a.w, acc.w));
+}
+// Multiply both complex numbers held in a float4 by w.
+__device__ __forceinline__ float4 cmul2(float4 a, float2 w) {
+  return make_float4(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x,
+                     a.z * w.x - a.w * w.y, a.z * w.y + a.w * w.x);
+}
+__device__ __forceinline__ int bitrev(int i, int logK) { return (int)(__brev((unsigned)i) >> (32 - logK)); }
+
+// In-place radix-2 decimation-in-time FFT of K float4 (two complex sequences)
+// held in shared memory in bit-reversed order; output in natural order.
+// INV selects exp(+2 pi i jk/K) (no 1/K normalisation).
+template <bool INV>
+__device__ void fft_smem(float4* buf, const float2* tw, int K, int logK) {
+  for (int s = 0; s < logK; ++s) {
+    const int hs = 1 << s;
+    const int step = K >> (s + 1);
+    for (int b = threadIdx.x; b < (K >> 1); b += blockDim.x) {
+      const int pos = b & (hs - 1);
+      const int i0 = ((b >> s) << (s + 1)) + pos;
+      const int i1 = i0 + hs;
+      float2 w = tw[pos * step];
+      if (INV) w.y = -w.y;
+      const float4 u = buf[i0];
+      const float4 v = cmul2(buf[i1], w);
+      buf[i0] = f4add(u, v);
+      buf[i1] = f4sub(u, v);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int gidx(int k, int off, int full, int K) {
+  return full ? (k & (K - 1)) : (k + off);
+}
+
+// ---------------------------------------------------------------- forward
+__global__ void k_fwd_rows(const float* __restrict__ X, int n, int N, const float* __restrict__ corr,
+                           const float2* __restrict__ tw, int K, int logK, float4* __restrict__ T1,
+                           int Wd, int off, int full) {
+  extern __shared__ float4 sm[];
+  float4* buf = sm;
+  float2* stw = reinterpret_cast<float2*>(sm + K);
+  const int p = blockIdx.x;
+  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  const float cy = corr[p];
+  const size_t row = (size_t)p * n;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int idx = (q - n / 2 + K) & (K - 1);
+    const float c = cy * corr[q];
+    const size_t o = row + q;
+    buf[bitrev(idx, logK)] = make_float4(X[o] * c, X[N + o] * c, X[2 * (size_t)N + o] * c,
+                                         X[3 * (size_t)N + o] * c);
+  }
+  __syncthreads();
+  fft_smem<false>(buf, stw, K, logK);
+  for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
+    const int k = full ? gx : gx - off;
+    T1[(size_t)p * Wd + gx] = buf[(k + K) & (K - 1)];
+  }
+}
+
+__global__ void k_fwd_cols(const float4* __restrict__ T1, int n, const float2* __restrict__ tw, int K,
+                           int logK, float4* __restrict__ G, int Wd, int off, int full) {
+  extern __shared__ float4 sm[];
+  float4* buf = sm;
+  float2* stw = reinterpret_cast<float2*>(sm + K);
+  const int gx = blockIdx.x;
+  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int idx = (p - n / 2 + K) & (K - 1);
+    buf[bitrev(idx, logK)] = T1[(size_t)p * Wd + gx];
+  }
+  __syncthreads();
+  fft_smem<false>(buf, stw, K, logK);
+  for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
+    const int k = full ? gy : gy - off;
+    G[(size_t)gy * Wd + gx] = buf[(k + K) & (K - 1)];
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void es_weights(float f, float beta, float* wt) {
+  // wt[j] = phi(f + hw - j), tap j at frequency c - hw + j.
+  constexpr int hw = W / 2;
+  const float inv = 2.0f / W;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const float z = (f + (float)(hw - j)) * inv;
+    const float s = 1.0f - z * z;
+    wt[j] = s > 0.f ? __expf(beta * (sqrtf(s) - 1.0f)) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void unpack_rec(float4 r, float& fx, float& fy, float& w, int& cx, int& cy) {
+  fx = r.x;
+  fy = r.y;
+  w = r.z;
+  const int pk = __float_as_int(r.w);
+  cx = (int)(short)(pk & 0xFFFF);
+  cy = pk >> 16;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T r = 0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : (T)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// Interpolate the packed spectra at +u and -u, unpack the four Stokes spectra,
+// mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. One CTA per chunk.
+template <int W>
+__global__ void __launch_bounds__(256) k_degrid(
+    const float4* __restrict__ rec, const float4* __restrict__ G, int Wd, int off, int full, int K,
+    float beta, int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
+    const float* __restrict__ cb, float inv_rho2, const int32_t* __restrict__ chunk_start,
+    const int32_t* __restrict__ chunk_block, double* __restrict__ chunk_part, float2* __restrict__ out) {
+  __shared__ double sh[32];
+  constexpr int hw = W / 2;
+  const int ch = blockIdx.x;
+  const int m0 = chunk_start[ch], m1 = chunk_start[ch + 1];
+  const float cscale = (mode == DEG_DUAL) ? cb[chunk_block[ch]] * inv_rho2 : 0.f;
+  double acc = 0.0;
+  for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+    float fx, fy, w;
+    int cx, cy;
+    unpack_rec(rec[m], fx, fy, w, cx, cy);
+    float wx[W], wy[W];
+    es_weights<W>(fx, beta, wx);
+    es_weights<W>(fy, beta, wy);
+    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
+#pragma unroll
+    for (int jy = 0; jy < W; ++jy) {
+      const float4* rowp = G + (size_t)gidx(cy - hw + jy, off, full, K) * Wd;
+      const float4* rown = G + (size_t)gidx(-cy - hw + jy, off, full, K) * Wd;
+      float4 ap = make_float4(0.f, 0.f, 0.f, 0.f), an = ap;
+#pragma unroll
+      for (int jx = 0; jx < W; ++jx) {
+        ap = f4fma(wx[jx], __ldg(rowp + gidx(cx - hw + jx, off, full, K)), ap);
+        an = f4fma(wx[W - 1 - jx], __ldg(rown + gidx(-cx - hw + jx, off, full, K)), an);
+      }
+      sp = f4fma(wy[jy], ap, sp);
+      sn = f4fma(wy[W - 1 - jy], an, sn);
+    }
+    // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
+    const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
+    const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
+    float4 v01 = make_float4(w * (FIr + FQr), w * (FIi + FQi), w * sp.z, w * sp.w);   // RR, RL = G2(u)
+    float4 v23 = make_float4(w * sn.z, -w * sn.w, w * (FIr - FQr), w * (FIi - FQi));  // LR = conj G2(-u), LL
+    float4* R4 = reinterpret_cast<float4*>(R);
+    const float4* Y4 = reinterpret_cast<const float4*>(Yv);
+    if (mode == DEG_DUAL) {
+      const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
+      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
+      v01 = f4sub(f4fma(cscale, r0, v01), y0);
+      v23 = f4sub(f4fma(cscale, r1, v23), y1);
+      R4[2 * (size_t)m] = v01;
+      R4[2 * (size_t)m + 1] = v23;
+      acc += (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w +
+                      v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
+    } else if (mode == DEG_RESID) {
+      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
+      v01 = f4sub(y0, v01);
+      v23 = f4sub(y1, v23);
+      acc += (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w +
+                      v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
+      if (out) {
+        float4* o4 = reinterpret_cast<float4*>(out);
+        o4[2 * (size_t)m] = v01;
+        o4[2 * (size_t)m + 1] = v23;
+      }
+    } else {
+      float4* o4 = reinterpret_cast<float4*>(out);
+      o4[2 * (size_t)m] = v01;
+      o4[2 * (size_t)m + 1] = v23;
+    }
+  }
+  if (mode != DEG_APPLY) {
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) chunk_part[ch] = s;
+  }
+}
+
+// Per-block factor c_b of B = c_b R after the l2-ball step (Algorithm 1 step 8):
+// with r = ||B~/rho2 - Y||_b, c_b = rho2 (1 - min(1, radius / r)).
+__global__ void k_block_scale(const double* __restrict__ part, const int32_t* __restrict__ block_chunk,
+                              const double* __restrict__ eps, int nblocks, double rho2, int literal,
+                              float* __restrict__ cb) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  double s = 0.0;
+  for (int c = block_chunk[b]; c < block_chunk[b + 1]; ++c) s += part[c];
+  const double r = sqrt(s);
+  const double radius = literal ? eps[b] / rho2 : eps[b];
+  const double keep = (r > radius) ? radius / r : 1.0;
+  cb[b] = (float)(rho2 * (1.0 - keep));
+}
+
+// Gridding (adjoint of the interpolation), Alg. 1 step 3's phi^dagger.
+// Visibilities are globally sorted by tap-centre cell. One CTA owns a work item:
+// up to kGridItem visibilities whose centres lie in one kGridTile^2 tile.
+//  1. Each thread stages one visibility: the conj(L)-mixed rows
+//     x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL), scaled by
+//     c_b w_m, and its W x and W y kernel weights, in shared memory.
+//  2. Visibilities sharing a centre cell (a "bin", split into chunks of <= 32)
+//     touch the same W x W cells, so thread (chunk, jy) accumulates the W x 8
+//     outputs of kernel row jy over the chunk in registers, then adds them once
+//     to a shared-memory tile (tile + halo).
+//  3. The tile is added to the global accumulator (one float4 atomic per
+//     non-zero half-cell).
+// Channels are gridded at +u only; k_adj_cols forms the -u half by Hermitian
+// symmetrisation.
+template <int W>
+__global__ void __launch_bounds__(256) k_grid(
+    const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const int32_t* __restrict__ gperm,
+    const uint16_t* __restrict__ gblk, const float4* __restrict__ rec, const float2* __restrict__ vin,
+    const float* __restrict__ cb, int use_scale, int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
+  constexpr int TS = kGridTile;
+  constexpr int SS = TS + W - 1;
+  constexpr int hw = W / 2;
+  constexpr int V = kGridItem;
+  extern __shared__ float4 smg[];
+  float* acc = reinterpret_cast<float*>(smg);   // SS*SS*8
+  float* xs = acc + SS * SS * 8;         // 8 x V
+  float* wxs = xs + 8 * V;               // W x V
+  float* wys = wxs + W * V;              // W x V
+  const GridItem it = items[blockIdx.x];
+  for (int i = threadIdx.x; i < SS * SS * 8; i += blockDim.x) acc[i] = 0.f;
+  const int nv = it.vend - it.vstart;
+  const float4* v4 = reinterpret_cast<const float4*>(vin);
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const int g = it.vstart + j;
+    const int idx = gperm[g];
+    float fx, fy, w;
+    int cx, cy;
+    unpack_rec(rec[idx], fx, fy, w, cx, cy);
+    const float s = (use_scale ? cb[gblk[g]] : 1.0f) * w;
+    const float4 b0 = v4[2 * (size_t)idx], b1 = v4[2 * (size_t)idx + 1];   // RR, RL | LR, LL
+    xs[0 * V + j] = s * (b0.x + b1.z);
+    xs[1 * V + j] = s * (b0.y + b1.w);
+    xs[2 * V + j] = s * (b0.x - b1.z);
+    xs[3 * V + j] = s * (b0.y - b1.w);
+    xs[4 * V + j] = s * (b0.z + b1.x);
+    xs[5 * V + j] = s * (b0.w + b1.y);
+    xs[6 * V + j] = -s * (b1.y - b0.w);
+    xs[7 * V + j] = s * (b1.x - b0.z);
+    float wx[W], wy[W];
+    es_weights<W>(fx, beta, wx);
+    es_weights<W>(fy, beta, wy);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      wxs[k * V + j] = wx[k];
+      wys[k * V + j] = wy[k];
+    }
+  }
+  __syncthreads();
+  const int per = blockDim.x / W;
+  const int cl = threadIdx.x / W, jy = threadIdx.x - cl * W;
+  const int nc = it.cend - it.cstart;
+  if (cl < per) {
+    for (int c = cl; c < nc; c += per) {
+      const int pk = chunks[it.cstart + c];
+      const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
+      float a[W][8];
+#pragma unroll
+      for (int jx = 0; jx < W; ++jx)
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) a[jx][ch] = 0.f;
+      for (int v = v0; v < v0 + cnt; ++v) {
+        const float wyv = wys[jy * V + v];
+        float x[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) x[ch] = wyv * xs[ch * V + v];
+#pragma unroll
+        for (int jx = 0; jx < W; ++jx) {
+          const float wv = wxs[jx * V + v];
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) a[jx][ch] = fmaf(wv, x[ch], a[jx][ch]);
+        }
+      }
+      float* dst = acc + ((ly + jy) * SS + lx) * 8;
+#pragma unroll
+      for (int jx = 0; jx < W; ++jx)
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) atomicAdd(dst + jx * 8 + ch, a[jx][ch]);
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < SS * SS; c += blockDim.x) {
+    const int ly = c / SS, lx = c - (c / SS) * SS;
+    int gy = it.ty * TS - hw + ly, gx = it.tx * TS - hw + lx;
+    if (full) {
+      gy &= (K - 1);
+      gx &= (K - 1);
+    } else if (gy < 0 || gy >= Wd || gx < 0 || gx >= Wd) {
+      continue;
+    }
+    const float* a = acc + c * 8;
+    const float4 lo = make_float4(a[0], a[1], a[2], a[3]);
+    const float4 hi = make_float4(a[4], a[5], a[6], a[7]);
+    float4* dst = Acc + 2 * ((size_t)gy * Wd + gx);
+    if (lo.x != 0.f || lo.y != 0.f || lo.z != 0.f || lo.w != 0.f) atomicAdd(dst, lo);
+    if (hi.x != 0.f || hi.y != 0.f || hi.z != 0.f || hi.w != 0.f) atomicAdd(dst + 1, hi);
+  }
+}
+
+template <int W>
+static constexpr size_t grid_smem() {
+  return (size_t)((kGridTile + W - 1) * (kGridTile + W - 1) * 8 + 8 * kGridItem + 2 * W * kGridItem) * sizeof(float);
+}
+
+// Hermitian symmetrisation + inverse column FFTs for the column pair (kx, -kx).
+// H1(k) = P1(k) + i Q1(k), P1(k) = aI(k) + conj aI(-k), Q1(k) = aQ(k) + conj aQ(-k);
+// H2 likewise from aU, aV. H(-k) = conj P(k) + i conj Q(k).
+__global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* __restrict__ tw, int K,
+                           int logK, float4* __restrict__ T2, int Wd, int off, int full) {
+  extern __shared__ float4 sm[];
+  float4* bp = sm;
+  float4* bm = sm + K;
+  float2* stw = reinterpret_cast<float2*>(sm + 2 * K);
+  const int kx = blockIdx.x;
+  const int self = (kx == 0) || (full && kx == K / 2);
+  const int gxp = gidx(kx, off, full, K), gxm = gidx(-kx, off, full, K);
+  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
+  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) sm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
+    const int ky = full ? (gy <= K / 2 ? gy : gy - K) : gy - off;
+    const int gym = gidx(-ky, off, full, K);
+    const float4 a0 = Acc[2 * ((size_t)gy * Wd + gxp)], a1 = Acc[2 * ((size_t)gy * Wd + gxp) + 1];
+    const float4 b0 = Acc[2 * ((size_t)gym * Wd + gxm)], b1 = Acc[2 * ((size_t)gym * Wd + gxm) + 1];
+    const float P1r = a0.x + b0.x, P1i = a0.y - b0.y, Q1r = a0.z + b0.z, Q1i = a0.w - b0.w;
+    const float P2r = a1.x + b1.x, P2i = a1.y - b1.y, Q2r = a1.z + b1.z, Q2i = a1.w - b1.w;
+    const float4 hp = make_float4(P1r - Q1i, P1i + Q1r, P2r - Q2i, P2i + Q2r);
+    bp[bitrev((ky + K) & (K - 1), logK)] = hp;
+    if (!self) {
+      const float4 hm = make_float4(P1r + Q1i, -P1i + Q1r, P2r + Q2i, -P2i + Q2r);
+      bm[bitrev((-ky + K) & (K - 1), logK)] = hm;
+    }
+  }
+  __syncthreads();
+  fft_smem<true>(bp, stw, K, logK);
+  if (!self) fft_smem<true>(bm, stw, K, logK);
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int idx = (p - n / 2 + K) & (K - 1);
+    T2[(size_t)p * Wd + gxp] = bp[idx];
+    if (!self) T2[(size_t)p * Wd + gxm] = bm[idx];
+  }
+}
+
+__global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const float* __restrict__ corr,
+                           const float2* __restrict__ tw, int K, int logK, int Wd, int off, int full,
+                           float* __restrict__ out) {
+  extern __shared__ float4 sm[];
+  float4* buf = sm;
+  float2* stw = reinterpret_cast<float2*>(sm + K);
+  const int p = blockIdx.x;
+  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
+    const int k = full ? gx : gx - off;
+    buf[bitrev((k + K) & (K - 1), logK)] = T2[(size_t)p * Wd + gx];
+  }
+  __syncthreads();
+  fft_smem<true>(buf, stw, K, logK);
+  const float cy = 0.5f * corr[p];
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const float4 v = buf[(q - n / 2 + K) & (K - 1)];
+    const float c = cy * corr[q];
+    const size_t o = (size_t)p * n + q;
+    out[o] = v.x * c;
+    out[(size_t)N + o] = v.y * c;
+    out[2 * (size_t)N + o] = v.z * c;
+    out[3 * (size_t)N + o] = v.w * c;
+  }
+}
+
+static size_t fft_smem_bytes(int K, int nbuf) { return (size_t)nbuf * K * sizeof(float4) + (K / 2) * sizeof(float2); }
+
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t configure_nufft_kernels() {
+  // Largest grid: n = 2048, K = 4096.
+  const size_t sm1 = fft_smem_bytes(4096, 1), sm2 = fft_smem_bytes(4096, 2);
+  cudaError_t e;
+  if ((e = set_smem((const void*)k_fwd_rows, sm1)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fwd_cols, sm1)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_adj_rows, sm1)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<5>, grid_smem<5>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<7>, grid_smem<7>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<9>, grid_smem<9>())) != cudaSuccess) return e;
+  return set_smem((const void*)k_adj_cols, sm2);
+}
+
+cudaError_t nufft_forward_grid(Handle* h, const float* X) {
+  const GridGeom& g = h->g;
+  const size_t sm1 = fft_smem_bytes(g.K, 1);
+  k_fwd_rows<<<h->n, 256, sm1, h->stream>>>(X, h->n, h->N, h->corr, h->tw, g.K, g.logK, h->T1, g.Wd, g.off, g.full);
+  k_fwd_cols<<<g.Wd, 256, sm1, h->stream>>>(h->T1, h->n, h->tw, g.K, g.logK, h->G, g.Wd, g.off, g.full);
+  return cudaGetLastError();
+}
+
+template <int W>
+static void launch_degrid(Handle* h, int mode, float2* out) {
+  const GridGeom& g = h->g;
+  k_degrid<W><<<h->nchunks, 256, 0, h->stream>>>(h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode, h->R, h->Y,
+                                                   h->cb, (float)(1.0 / h->rho2), h->chunk_start, h->chunk_block,
+                                                   h->chunk_part, out);
+}
+
+cudaError_t nufft_degrid(Handle* h, int mode, float2* out) {
+  if (h->nchunks == 0) return cudaSuccess;
+  switch (h->g.W) {
+    case 5: launch_degrid<5>(h, mode, out); break;
+    case 9: launch_degrid<9>(h, mode, out); break;
+    default: launch_degrid<7>(h, mode, out); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t block_scales(Handle* h) {
+  if (h->nblocks == 0) return cudaSuccess;
+  k_block_scale<<<(h->nblocks + 127) / 128, 128, 0, h->stream>>>(h->chunk_part, h->block_chunk, h->eps, h->nblocks,
+                                                                 h->rho2, h->cfg.literal_ball, h->cb);
+  return cudaGetLastError();
+}
+
+template <int W>
+static void launch_grid(Handle* h, const float2* in, int use_scale) {
+  const GridGeom& g = h->g;
+  k_grid<W><<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->gperm, h->gblk, h->rec, in, h->cb,
+                                                            use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
+}
+
+cudaError_t nufft_grid(Handle* h, const float2* in, int use_scale) {
+  const GridGeom& g = h->g;
+  cudaError_t e = cudaMemsetAsync(h->Acc, 0, (size_t)g.Wd * g.Wd * 2 * sizeof(float4), h->stream);
+  if (e != cudaSuccess || h->nitems == 0) return e;
+  switch (g.W) {
+    case 5: launch_grid<5>(h, in, use_scale); break;
+    case 9: launch_grid<9>(h, in, use_scale); break;
+    default: launch_grid<7>(h, in, use_scale); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t nufft_adjoint_image(Handle* h, float* out) {
+  const GridGeom& g = h->g;
+  const size_t sm2 = fft_smem_bytes(g.K, 2), sm1 = fft_smem_bytes(g.K, 1);
+  const int ncols = g.full ? (g.K / 2 + 1) : (g.R + 1);
+  k_adj_cols<<<ncols, 256, sm2, h->stream>>>(h->Acc, h->n, h->tw, g.K, g.logK, h->T2, g.Wd, g.off, g.full);
+  k_adj_rows<<<h->n, 256, sm1, h->stream>>>(h->T2, h->n, h->N, h->corr, h->tw, g.K, g.logK, g.Wd, g.off, g.full, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ps

@@ -1,0 +1,355 @@
+// Per-pixel steps of Algorithm 1 and the reductions of the stopping rules.
+//
+// k_primal fuses, per pixel, Algorithm 1 steps 3-4 (primal S and Z with P_U or
+// P_U' and P_V), the extrapolations 2 S^(k+1) - S^(k), 2 Z^(k+1) - Z^(k), steps
+// 9-12 (epigraph duals C, D through P_E1 and P_E2, Eqs. proj_e1 and
+// proj_e2_def) and the Dirac part of steps 5-6 (A_dirac = clamp(A + rho1 Xb/3,
+// +-gamma W)). It also writes per-CTA FP64 partials of ||S^(k+1) - S^(k)||^2 and
+// ||S^(k)||^2 per map for the relative-change rule (Eq. stop_crit).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace ps {
+
+constexpr int kSweepThreads = 256;
+constexpr int kSweepPix = 4;   // pixels per thread
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// P_E1 of Eq. proj_e1 on (c, d).
+__device__ __forceinline__ void proj_e1(float c, float d, float& pc, float& pd) {
+  if (c + d >= 0.f) {
+    pc = c;
+    pd = d;
+  } else {
+    pc = 0.5f * (c - d);
+    pd = 0.5f * (d - c);
+  }
+}
+
+// P_E2 of Eq. proj_e2_def on (r1, r2, r3, d).
+__device__ __forceinline__ void proj_e2(float r1, float r2, float r3, float d, float& p1, float& p2, float& p3,
+                                        float& pd) {
+  const float nr = sqrtf(r1 * r1 + r2 * r2 + r3 * r3);
+  if (nr < -d || (nr == 0.f && d <= 0.f)) {
+    p1 = p2 = p3 = pd = 0.f;
+  } else if (nr < d) {
+    p1 = r1;
+    p2 = r2;
+    p3 = r3;
+    pd = d;
+  } else {
+    const float a = 0.5f * (1.0f + d / nr);
+    p1 = a * r1;
+    p2 = a * r2;
+    p3 = a * r3;
+    pd = a * nr;
+  }
+}
+
+__global__ void __launch_bounds__(kSweepThreads) k_primal(
+    int N, int mode, float tau, float rho1, float rho3, float* __restrict__ S, float* __restrict__ Z,
+    float* __restrict__ C, float* __restrict__ D, const float* __restrict__ PsiA, const float* __restrict__ Adj,
+    float* __restrict__ Xb, float* __restrict__ A, const float* __restrict__ T, size_t cstride,
+    double* __restrict__ part) {
+  __shared__ double sh[kSweepThreads / 32][8];
+  float dss[4] = {0.f, 0.f, 0.f, 0.f}, ss[4] = {0.f, 0.f, 0.f, 0.f};
+  const int base = blockIdx.x * (kSweepThreads * kSweepPix) + threadIdx.x;
+  const float inv_r3 = 1.0f / rho3;
+  const float r1_3 = rho1 * (1.0f / 3.0f);
+#pragma unroll
+  for (int t = 0; t < kSweepPix; ++t) {
+    const int i = base + t * kSweepThreads;
+    if (i >= N) break;
+    float xb[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const size_t o = (size_t)c * N + i;
+      float grad = Adj[o];
+      if (mode != PS_NNLS) grad += PsiA[o];
+      if (mode == PS_POLARIZED) grad += C[o];
+      const float so = S[o];
+      float sn = so - tau * grad;                       // step 3 (P_U: real already)
+      if (mode != PS_POLARIZED && c == 0) sn = fmaxf(sn, 0.f);   // P_U'
+      xb[c] = 2.f * sn - so;
+      dss[c] += (sn - so) * (sn - so);
+      ss[c] += so * so;
+      S[o] = sn;
+      Xb[o] = xb[c];
+      if (mode != PS_NNLS) {                            // Dirac part of steps 5-6
+        const size_t ao = (size_t)c * cstride + i;
+        const float t = T[ao];
+        A[ao] = fminf(fmaxf(fmaf(r1_3, xb[c], A[ao]), -t), t);
+      }
+    }
+    if (mode == PS_POLARIZED) {
+      // Step 4: Z = P_V(Z - tau D).
+      const float z1o = Z[i], z2o = Z[(size_t)N + i];
+      float z1 = z1o - tau * D[i], z2 = z2o - tau * D[(size_t)N + i];
+      if (z1 + z2 > 0.f) {
+        const float a = 0.5f * (z1 - z2);
+        z2 = 0.5f * (z2 - z1);
+        z1 = a;
+      }
+      Z[i] = z1;
+      Z[(size_t)N + i] = z2;
+      const float zb1 = 2.f * z1 - z1o, zb2 = 2.f * z2 - z2o;
+      // Steps 9-12.
+      float ct[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ct[c] = C[(size_t)c * N + i] + rho3 * xb[c];
+      const float dt1 = D[i] + rho3 * zb1, dt2 = D[(size_t)N + i] + rho3 * zb2;
+      float pc, pd;
+      proj_e1(ct[0] * inv_r3, dt1 * inv_r3, pc, pd);
+      C[i] = ct[0] - rho3 * pc;
+      D[i] = dt1 - rho3 * pd;
+      float p1, p2, p3, pd2;
+      proj_e2(ct[1] * inv_r3, ct[2] * inv_r3, ct[3] * inv_r3, dt2 * inv_r3, p1, p2, p3, pd2);
+      C[(size_t)N + i] = ct[1] - rho3 * p1;
+      C[2 * (size_t)N + i] = ct[2] - rho3 * p2;
+      C[3 * (size_t)N + i] = ct[3] - rho3 * p3;
+      D[(size_t)N + i] = dt2 - rho3 * pd2;
+    }
+  }
+  // FP64 partials for the relative-change statistic.
+  double v[8];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    v[c] = warp_sum((double)dss[c]);
+    v[4 + c] = warp_sum((double)ss[c]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sh[wid][c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double s = 0.0;
+    for (int w = 0; w < kSweepThreads / 32; ++w) s += sh[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 8 + threadIdx.x] = s;
+  }
+}
+
+int sweep_blocks(int N) { return (N + kSweepThreads * kSweepPix - 1) / (kSweepThreads * kSweepPix); }
+
+cudaError_t primal_sweep(Handle* h) {
+  const int nb = sweep_blocks(h->N);
+  k_primal<<<nb, kSweepThreads, 0, h->stream>>>(h->N, h->mode, (float)h->tau, (float)h->rho1, (float)h->rho3, h->S,
+                                                h->Z, h->C, h->D, h->PsiA, h->Adj, h->Xb, h->A, h->T,
+                                                (size_t)kBases * h->N, h->red);
+  return cudaGetLastError();
+}
+
+// Dirac part of Psi^dagger for the APPLY and REWEIGHT modes.
+__global__ void k_dirac(int N, const float* __restrict__ X, float* __restrict__ coef, float* __restrict__ thr,
+                        size_t cstride, int mode, float scale, float gamma, float delta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= N) return;
+  const float v = X[(size_t)c * N + i];
+  const size_t o = (size_t)c * cstride + i;
+  if (mode == SARA_APPLY) coef[o] = scale * v;
+  else thr[o] = gamma * delta / (delta + fabsf(scale * v));
+}
+
+cudaError_t dirac_apply(Handle* h, const float* X, float* coef, float* thr, int mode, float scale, float gamma,
+                        float delta) {
+  dim3 grid((h->N + 255) / 256, 4);
+  k_dirac<<<grid, 256, 0, h->stream>>>(h->N, X, coef, thr, (size_t)kBases * h->N, mode, scale, gamma, delta);
+  return cudaGetLastError();
+}
+
+// Deterministic two-stage FP64 reductions: per-CTA partials then one CTA.
+__global__ void k_dot_partial(const float* __restrict__ a, const float* __restrict__ b, size_t len,
+                              double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int np, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+static constexpr int kRedBlocks = 256;
+
+cudaError_t reduce_dot(Handle* h, const float* a, const float* b, size_t len, double* dev_out) {
+  double* part = h->red + (size_t)h->red_cap - 2 * kRedBlocks;
+  k_dot_partial<<<kRedBlocks, 256, 0, h->stream>>>(a, b, len, part);
+  k_sum_partials<<<1, 256, 0, h->stream>>>(part, kRedBlocks, dev_out);
+  return cudaGetLastError();
+}
+
+__global__ void k_violations(int N, const float* __restrict__ S, double zeta, double* __restrict__ part) {
+  __shared__ double sh[2][32];
+  double c0 = 0.0, c1 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double I = S[i], Q = S[(size_t)N + i], U = S[2 * (size_t)N + i], V = S[3 * (size_t)N + i];
+    const double p = -I + sqrt(Q * Q + U * U + V * V);
+    c0 += (p > zeta) ? 1.0 : 0.0;
+    c1 += (p > 0.0) ? 1.0 : 0.0;
+  }
+  c0 = warp_sum(c0);
+  c1 = warp_sum(c1);
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = c0;
+    sh[1][threadIdx.x >> 5] = c1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+    part[2 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_pairs(const double* __restrict__ part, int np, double* __restrict__ out) {
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += part[2 * i + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+cudaError_t violation_count(Handle* h, const float* S, double zeta, double* dev_out) {
+  double* part = h->red + (size_t)h->red_cap - 2 * kRedBlocks;
+  k_violations<<<kRedBlocks / 2, 256, 0, h->stream>>>(h->N, S, zeta, part);
+  k_sum_pairs<<<1, 32, 0, h->stream>>>(part, kRedBlocks / 2, dev_out);
+  return cudaGetLastError();
+}
+
+__global__ void k_wl1_partial(const float* __restrict__ c, const float* __restrict__ t, size_t len,
+                              double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    s += (double)t[i] * fabs((double)c[i]);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+    part[blockIdx.x] = r;
+  }
+}
+
+cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* dev_out) {
+  double* part = h->red + (size_t)h->red_cap - 2 * kRedBlocks;
+  k_wl1_partial<<<kRedBlocks, 256, 0, h->stream>>>(coef, thr, (size_t)36 * h->N, part);
+  k_sum_partials<<<1, 256, 0, h->stream>>>(part, kRedBlocks, dev_out);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_copy(const float* __restrict__ x, float* __restrict__ y, size_t len, double s) {
+  const float sf = (float)s;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * sf;
+}
+
+cudaError_t scale_copy(Handle* h, const float* x, float* y, size_t len, double s) {
+  k_scale_copy<<<1024, 256, 0, h->stream>>>(x, y, len, s);
+  return cudaGetLastError();
+}
+
+// Visibility order changes: sorted row m holds caller row perm[m].
+__global__ void k_gather_vis(int M, const int32_t* __restrict__ perm, const float4* __restrict__ user,
+                             float4* __restrict__ sorted) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const size_t u = (size_t)perm[m];
+  sorted[2 * (size_t)m] = user[2 * u];
+  sorted[2 * (size_t)m + 1] = user[2 * u + 1];
+}
+
+__global__ void k_scatter_vis(int M, const int32_t* __restrict__ perm, const float4* __restrict__ sorted,
+                              float4* __restrict__ user) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const size_t u = (size_t)perm[m];
+  user[2 * u] = sorted[2 * (size_t)m];
+  user[2 * u + 1] = sorted[2 * (size_t)m + 1];
+}
+
+cudaError_t gather_vis(Handle* h, const float2* user, float2* sorted) {
+  if (h->M == 0) return cudaSuccess;
+  k_gather_vis<<<(h->M + 255) / 256, 256, 0, h->stream>>>(h->M, h->perm, reinterpret_cast<const float4*>(user),
+                                                          reinterpret_cast<float4*>(sorted));
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_vis(Handle* h, const float2* sorted, float2* user) {
+  if (h->M == 0) return cudaSuccess;
+  k_scatter_vis<<<(h->M + 255) / 256, 256, 0, h->stream>>>(h->M, h->perm, reinterpret_cast<const float4*>(sorted),
+                                                           reinterpret_cast<float4*>(user));
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_vis(const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ chunk_block,
+                            const float* __restrict__ cb, float4* __restrict__ v) {
+  const int ch = blockIdx.x;
+  const float s = cb[chunk_block[ch]];
+  for (int m = chunk_start[ch] + threadIdx.x; m < chunk_start[ch + 1]; m += blockDim.x) {
+    float4 a = v[2 * (size_t)m], b = v[2 * (size_t)m + 1];
+    v[2 * (size_t)m] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+    v[2 * (size_t)m + 1] = make_float4(b.x * s, b.y * s, b.z * s, b.w * s);
+  }
+}
+
+cudaError_t scale_vis(Handle* h, float2* v) {
+  if (h->nchunks == 0) return cudaSuccess;
+  k_scale_vis<<<h->nchunks, 256, 0, h->stream>>>(h->chunk_start, h->chunk_block, h->cb, reinterpret_cast<float4*>(v));
+  return cudaGetLastError();
+}
+
+__global__ void k_vis_norms(const int32_t* __restrict__ chunk_start, const float4* __restrict__ v,
+                            double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int ch = blockIdx.x;
+  double s = 0.0;
+  for (int m = chunk_start[ch] + threadIdx.x; m < chunk_start[ch + 1]; m += blockDim.x) {
+    const float4 a = v[2 * (size_t)m], b = v[2 * (size_t)m + 1];
+    s += (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w + b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+    part[ch] = r;
+  }
+}
+
+cudaError_t vis_norms(Handle* h, const float2* v, double* dev_out) {
+  if (h->nchunks == 0) return cudaSuccess;
+  k_vis_norms<<<h->nchunks, 256, 0, h->stream>>>(h->chunk_start, reinterpret_cast<const float4*>(v), dev_out);
+  return cudaGetLastError();
+}
+
+}  // namespace ps

@@ -1,0 +1,158 @@
+"""Host driver of Algorithm 2 (reweighting, Section 4.3.4) over the CUDA library.
+
+Every step of the primal-dual iteration runs in libpolsara.so; this module only
+sequences the C ABI calls: NNLS start, reweights with a decreasing delta, and the
+stopping rules of Section 5.5.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import binding as B
+
+
+@dataclasses.dataclass
+class Schedule:
+    """Fixed budget: `iterations` split over `reweights + 1` cycles, the first in NNLS mode.
+
+    delta^(1) = delta_factor * max |Psi^dagger S_nnls|, multiplied by delta_decay after each
+    reweight (delta -> 0, Eq. weights).
+    """
+    iterations: int
+    reweights: int
+    gamma: float
+    delta_factor: float = 0.1
+    delta_decay: float = 0.5
+
+
+class PolarizedSARA:
+    """One imaging problem resident on the GPU (a ps_handle)."""
+
+    def __init__(self, n: int, levels: int, mode: int = B.PS_POLARIZED, kernel_width: int = 7,
+                 literal_ball: bool = False, tau: float = 0.0, rho1: float = 0.0, rho2: float = 0.0,
+                 rho3: float = 0.0, stream=None):
+        cfg = B.ps_config(n=n, levels=levels, mode=mode, literal_ball=int(literal_ball),
+                          kernel_width=kernel_width, reserved=0, tau=tau, rho1=rho1, rho2=rho2, rho3=rho3)
+        self.n, self.levels = n, levels
+        self.h = B.ps_create(cfg, stream)
+        self.nblocks = 0
+        self.M = 0
+
+    def close(self) -> None:
+        if self.h is not None:
+            B.ps_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # Thin forwards to the C ABI.
+    def set_measurements(self, uv, vis, weights, block_offsets, eps) -> None:
+        B.ps_set_measurements(self.h, uv, vis, weights, block_offsets, eps)
+        self.nblocks = len(eps)
+        self.M = int(uv.shape[0])
+
+    def set_sara_weights(self, W, gamma: float) -> None:
+        B.ps_set_sara_weights(self.h, W, gamma)
+
+    def get_sara_weights(self) -> np.ndarray:
+        out = np.empty((4, 9, self.n, self.n), np.float32)
+        B.ps_get_sara_weights(self.h, out)
+        return out
+
+    def pd_iterate(self, n_iter: int) -> None:
+        B.ps_pd_iterate(self.h, n_iter)
+
+    def reweight(self, delta: float) -> None:
+        B.ps_reweight(self.h, delta)
+
+    def set_mode(self, mode: int) -> None:
+        B.ps_set_mode(self.h, mode)
+
+    def get_stokes(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((4, self.n, self.n), dtype=np.float32)
+        B.ps_get_stokes(self.h, out)
+        return out
+
+    def get_state(self) -> dict:
+        n, M = self.n, self.M
+        st = {"S": np.empty((4, n, n), np.float32), "Z": np.empty((2, n, n), np.float32),
+              "A": np.empty((4, 9, n, n), np.float32), "B": np.empty((M, 4), np.complex64),
+              "C": np.empty((4, n, n), np.float32), "D": np.empty((2, n, n), np.float32)}
+        B.ps_get_state(self.h, st)
+        return st
+
+    def set_state(self, st: dict) -> None:
+        B.ps_set_state(self.h, st)
+
+    def params(self) -> dict:
+        return B.ps_get_params(self.h)
+
+    def stats(self, zeta_sigma: float = 3.0) -> dict:
+        return B.ps_compute_stats(self.h, zeta_sigma, self.nblocks)
+
+    def synchronize(self) -> None:
+        B.ps_synchronize(self.h)
+
+    def psi_adjoint(self, S) -> np.ndarray:
+        out = np.empty((4, 9, self.n, self.n), np.float32)
+        B.ps_apply_psi_adjoint(self.h, S, out)
+        return out
+
+    # Algorithm 2.
+    def solve(self, sch: Schedule, W0=None) -> np.ndarray:
+        """NNLS start, then `reweights` cycles of Algorithm 1 each preceded by a reweight."""
+        per = sch.iterations // (sch.reweights + 1)
+        self.set_mode(B.PS_NNLS)
+        self.pd_iterate(per)
+        S = self.get_stokes()
+        delta = sch.delta_factor * float(np.max(np.abs(self.psi_adjoint(S))))
+        self.set_sara_weights(W0, sch.gamma)
+        self.set_mode(B.PS_POLARIZED)
+        for _ in range(sch.reweights):
+            self.reweight(delta)
+            self.pd_iterate(per)
+            delta *= sch.delta_decay
+        return self.get_stokes()
+
+    def solve_until(self, gamma: float, rel_tol: float = 1e-4, max_iter: int = 2000, reweights: int = 5,
+                    check_every: int = 20, delta_factor: float = 0.1, delta_decay: float = 0.5) -> dict:
+        """Stop each cycle when max_i rel-change <= rel_tol (Eq. stop_crit) or at the iteration cap."""
+        used = 0
+        per_cap = max(check_every, max_iter // (reweights + 1))
+
+        def cycle():
+            nonlocal used
+            k = 0
+            while k < per_cap and used < max_iter:
+                step = min(check_every, per_cap - k, max_iter - used)
+                self.pd_iterate(step)
+                k += step
+                used += step
+                if float(np.max(self.stats()["rel_change"][:3])) <= rel_tol:
+                    break
+        self.set_mode(B.PS_NNLS)
+        cycle()
+        S = self.get_stokes()
+        delta = delta_factor * float(np.max(np.abs(self.psi_adjoint(S))))
+        self.set_sara_weights(None, gamma)
+        self.set_mode(B.PS_POLARIZED)
+        for _ in range(reweights):
+            if used >= max_iter:
+                break
+            self.reweight(delta)
+            cycle()
+            delta *= delta_decay
+        return {"iterations": used, "S": self.get_stokes()}

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: per-operator relative l2 error <= 1e-5 (FP32 arithmetic plus the
+NUFFT interpolation error of the W=7, 2x-oversampled kernel, ~1e-6). After k
+iterations of Algorithm 1 from a random state every array is within 2e-5 * k:
+each iteration composes operators that are each within 1e-5, and the
+nonexpansive proximal steps do not amplify the difference. Full solves are
+within 1e-3 relative l2 per Stokes map with the same constraint-violation count.
+"""
+import numpy as np
+import pytest
+
+from oracle import measurement as meas
+from oracle import primal_dual as opd
+from oracle import wavelets as wav
+from paper_1801_02417_gb300 import binding as B
+from paper_1801_02417_gb300 import inputs
+from paper_1801_02417_gb300.solver import PolarizedSARA, Schedule
+from problems import make_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1801_02417_gb300 import _build
+    _build.build_library()
+    B.lib()
+
+
+def _solver(pb, n, levels, mode=B.PS_POLARIZED, steps=None, **kw):
+    steps = steps or {}
+    s = PolarizedSARA(n, levels, mode=mode, **steps, **kw)
+    s.set_measurements(pb["uv"], pb["Y"], pb["w"], pb["off"], pb["eps"])
+    return s
+
+
+@pytest.mark.parametrize("coverage,n,M", [("tracks", 32, 777), ("random", 32, 1001), ("tracks", 64, 2000),
+                                          ("random", 16, 257)])
+def test_phi_and_adjoint_match_direct_dft(coverage, n, M):
+    pb = make_problem(n, M, 2, 3, seed=5, coverage=coverage)
+    rng = np.random.default_rng(3)
+    S = rng.normal(size=(4, n, n)).astype(np.float32)
+    Yr = (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))).astype(np.complex64)
+    with _solver(pb, n, 2) as s:
+        Yg = np.empty((M, 4), np.complex64)
+        B.ps_apply_phi(s.h, S, Yg)
+        Sg = np.empty((4, n, n), np.float32)
+        B.ps_apply_phi_adjoint(s.h, Yr, Sg)
+    w = pb["w"].astype(np.float64)
+    assert rel_err(Yg, meas.phi(S.astype(np.float64), pb["uv"], w)) <= OP_TOL
+    assert rel_err(Sg, meas.phi_adjoint(Yr.astype(np.complex128), pb["uv"], w, n)) <= OP_TOL
+    # FP32 adjointness of the GPU pair itself.
+    lhs = np.sum(np.real(np.conj(Yg.astype(np.complex128)) * Yr))
+    rhs = np.sum(S.astype(np.float64) * Sg)
+    assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(Yg) ** 2) * np.sum(np.abs(Yr) ** 2))
+
+
+@pytest.mark.parametrize("n,levels", [(64, 4), (32, 3), (16, 4), (128, 2)])
+def test_psi_and_adjoint_match_oracle(n, levels):
+    pb = make_problem(n, 64, levels, 1, seed=2)
+    rng = np.random.default_rng(4)
+    S = rng.normal(size=(4, n, n)).astype(np.float32)
+    A = rng.normal(size=(4, 9, n, n)).astype(np.float32)
+    with _solver(pb, n, levels) as s:
+        Ag = np.empty((4, 9, n, n), np.float32)
+        B.ps_apply_psi_adjoint(s.h, S, Ag)
+        Sg = np.empty((4, n, n), np.float32)
+        B.ps_apply_psi(s.h, A, Sg)
+    assert rel_err(Ag, wav.psi_adjoint(S.astype(np.float64), levels)) <= 1e-6
+    assert rel_err(Sg, wav.psi(A.astype(np.float64), levels)) <= 1e-6
+
+
+def test_operator_norm_power_iteration():
+    pb = make_problem(32, 900, 2, 2, seed=8)
+    with _solver(pb, 32, 2) as s:
+        par = s.params()
+    ref = meas.op_norm_sq_lanczos(pb["uv"], pb["w"].astype(np.float64), 32)
+    assert abs(par["opnorm_sq"] - ref) <= 1e-4 * ref
+    assert abs(par["rho2"] * par["opnorm_sq"] - 1.0) < 1e-12
+    assert abs(par["tau"] - 0.99 / 3.0) < 1e-12
+
+
+def _random_state(n, M, seed, scale=1.0):
+    st = inputs.random_state(n, M, seed, scale)
+    return {k: (v.astype(np.complex64) if k == "B" else v.astype(np.float32)) for k, v in st.items()}
+
+
+@pytest.mark.parametrize("mode", [B.PS_POLARIZED, B.PS_NO_CONSTRAINT, B.PS_NNLS])
+@pytest.mark.parametrize("n,M,levels,nblocks,coverage", [(32, 1500, 3, 4, "tracks"), (16, 333, 2, 1, "random")])
+def test_iterations_from_random_state_match_oracle(mode, n, M, levels, nblocks, coverage):
+    pb = make_problem(n, M, levels, nblocks, seed=11, coverage=coverage)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, n)
+    p = opd.step_sizes(on, mode)
+    st32 = _random_state(n, M, 21, scale=0.05)
+    rng = np.random.default_rng(5)
+    W = rng.uniform(0.2, 1.0, size=(4, 9, n, n)).astype(np.float32)
+    gamma = 0.02
+    T = gamma * W.astype(np.float64)
+    ref = {k: v.astype(np.complex128 if k == "B" else np.float64) for k, v in st32.items()}
+    if mode != B.PS_POLARIZED:
+        for k in ("Z", "C", "D"):
+            st32[k][:] = 0
+            ref[k][:] = 0
+    if mode == B.PS_NNLS:
+        st32["A"][:] = 0
+        ref["A"][:] = 0
+    steps = dict(tau=p.tau, rho1=p.rho1, rho2=p.rho2, rho3=p.rho3)
+    with _solver(pb, n, levels, mode=mode, steps=steps) as s:
+        s.set_sara_weights(W, gamma)
+        s.set_state(st32)
+        done = 0
+        for k_iter in (1, 3):
+            s.pd_iterate(k_iter)
+            for _ in range(k_iter):
+                ref = opd.pd_iteration(ref, prob, T, p, mode)
+            done += k_iter
+            got = s.get_state()
+            for k in ("S", "A", "B") + (("Z", "C", "D") if mode == B.PS_POLARIZED else ()):
+                err = rel_err(got[k], ref[k])
+                assert err <= 2e-5 * done, (done, k, err)
+
+
+def test_reweight_matches_eq_weights():
+    n, levels = 32, 3
+    pb = make_problem(n, 500, levels, 1, seed=3)
+    rng = np.random.default_rng(6)
+    st = {"S": rng.normal(size=(4, n, n)).astype(np.float32)}
+    gamma, delta = 0.3, 0.05
+    with _solver(pb, n, levels) as s:
+        s.set_sara_weights(None, gamma)
+        s.set_state(st)
+        s.reweight(delta)
+        T = s.get_sara_weights()
+    ref = gamma * opd.reweight(st["S"].astype(np.float64), levels, delta)
+    assert rel_err(T, ref) <= 1e-6
+
+
+def test_stats_match_oracle():
+    n, levels = 32, 2
+    pb = make_problem(n, 1200, levels, 3, seed=4)
+    prob = pb["prob"]
+    rng = np.random.default_rng(9)
+    S = (pb["truth"] + 0.05 * rng.normal(size=(4, n, n))).astype(np.float32)
+    with _solver(pb, n, levels) as s:
+        s.set_state({"S": S})
+        st = s.stats(zeta_sigma=3.0)
+    S64 = S.astype(np.float64)
+    res = opd.residual_norms(S64, prob)
+    assert np.allclose(st["block_residual"], res, rtol=1e-5)
+    zeta = opd.zeta_threshold(S64, prob, 3.0)
+    assert abs(st["zeta"] - zeta) <= 1e-4 * zeta
+    # Counts compared at the GPU's zeta (the decision is taken on the same threshold).
+    assert st["violations"] == opd.violation_count(S64, st["zeta"])
+    assert st["violations_raw"] == opd.violation_count(S64, 0.0)
+
+
+def test_state_roundtrip_and_block_order():
+    n, levels, M = 16, 2, 401
+    pb = make_problem(n, M, levels, 3, seed=7, coverage="random")
+    st = _random_state(n, M, 3)
+    with _solver(pb, n, levels) as s:
+        s.set_state(st)
+        got = s.get_state()
+    for k in "SZABCD":
+        assert np.array_equal(got[k], st[k]), k
+
+
+def test_error_paths():
+    with PolarizedSARA(32, 2) as s:
+        with pytest.raises(B.PolsaraError) as e:
+            s.pd_iterate(1)
+        assert e.value.status == B.PS_ESTATE
+        with pytest.raises(B.PolsaraError) as e:
+            B.ps_set_measurements(s.h, np.array([[4.0, 0.0]]), np.zeros((1, 4), np.complex64), None,
+                                  np.array([0, 1]), np.array([1.0]))
+        assert e.value.status == B.PS_EINVAL
+        with pytest.raises(B.PolsaraError) as e:
+            s.reweight(-1.0)
+        assert e.value.status == B.PS_EINVAL
+    # Empty measurement set: the iteration runs with no data term.
+    with PolarizedSARA(16, 2) as s:
+        s.set_measurements(np.zeros((0, 2)), np.zeros((0, 4), np.complex64), None, np.array([0]), np.array([]))
+        s.set_sara_weights(None, 0.1)
+        s.pd_iterate(3)
+        assert np.all(np.isfinite(s.get_stokes()))
+
+
+def test_full_solve_img64_matches_oracle():
+    """64x64, M=2000, 8 stations, 1 block, 4 levels, 300 iterations, 3 reweights (NNLS start)."""
+    wl = inputs.WORKLOADS["img64_m2k"]
+    pb = make_problem(wl.n, wl.M, wl.levels, wl.nblocks, seed=wl.seed, stations=wl.stations,
+                      weight_spread=0.0)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, wl.n)
+    gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, wl.n),
+                                                          wl.levels))))
+    ref = opd.solve(prob, wl.iterations, wl.reweights, gamma, on)
+    p = opd.step_sizes(on, opd.POLARIZED)
+    with _solver(pb, wl.n, wl.levels, steps=dict(rho2=p.rho2)) as s:
+        S = s.solve(Schedule(wl.iterations, wl.reweights, gamma))
+        st = s.stats()
+    for i in range(4):
+        assert rel_err(S[i], ref["S"][i]) <= 1e-3, (i, rel_err(S[i], ref["S"][i]))
+    assert st["violations"] == opd.violation_count(ref["S"], st["zeta"])

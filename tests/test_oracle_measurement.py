@@ -96,6 +96,7 @@ def test_operator_norm_closed_form_and_power_iteration():
     assert abs(lam_dense - 2 * lam) <= 1e-10 * lam_dense
     lam_pow = meas.op_norm_sq(uv, w, n, iters=5000, tol=1e-15)
     assert abs(lam_pow - 2 * lam) <= 1e-8 * lam_pow
+    assert abs(meas.op_norm_sq_lanczos(uv, w, n) - 2 * lam) <= 1e-9 * lam
 
 
 def test_chi2_epsilon_two_sigma_coverage():
