@@ -24,7 +24,8 @@
  *     rows [h,m) cols [h,m) x-high/y-high; the coarsest approximation fills the
  *     top-left (n >> levels)^2 block.
  *   - `device_ptrs` = 1: pointers are CUDA device pointers read/written on the
- *     handle's stream; 0: host pointers (the call then synchronises the stream).
+ *     handle's stream, and must be 16-byte aligned (else PS_EINVAL); 0: host
+ *     pointers (the call then synchronises the stream).
  *   - Ownership: inputs are copied; outputs go to caller-allocated buffers; the
  *     handle owns all its device state until ps_destroy.
  *   - Errors: every call returns a ps_status; ps_last_error() holds a message.

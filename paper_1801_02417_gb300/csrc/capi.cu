@@ -67,6 +67,13 @@ static void dfree(Handle* h, T*& p, size_t count) {
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Device arrays are read and written as float4: caller device pointers must be 16-byte aligned.
+static bool misaligned(const void* p, int device_ptrs) { return device_ptrs && p && ((uintptr_t)p & 15u) != 0; }
+#define CHECK_ALIGN(h, p, dp, what)                                                               \
+  do {                                                                                            \
+    if (misaligned((p), (dp))) return fail((h), PS_EINVAL, std::string(what) + ": device pointer not 16-byte aligned"); \
+  } while (0)
+
 static int sweep_blocks_host(int N) { return (N + 1023) / 1024; }
 
 static void free_vis(Handle* h) {
@@ -340,6 +347,9 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   if (!h) return PS_EINVAL;
   if (M64 < 0 || M64 > (int64_t)1 << 30) return fail(h, PS_EINVAL, "set_measurements: M out of range");
   const int M = (int)M64;
+  CHECK_ALIGN(h, uv, device_ptrs, "set_measurements");
+  CHECK_ALIGN(h, vis, device_ptrs, "set_measurements");
+  CHECK_ALIGN(h, weights, device_ptrs, "set_measurements");
   if (M > 0 && (!uv || !vis || !block_offsets || !eps || nblocks < 1 || nblocks > 2047))
     return fail(h, PS_EINVAL, "set_measurements: need uv, vis, block_offsets, eps and 1 <= nblocks <= 2047");
   if (M > 0) {
@@ -581,6 +591,7 @@ static ps_status power_iteration(Handle* h) {
 
 ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_t device_ptrs) {
   if (!h) return PS_EINVAL;
+  CHECK_ALIGN(h, W, device_ptrs, "set_sara_weights");
   if (!(gamma > 0) || !std::isfinite(gamma)) return fail(h, PS_EINVAL, "set_sara_weights: gamma must be > 0");
   const size_t len = 36 * (size_t)h->N;
   if (W) {
@@ -641,16 +652,21 @@ static ps_status copy_out(Handle* h, const void* dsrc, void* dst, size_t bytes, 
 
 ps_status ps_get_stokes(ps_handle* h, float* out, int32_t device_ptrs) {
   if (!h || !out) return h ? fail(h, PS_EINVAL, "get_stokes: null output") : PS_EINVAL;
+  CHECK_ALIGN(h, out, device_ptrs, "get_stokes");
   return copy_out(h, h->S, out, 4 * (size_t)h->N * sizeof(float), device_ptrs);
 }
 
 ps_status ps_get_sara_weights(ps_handle* h, float* out, int32_t device_ptrs) {
   if (!h || !out) return h ? fail(h, PS_EINVAL, "get_sara_weights: null output") : PS_EINVAL;
+  CHECK_ALIGN(h, out, device_ptrs, "get_sara_weights");
   return copy_out(h, h->T, out, 36 * (size_t)h->N * sizeof(float), device_ptrs);
 }
 
 ps_status ps_get_state(ps_handle* h, const ps_state_view* v) {
   if (!h || !v) return PS_EINVAL;
+  for (const void* p : {(const void*)v->S, (const void*)v->Z, (const void*)v->A, (const void*)v->B, (const void*)v->C,
+                        (const void*)v->D})
+    CHECK_ALIGN(h, p, v->device_ptrs, "get_state");
   const size_t N = h->N;
   const int dp = v->device_ptrs;
   ps_status st;
@@ -677,6 +693,9 @@ ps_status ps_get_state(ps_handle* h, const ps_state_view* v) {
 
 ps_status ps_set_state(ps_handle* h, const ps_state_view* v) {
   if (!h || !v) return PS_EINVAL;
+  for (const void* p : {(const void*)v->S, (const void*)v->Z, (const void*)v->A, (const void*)v->B, (const void*)v->C,
+                        (const void*)v->D})
+    CHECK_ALIGN(h, p, v->device_ptrs, "set_state");
   if (!h->have_meas) return fail(h, PS_ESTATE, "set_state: call ps_set_measurements first");
   const size_t N = h->N;
   const int dp = v->device_ptrs;
@@ -770,6 +789,8 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
 
 ps_status ps_apply_phi(ps_handle* h, const float* S, float* Y, int32_t device_ptrs) {
   if (!h || !S || !Y) return h ? fail(h, PS_EINVAL, "apply_phi: null pointer") : PS_EINVAL;
+  CHECK_ALIGN(h, S, device_ptrs, "apply_phi");
+  CHECK_ALIGN(h, Y, device_ptrs, "apply_phi");
   if (!h->have_meas) return fail(h, PS_ESTATE, "apply_phi: call ps_set_measurements first");
   if (h->M == 0) return PS_OK;
   const size_t N4 = 4 * (size_t)h->N, V = 4 * (size_t)h->M;
@@ -796,6 +817,8 @@ ps_status ps_apply_phi(ps_handle* h, const float* S, float* Y, int32_t device_pt
 
 ps_status ps_apply_phi_adjoint(ps_handle* h, const float* Yin, float* S, int32_t device_ptrs) {
   if (!h || !Yin || !S) return h ? fail(h, PS_EINVAL, "apply_phi_adjoint: null pointer") : PS_EINVAL;
+  CHECK_ALIGN(h, Yin, device_ptrs, "apply_phi_adjoint");
+  CHECK_ALIGN(h, S, device_ptrs, "apply_phi_adjoint");
   if (!h->have_meas) return fail(h, PS_ESTATE, "apply_phi_adjoint: call ps_set_measurements first");
   const size_t N4 = 4 * (size_t)h->N, V = 4 * (size_t)h->M;
   float* out = device_ptrs ? S : h->tmp4;
@@ -822,6 +845,8 @@ ps_status ps_apply_phi_adjoint(ps_handle* h, const float* Yin, float* S, int32_t
 
 ps_status ps_apply_psi_adjoint(ps_handle* h, const float* S, float* A, int32_t device_ptrs) {
   if (!h || !S || !A) return h ? fail(h, PS_EINVAL, "apply_psi_adjoint: null pointer") : PS_EINVAL;
+  CHECK_ALIGN(h, S, device_ptrs, "apply_psi_adjoint");
+  CHECK_ALIGN(h, A, device_ptrs, "apply_psi_adjoint");
   const size_t N4 = 4 * (size_t)h->N;
   const float* X = S;
   float* coef = A;
@@ -840,6 +865,8 @@ ps_status ps_apply_psi_adjoint(ps_handle* h, const float* S, float* A, int32_t d
 
 ps_status ps_apply_psi(ps_handle* h, const float* A, float* S, int32_t device_ptrs) {
   if (!h || !A || !S) return h ? fail(h, PS_EINVAL, "apply_psi: null pointer") : PS_EINVAL;
+  CHECK_ALIGN(h, A, device_ptrs, "apply_psi");
+  CHECK_ALIGN(h, S, device_ptrs, "apply_psi");
   const float* coef = A;
   float* out = S;
   if (!device_ptrs) {

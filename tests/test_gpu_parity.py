@@ -58,7 +58,7 @@ def test_phi_and_adjoint_match_direct_dft(coverage, n, M):
     assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(Yg) ** 2) * np.sum(np.abs(Yr) ** 2))
 
 
-@pytest.mark.parametrize("n,levels", [(64, 4), (32, 3), (16, 4), (128, 2)])
+@pytest.mark.parametrize("n,levels", [(64, 4), (32, 3), (16, 4), (128, 2), (256, 6)])
 def test_psi_and_adjoint_match_oracle(n, levels):
     pb = make_problem(n, 64, levels, 1, seed=2)
     rng = np.random.default_rng(4)
