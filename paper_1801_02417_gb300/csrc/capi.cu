@@ -85,14 +85,10 @@ static void free_vis(Handle* h) {
   dfree(h, h->perm, M);
   dfree(h, h->eps, (size_t)h->nblocks);
   dfree(h, h->cb, (size_t)h->nblocks);
-  dfree(h, h->chunk_start, (size_t)h->nchunks + 1);
-  dfree(h, h->chunk_block, (size_t)h->nchunks);
-  dfree(h, h->chunk_part, (size_t)h->nchunks);
-  dfree(h, h->block_chunk, (size_t)h->nblocks + 1);
+  dfree(h, h->block_sum, (size_t)h->nblocks);
   dfree(h, h->items, (size_t)h->nitems);
   dfree(h, h->gchunks, (size_t)h->ngchunks);
-  dfree(h, h->gperm, M);
-  dfree(h, h->gblk, M);
+  dfree(h, h->vblk, M);
   const size_t Wd = h->g.Wd;
   dfree(h, h->T1, (size_t)h->n * Wd);
   dfree(h, h->G, Wd * Wd);
@@ -100,7 +96,7 @@ static void free_vis(Handle* h) {
   dfree(h, h->T2, (size_t)h->n * Wd);
   dfree(h, h->tw, (size_t)h->g.K / 2);
   dfree(h, h->corr, (size_t)h->n);
-  h->M = h->nblocks = h->nchunks = h->nitems = h->ngchunks = 0;
+  h->M = h->nblocks = h->nitems = h->ngchunks = 0;
   h->g = ps::GridGeom{};
 }
 
@@ -133,6 +129,7 @@ static ps_status reset_state(Handle* h) {
   CK(h, cudaMemsetAsync(h->Adj, 0, 4 * N * sizeof(float), h->stream));
   CK(h, cudaMemsetAsync(h->Xb, 0, 4 * N * sizeof(float), h->stream));
   CK(h, cudaMemsetAsync(h->red, 0, (size_t)h->red_cap * sizeof(double), h->stream));
+  CK(h, cudaMemsetAsync(h->dev_flags, 0, 4 * sizeof(int), h->stream));
   if (h->M > 0) {
     CK(h, cudaMemsetAsync(h->R, 0, 4 * (size_t)h->M * sizeof(float2), h->stream));
     CK(h, cudaMemsetAsync(h->cb, 0, (size_t)h->nblocks * sizeof(float), h->stream));
@@ -275,6 +272,7 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
             dalloc(h, &h->Adj, 4 * N) == cudaSuccess && dalloc(h, &h->tmp4, 4 * N) == cudaSuccess &&
             dalloc(h, &h->A, 36 * N) == cudaSuccess && dalloc(h, &h->T, 36 * N) == cudaSuccess &&
             dalloc(h, &h->approx, 16 * N) == cudaSuccess && dalloc(h, &h->red, (size_t)h->red_cap) == cudaSuccess &&
+            dalloc(h, &h->dev_flags, 4) == cudaSuccess &&
             cudaMallocHost((void**)&h->red_host, 1024 * sizeof(double)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -314,16 +312,29 @@ void ps_destroy(ps_handle* h) {
   dfree(h, h->T, 36 * N);
   dfree(h, h->approx, 16 * N);
   dfree(h, h->red, (size_t)h->red_cap);
+  dfree(h, h->dev_flags, 4);
   if (h->red_host) cudaFreeHost(h->red_host);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+// Reads the device error flags after a synchronisation: a bounded in-kernel wait
+// that gave up is reported as PS_ETIMEOUT (the flag is then cleared).
+static ps_status check_flags(Handle* h) {
+  int f[4] = {0, 0, 0, 0};
+  CK(h, cudaMemcpy(f, h->dev_flags, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f[0]) {
+    CK(h, cudaMemset(h->dev_flags, 0, sizeof(f)));
+    return fail(h, PS_ETIMEOUT, "a bounded device wait (bulk-copy barrier) gave up; results of that launch are invalid");
+  }
+  return PS_OK;
 }
 
 ps_status ps_synchronize(ps_handle* h) {
   if (!h) return PS_EINVAL;
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaGetLastError());
-  return PS_OK;
+  return check_flags(h);
 }
 
 // Copy `bytes` from a caller pointer into device memory `dst` (or alias when on device).
@@ -415,7 +426,7 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   g.tilesX = (g.Wd + ps::kGridTile - 1) / ps::kGridTile;
   auto gi = [&](int k) { return g.full ? (k & (g.K - 1)) : k + g.off; };
 
-  // Sort rows by gridding tile within each block (blocks stay contiguous).
+  // Sort key of each row: gridding tile, then tap-centre cell.
   std::vector<int32_t> perm(M);
   std::iota(perm.begin(), perm.end(), 0);
   std::vector<int64_t> key(M);
@@ -424,38 +435,23 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
     const int64_t tile = (int64_t)(gy / ps::kGridTile) * g.tilesX + gx / ps::kGridTile;
     key[m] = (tile << 26) | ((int64_t)gy << 13) | gx;
   }
-  std::vector<int32_t> cstart, cblock, bchunk;
   if (M > 0) h->offsets_host.assign(block_offsets, block_offsets + nblocks + 1);
   else h->offsets_host.assign(1, 0);
-  std::vector<uint16_t> blk_of(M);
-  for (int b = 0; b < (M > 0 ? nblocks : 0); ++b) {
-    const int s = (int)block_offsets[b], e = (int)block_offsets[b + 1];
-    std::stable_sort(perm.begin() + s, perm.begin() + e, [&](int32_t a, int32_t c) { return key[a] < key[c]; });
-    bchunk.push_back((int32_t)cblock.size());
-    for (int c0 = s; c0 < e; c0 += ps::kChunk) {
-      cstart.push_back(c0);
-      cblock.push_back(b);
-    }
-    for (int i = s; i < e; ++i) blk_of[i] = (uint16_t)b;
-  }
-  if (M > 0) {
-    bchunk.push_back((int32_t)cblock.size());
-    cstart.push_back(M);
-  }
-  // Gridding order: every storage row sorted by tap-centre cell (tile-major).
-  std::vector<int32_t> gperm(M);
-  std::iota(gperm.begin(), gperm.end(), 0);
-  std::stable_sort(gperm.begin(), gperm.end(), [&](int32_t a, int32_t c) { return key[perm[a]] < key[perm[c]]; });
-  std::vector<uint16_t> gblk(M);
-  for (int j = 0; j < M; ++j) gblk[j] = blk_of[gperm[j]];
+  // Storage order: every row sorted by tap-centre cell (tile-major), blocks interleaved.
+  std::vector<uint16_t> blk_user(M);
+  for (int b = 0; b < (M > 0 ? nblocks : 0); ++b)
+    for (int64_t i = block_offsets[b]; i < block_offsets[b + 1]; ++i) blk_user[i] = (uint16_t)b;
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t c) { return key[a] < key[c]; });
+  std::vector<uint16_t> vblk(M);
+  for (int i = 0; i < M; ++i) vblk[i] = blk_user[perm[i]];
   std::vector<ps::GridItem> items;
   std::vector<int32_t> gchunks;
   {
     int j0 = 0;
     while (j0 < M) {
-      const int64_t tile = key[perm[gperm[j0]]] >> 26;
+      const int64_t tile = key[perm[j0]] >> 26;
       int j1 = j0;
-      while (j1 < M && j1 - j0 < ps::kGridItem && (key[perm[gperm[j1]]] >> 26) == tile) ++j1;
+      while (j1 < M && j1 - j0 < ps::kGridItem && (key[perm[j1]] >> 26) == tile) ++j1;
       ps::GridItem it{};
       it.ty = (int32_t)(tile / g.tilesX);
       it.tx = (int32_t)(tile % g.tilesX);
@@ -464,9 +460,9 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
       it.cstart = (int32_t)gchunks.size();
       int c0 = j0;
       while (c0 < j1) {
-        const int64_t cell = key[perm[gperm[c0]]] & ((1LL << 26) - 1);
+        const int64_t cell = key[perm[c0]] & ((1LL << 26) - 1);
         int c1 = c0;
-        while (c1 < j1 && c1 - c0 < ps::kBinChunk && (key[perm[gperm[c1]]] & ((1LL << 26) - 1)) == cell) ++c1;
+        while (c1 < j1 && c1 - c0 < ps::kBinChunk && (key[perm[c1]] & ((1LL << 26) - 1)) == cell) ++c1;
         const int gy = (int)(cell >> 13), gx = (int)(cell & 8191);
         const int ly = gy - it.ty * ps::kGridTile, lx = gx - it.tx * ps::kGridTile;
         gchunks.push_back((c0 - j0) | ((c1 - c0) << 10) | (ly << 16) | (lx << 24));
@@ -479,12 +475,10 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   }
   h->M = M;
   h->nblocks = M > 0 ? nblocks : 0;
-  h->nchunks = (int)cblock.size();
   h->nitems = (int)items.size();
   h->ngchunks = (int)gchunks.size();
   if (M > 0) h->eps_host.assign(eps, eps + h->nblocks);
   else h->eps_host.clear();
-  h->block_chunk_host = bchunk;
 
   std::vector<float4> rech(M);
   double psf = 0.0;
@@ -504,12 +498,9 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
             dalloc(h, &h->vtmp, 4 * (size_t)M) == cudaSuccess && dalloc(h, &h->rec, (size_t)M) == cudaSuccess &&
             dalloc(h, &h->perm, (size_t)M) == cudaSuccess && dalloc(h, &h->eps, (size_t)h->nblocks) == cudaSuccess &&
             dalloc(h, &h->cb, (size_t)h->nblocks) == cudaSuccess &&
-            dalloc(h, &h->chunk_start, cstart.size()) == cudaSuccess &&
-            dalloc(h, &h->chunk_block, cblock.size()) == cudaSuccess &&
-            dalloc(h, &h->chunk_part, cblock.size()) == cudaSuccess &&
-            dalloc(h, &h->block_chunk, bchunk.size()) == cudaSuccess && dalloc(h, &h->items, items.size()) == cudaSuccess &&
-            dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess && dalloc(h, &h->gperm, (size_t)M) == cudaSuccess &&
-            dalloc(h, &h->gblk, (size_t)M) == cudaSuccess &&
+            dalloc(h, &h->block_sum, (size_t)h->nblocks) == cudaSuccess &&
+            dalloc(h, &h->items, items.size()) == cudaSuccess &&
+            dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess && dalloc(h, &h->vblk, (size_t)M) == cudaSuccess &&
             dalloc(h, &h->T1, (size_t)h->n * Wd) == cudaSuccess && dalloc(h, &h->G, Wd * Wd) == cudaSuccess &&
             dalloc(h, &h->Acc, 2 * Wd * Wd) == cudaSuccess && dalloc(h, &h->T2, (size_t)h->n * Wd) == cudaSuccess &&
             dalloc(h, &h->tw, (size_t)g.K / 2) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess;
@@ -532,13 +523,9 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
     CK(h, cudaMemcpy(h->rec, rech.data(), rech.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->eps, eps, h->nblocks * sizeof(double), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->chunk_start, cstart.data(), cstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->chunk_block, cblock.data(), cblock.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->block_chunk, bchunk.data(), bchunk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->items, items.data(), items.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->gchunks, gchunks.data(), gchunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->gperm, gperm.data(), gperm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->gblk, gblk.data(), gblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->vblk, vblk.data(), vblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     // Measurements into sorted order.
     ps_status st = stage_in(h, vis, 4 * (size_t)M * sizeof(float2), device_ptrs, h->vtmp);
     if (st != PS_OK) return st;
@@ -741,13 +728,12 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
   std::vector<double> part(8 * (size_t)nb);
   CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   // Residual Y - phi(S) per block, and the residual image.
-  std::vector<double> chunk(h->nchunks);
+  std::vector<double> bsum(h->nblocks);
   double rms = 0.0;
   if (h->M > 0) {
     CK(h, ps::nufft_forward_grid(h, h->S));
     CK(h, ps::nufft_degrid(h, ps::DEG_RESID, h->vtmp));
-    CK(h, cudaMemcpyAsync(chunk.data(), h->chunk_part, chunk.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                          h->stream));
+    CK(h, cudaMemcpyAsync(bsum.data(), h->block_sum, bsum.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, ps::nufft_grid(h, h->vtmp, 0));
     CK(h, ps::nufft_adjoint_image(h, h->tmp4));
     CK(h, ps::reduce_dot(h, h->tmp4, h->tmp4, N, dres));
@@ -764,13 +750,8 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
     }
     out->rel_change[c] = den > 0 ? std::sqrt(num / den) : INFINITY;
   }
-  if (out->block_residual) {
-    for (int b = 0; b < std::min(out->nblocks, h->nblocks); ++b) {
-      double s = 0;
-      for (int c = h->block_chunk_host[b]; c < h->block_chunk_host[b + 1]; ++c) s += chunk[c];
-      out->block_residual[b] = std::sqrt(s);
-    }
-  }
+  if (out->block_residual)
+    for (int b = 0; b < std::min(out->nblocks, h->nblocks); ++b) out->block_residual[b] = std::sqrt(bsum[b]);
   out->zeta = h->psf_peak > 0 ? zeta_sigma * rms / h->psf_peak : 0.0;
   CK(h, ps::violation_count(h, h->S, out->zeta, dres + 2));
   ps_status st = ensure_tmp36(h);
@@ -784,7 +765,7 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
   out->violations_raw = (int64_t)h->red_host[3];
   out->weighted_l1 = h->red_host[4];
   out->iterations = h->iterations;
-  return PS_OK;
+  return check_flags(h);
 }
 
 ps_status ps_apply_phi(ps_handle* h, const float* S, float* Y, int32_t device_ptrs) {

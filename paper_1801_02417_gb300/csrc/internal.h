@@ -67,8 +67,9 @@ struct Handle {
   double *red = nullptr;      // reduction partials
   int red_cap = 0;
   double *red_host = nullptr; // pinned
+  int *dev_flags = nullptr;   // device error flags: [0] a bounded wait gave up
 
-  // Visibility-domain state, rows sorted by tile within each block.
+  // Visibility-domain state, rows stored in tap-centre-cell order (tile-major).
   int M = 0, nblocks = 0;
   float2 *R = nullptr;        // residual form of B: B = c_b R  (M x 4)
   float2 *Y = nullptr;        // measurements (M x 4)
@@ -77,18 +78,12 @@ struct Handle {
   float2 *vtmp = nullptr;     // M x 4 scratch
   double *eps = nullptr;      // per block radius (device)
   float *cb = nullptr;        // per block scale c_b (device)
-  int nchunks = 0;
-  int32_t *chunk_start = nullptr;  // nchunks+1 (device)
-  int32_t *chunk_block = nullptr;  // nchunks
-  double *chunk_part = nullptr;    // nchunks partial sums
-  int32_t *block_chunk = nullptr;  // nblocks+1 first chunk of each block
+  double *block_sum = nullptr;     // nblocks FP64 sums filled by the degridding kernel
   int nitems = 0, ngchunks = 0;
   GridItem *items = nullptr;       // gridding work items
   int32_t *gchunks = nullptr;      // packed (start, count, ly, lx) of same-cell chunks
-  int32_t *gperm = nullptr;        // gridding order -> storage row
-  uint16_t *gblk = nullptr;        // block of each gridding-order row
+  uint16_t *vblk = nullptr;        // l2 block of each stored row
   std::vector<double> eps_host;
-  std::vector<int32_t> block_chunk_host;
   double psf_peak = 0.0;      // 2 sum w_m^2: peak of the Stokes-I PSF
   float *tmp36 = nullptr;     // 36N scratch for operator calls (allocated on first use)
   std::vector<int64_t> offsets_host;
@@ -135,7 +130,6 @@ cudaError_t dirac_apply(Handle* h, const float* X, float* coef, float* thr, int 
 cudaError_t reduce_dot(Handle* h, const float* a, const float* b, size_t len, double* dev_out);
 cudaError_t violation_count(Handle* h, const float* S, double zeta, double* dev_out);
 cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* dev_out);
-cudaError_t vis_norms(Handle* h, const float2* v, double* dev_out);
 cudaError_t scale_copy(Handle* h, const float* x, float* y, size_t len, double s);
 cudaError_t gather_vis(Handle* h, const float2* user, float2* sorted);
 cudaError_t scatter_vis(Handle* h, const float2* sorted, float2* user);

@@ -160,20 +160,27 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // Interpolate the packed spectra at +u and -u, unpack the four Stokes spectra,
-// mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. One CTA per chunk.
+// mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. Rows are stored in
+// tap-centre-cell order, so the lanes of a warp mostly read the same spectrum
+// cells (L1 broadcasts) while the row data streams sequentially. Per-block sums of
+// ||B~/rho2 - Y||^2 (DUAL) or ||Y - phi X||^2 (RESID) are combined per warp over
+// lanes of the same block, then through shared-memory FP64 accumulators into
+// global FP64 atomics (block_sum, cleared by the caller).
 template <int W>
-__global__ void __launch_bounds__(256) k_degrid(
-    const float4* __restrict__ rec, const float4* __restrict__ G, int Wd, int off, int full, int K,
-    float beta, int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
-    const float* __restrict__ cb, float inv_rho2, const int32_t* __restrict__ chunk_start,
-    const int32_t* __restrict__ chunk_block, double* __restrict__ chunk_part, float2* __restrict__ out) {
-  __shared__ double sh[32];
+__global__ void __launch_bounds__(256, 3) k_degrid(
+    const float4* __restrict__ rec, const float4* __restrict__ G, int Wd, int off, int full, int K, float beta,
+    int mode, float2* __restrict__ R, const float2* __restrict__ Yv, const float* __restrict__ cb, float inv_rho2,
+    const uint16_t* __restrict__ vblk, int M, int nblocks, double* __restrict__ block_sum, float2* __restrict__ out) {
+  extern __shared__ double bsum[];
   constexpr int hw = W / 2;
-  const int ch = blockIdx.x;
-  const int m0 = chunk_start[ch], m1 = chunk_start[ch + 1];
-  const float cscale = (mode == DEG_DUAL) ? cb[chunk_block[ch]] * inv_rho2 : 0.f;
-  double acc = 0.0;
-  for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+  const bool reduce = (mode != DEG_APPLY);
+  if (reduce)
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) bsum[b] = 0.0;
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  int blk = -1;
+  double e2 = 0.0;
+  if (m < M) {
     float fx, fy, w;
     int cx, cy;
     unpack_rec(rec[m], fx, fy, w, cx, cy);
@@ -201,140 +208,154 @@ __global__ void __launch_bounds__(256) k_degrid(
     float4 v23 = make_float4(w * sn.z, -w * sn.w, w * (FIr - FQr), w * (FIi - FQi));  // LR = conj G2(-u), LL
     float4* R4 = reinterpret_cast<float4*>(R);
     const float4* Y4 = reinterpret_cast<const float4*>(Yv);
-    if (mode == DEG_DUAL) {
-      const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
-      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
-      v01 = f4sub(f4fma(cscale, r0, v01), y0);
-      v23 = f4sub(f4fma(cscale, r1, v23), y1);
-      R4[2 * (size_t)m] = v01;
-      R4[2 * (size_t)m + 1] = v23;
-      acc += (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w +
-                      v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
-    } else if (mode == DEG_RESID) {
-      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
-      v01 = f4sub(y0, v01);
-      v23 = f4sub(y1, v23);
-      acc += (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w +
-                      v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
-      if (out) {
-        float4* o4 = reinterpret_cast<float4*>(out);
-        o4[2 * (size_t)m] = v01;
-        o4[2 * (size_t)m + 1] = v23;
-      }
-    } else {
+    if (mode == DEG_APPLY) {
       float4* o4 = reinterpret_cast<float4*>(out);
       o4[2 * (size_t)m] = v01;
       o4[2 * (size_t)m + 1] = v23;
+    } else {
+      blk = vblk[m];
+      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
+      if (mode == DEG_DUAL) {
+        const float cs = cb[blk] * inv_rho2;
+        const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
+        v01 = f4sub(f4fma(cs, r0, v01), y0);
+        v23 = f4sub(f4fma(cs, r1, v23), y1);
+        R4[2 * (size_t)m] = v01;
+        R4[2 * (size_t)m + 1] = v23;
+      } else {
+        v01 = f4sub(y0, v01);
+        v23 = f4sub(y1, v23);
+        if (out) {
+          float4* o4 = reinterpret_cast<float4*>(out);
+          o4[2 * (size_t)m] = v01;
+          o4[2 * (size_t)m + 1] = v23;
+        }
+      }
+      e2 = (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
+           (double)(v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
     }
   }
-  if (mode != DEG_APPLY) {
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) chunk_part[ch] = s;
+  if (reduce) {
+    // Lanes holding the same block add their terms; the lowest such lane updates shared memory.
+    const unsigned peers = __match_any_sync(0xffffffffu, blk);
+    double sum = 0.0;
+    for (unsigned p = peers; p; p &= p - 1) sum += __shfl_sync(peers, e2, __ffs(p) - 1);
+    if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bsum[blk], sum);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+      if (bsum[b] != 0.0) atomicAdd(&block_sum[b], bsum[b]);
   }
 }
 
 // Per-block factor c_b of B = c_b R after the l2-ball step (Algorithm 1 step 8):
 // with r = ||B~/rho2 - Y||_b, c_b = rho2 (1 - min(1, radius / r)).
-__global__ void k_block_scale(const double* __restrict__ part, const int32_t* __restrict__ block_chunk,
-                              const double* __restrict__ eps, int nblocks, double rho2, int literal,
-                              float* __restrict__ cb) {
+__global__ void k_block_scale(const double* __restrict__ block_sum, const double* __restrict__ eps, int nblocks,
+                              double rho2, int literal, float* __restrict__ cb) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblocks) return;
-  double s = 0.0;
-  for (int c = block_chunk[b]; c < block_chunk[b + 1]; ++c) s += part[c];
-  const double r = sqrt(s);
+  const double r = sqrt(block_sum[b]);
   const double radius = literal ? eps[b] / rho2 : eps[b];
   const double keep = (r > radius) ? radius / r : 1.0;
   cb[b] = (float)(rho2 * (1.0 - keep));
 }
 
 // Gridding (adjoint of the interpolation), Alg. 1 step 3's phi^dagger.
-// Visibilities are globally sorted by tap-centre cell. One CTA owns a work item:
+// Rows are stored sorted by tap-centre cell. One CTA owns a work item:
 // up to kGridItem visibilities whose centres lie in one kGridTile^2 tile.
-//  1. Each thread stages one visibility: the conj(L)-mixed rows
-//     x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL), scaled by
-//     c_b w_m, and its W x and W y kernel weights, in shared memory.
-//  2. Visibilities sharing a centre cell (a "bin", split into chunks of <= 32)
-//     touch the same W x W cells, so thread (chunk, jy) accumulates the W x 8
-//     outputs of kernel row jy over the chunk in registers, then adds them once
-//     to a shared-memory tile (tile + halo).
-//  3. The tile is added to the global accumulator (one float4 atomic per
-//     non-zero half-cell).
+//  1. Each thread stages one visibility as a row of shared memory: the
+//     conj(L)-mixed values x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR,
+//     x_V = i (LR - RL) scaled by c_b w_m, then its W x and W y kernel weights.
+//  2. Visibilities sharing a centre cell (a chunk of <= 32) touch the same W x W
+//     cells. One warp takes one chunk; lane l owns kernel cells l, l+32, ... and
+//     accumulates their 8 channels over the chunk in registers (the staged row is
+//     read as a broadcast), then adds them once to a shared-memory tile.
+//  3. The tile (with halo) is added to the global accumulator.
 // Channels are gridded at +u only; k_adj_cols forms the -u half by Hermitian
 // symmetrisation.
 template <int W>
+__host__ __device__ constexpr int grid_row() { return (8 + 2 * W + 3) / 4 * 4; }
+
+template <int W>
 __global__ void __launch_bounds__(256) k_grid(
-    const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const int32_t* __restrict__ gperm,
-    const uint16_t* __restrict__ gblk, const float4* __restrict__ rec, const float2* __restrict__ vin,
+    const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
+    const float4* __restrict__ rec, const float2* __restrict__ vin,
     const float* __restrict__ cb, int use_scale, int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
   constexpr int TS = kGridTile;
   constexpr int SS = TS + W - 1;
   constexpr int hw = W / 2;
   constexpr int V = kGridItem;
+  constexpr int P = grid_row<W>();
+  constexpr int CPL = (W * W + 31) / 32;          // kernel cells per lane
   extern __shared__ float4 smg[];
   float* acc = reinterpret_cast<float*>(smg);   // SS*SS*8
-  float* xs = acc + SS * SS * 8;         // 8 x V
-  float* wxs = xs + 8 * V;               // W x V
-  float* wys = wxs + W * V;              // W x V
+  float* st = acc + SS * SS * 8;                // V rows of P floats: x[8], wx[W], wy[W]
   const GridItem it = items[blockIdx.x];
   for (int i = threadIdx.x; i < SS * SS * 8; i += blockDim.x) acc[i] = 0.f;
   const int nv = it.vend - it.vstart;
   const float4* v4 = reinterpret_cast<const float4*>(vin);
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    const int g = it.vstart + j;
-    const int idx = gperm[g];
+    const int idx = it.vstart + j;
     float fx, fy, w;
     int cx, cy;
     unpack_rec(rec[idx], fx, fy, w, cx, cy);
-    const float s = (use_scale ? cb[gblk[g]] : 1.0f) * w;
+    const float sc = (use_scale ? cb[vblk[idx]] : 1.0f) * w;
     const float4 b0 = v4[2 * (size_t)idx], b1 = v4[2 * (size_t)idx + 1];   // RR, RL | LR, LL
-    xs[0 * V + j] = s * (b0.x + b1.z);
-    xs[1 * V + j] = s * (b0.y + b1.w);
-    xs[2 * V + j] = s * (b0.x - b1.z);
-    xs[3 * V + j] = s * (b0.y - b1.w);
-    xs[4 * V + j] = s * (b0.z + b1.x);
-    xs[5 * V + j] = s * (b0.w + b1.y);
-    xs[6 * V + j] = -s * (b1.y - b0.w);
-    xs[7 * V + j] = s * (b1.x - b0.z);
+    float* row = st + j * P;
+    *reinterpret_cast<float4*>(row) =
+        make_float4(sc * (b0.x + b1.z), sc * (b0.y + b1.w), sc * (b0.x - b1.z), sc * (b0.y - b1.w));
+    *reinterpret_cast<float4*>(row + 4) =
+        make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
     float wx[W], wy[W];
     es_weights<W>(fx, beta, wx);
     es_weights<W>(fy, beta, wy);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      wxs[k * V + j] = wx[k];
-      wys[k * V + j] = wy[k];
+      row[8 + k] = wx[k];
+      row[8 + W + k] = wy[k];
     }
   }
   __syncthreads();
-  const int per = blockDim.x / W;
-  const int cl = threadIdx.x / W, jy = threadIdx.x - cl * W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nc = it.cend - it.cstart;
-  if (cl < per) {
-    for (int c = cl; c < nc; c += per) {
-      const int pk = chunks[it.cstart + c];
-      const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
-      float a[W][8];
+  int cjx[CPL], cjy[CPL];
 #pragma unroll
-      for (int jx = 0; jx < W; ++jx)
+  for (int q = 0; q < CPL; ++q) {
+    const int cell = lane + 32 * q;
+    cjy[q] = cell < W * W ? cell / W : 0;
+    cjx[q] = cell < W * W ? cell - (cell / W) * W : 0;
+  }
+  for (int c = warp; c < nc; c += nwarps) {
+    const int pk = chunks[it.cstart + c];
+    const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
+    float a[CPL][8];
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) a[jx][ch] = 0.f;
-      for (int v = v0; v < v0 + cnt; ++v) {
-        const float wyv = wys[jy * V + v];
-        float x[8];
+    for (int q = 0; q < CPL; ++q)
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) x[ch] = wyv * xs[ch * V + v];
+      for (int ch = 0; ch < 8; ++ch) a[q][ch] = 0.f;
+    for (int v = v0; v < v0 + cnt; ++v) {
+      const float* row = st + v * P;
+      const float4 x0 = *reinterpret_cast<const float4*>(row);
+      const float4 x1 = *reinterpret_cast<const float4*>(row + 4);
 #pragma unroll
-        for (int jx = 0; jx < W; ++jx) {
-          const float wv = wxs[jx * V + v];
-#pragma unroll
-          for (int ch = 0; ch < 8; ++ch) a[jx][ch] = fmaf(wv, x[ch], a[jx][ch]);
-        }
+      for (int q = 0; q < CPL; ++q) {
+        const float k = row[8 + cjx[q]] * row[8 + W + cjy[q]];
+        a[q][0] = fmaf(k, x0.x, a[q][0]);
+        a[q][1] = fmaf(k, x0.y, a[q][1]);
+        a[q][2] = fmaf(k, x0.z, a[q][2]);
+        a[q][3] = fmaf(k, x0.w, a[q][3]);
+        a[q][4] = fmaf(k, x1.x, a[q][4]);
+        a[q][5] = fmaf(k, x1.y, a[q][5]);
+        a[q][6] = fmaf(k, x1.z, a[q][6]);
+        a[q][7] = fmaf(k, x1.w, a[q][7]);
       }
-      float* dst = acc + ((ly + jy) * SS + lx) * 8;
+    }
 #pragma unroll
-      for (int jx = 0; jx < W; ++jx)
+    for (int q = 0; q < CPL; ++q) {
+      if (lane + 32 * q < W * W) {
+        float* dst = acc + ((ly + cjy[q]) * SS + (lx + cjx[q])) * 8;
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) atomicAdd(dst + jx * 8 + ch, a[jx][ch]);
+        for (int ch = 0; ch < 8; ++ch) atomicAdd(dst + ch, a[q][ch]);
+      }
     }
   }
   __syncthreads();
@@ -358,7 +379,7 @@ __global__ void __launch_bounds__(256) k_grid(
 
 template <int W>
 static constexpr size_t grid_smem() {
-  return (size_t)((kGridTile + W - 1) * (kGridTile + W - 1) * 8 + 8 * kGridItem + 2 * W * kGridItem) * sizeof(float);
+  return (size_t)((kGridTile + W - 1) * (kGridTile + W - 1) * 8 + kGridItem * grid_row<W>()) * sizeof(float);
 }
 
 // Hermitian symmetrisation + inverse column FFTs for the column pair (kx, -kx).
@@ -444,6 +465,10 @@ cudaError_t configure_nufft_kernels() {
   if ((e = set_smem((const void*)k_grid<5>, grid_smem<5>())) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_grid<7>, grid_smem<7>())) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_grid<9>, grid_smem<9>())) != cudaSuccess) return e;
+  // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
+  if ((e = set_smem((const void*)k_degrid<5>, 2048 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_degrid<7>, 2048 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_degrid<9>, 2048 * sizeof(double))) != cudaSuccess) return e;
   return set_smem((const void*)k_adj_cols, sm2);
 }
 
@@ -458,13 +483,18 @@ cudaError_t nufft_forward_grid(Handle* h, const float* X) {
 template <int W>
 static void launch_degrid(Handle* h, int mode, float2* out) {
   const GridGeom& g = h->g;
-  k_degrid<W><<<h->nchunks, 256, 0, h->stream>>>(h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode, h->R, h->Y,
-                                                   h->cb, (float)(1.0 / h->rho2), h->chunk_start, h->chunk_block,
-                                                   h->chunk_part, out);
+  const size_t sm = (size_t)h->nblocks * sizeof(double);
+  k_degrid<W><<<(h->M + 255) / 256, 256, sm, h->stream>>>(h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode, h->R,
+                                                          h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->M,
+                                                          h->nblocks, h->block_sum, out);
 }
 
 cudaError_t nufft_degrid(Handle* h, int mode, float2* out) {
-  if (h->nchunks == 0) return cudaSuccess;
+  if (h->M == 0) return cudaSuccess;
+  if (mode != DEG_APPLY) {
+    cudaError_t e = cudaMemsetAsync(h->block_sum, 0, (size_t)h->nblocks * sizeof(double), h->stream);
+    if (e != cudaSuccess) return e;
+  }
   switch (h->g.W) {
     case 5: launch_degrid<5>(h, mode, out); break;
     case 9: launch_degrid<9>(h, mode, out); break;
@@ -475,15 +505,15 @@ cudaError_t nufft_degrid(Handle* h, int mode, float2* out) {
 
 cudaError_t block_scales(Handle* h) {
   if (h->nblocks == 0) return cudaSuccess;
-  k_block_scale<<<(h->nblocks + 127) / 128, 128, 0, h->stream>>>(h->chunk_part, h->block_chunk, h->eps, h->nblocks,
-                                                                 h->rho2, h->cfg.literal_ball, h->cb);
+  k_block_scale<<<(h->nblocks + 127) / 128, 128, 0, h->stream>>>(h->block_sum, h->eps, h->nblocks, h->rho2,
+                                                                 h->cfg.literal_ball, h->cb);
   return cudaGetLastError();
 }
 
 template <int W>
 static void launch_grid(Handle* h, const float2* in, int use_scale) {
   const GridGeom& g = h->g;
-  k_grid<W><<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->gperm, h->gblk, h->rec, in, h->cb,
+  k_grid<W><<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->vblk, h->rec, in, h->cb,
                                                             use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
 }
 

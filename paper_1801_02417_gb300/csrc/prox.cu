@@ -310,45 +310,19 @@ cudaError_t scatter_vis(Handle* h, const float2* sorted, float2* user) {
   return cudaGetLastError();
 }
 
-__global__ void k_scale_vis(const int32_t* __restrict__ chunk_start, const int32_t* __restrict__ chunk_block,
-                            const float* __restrict__ cb, float4* __restrict__ v) {
-  const int ch = blockIdx.x;
-  const float s = cb[chunk_block[ch]];
-  for (int m = chunk_start[ch] + threadIdx.x; m < chunk_start[ch + 1]; m += blockDim.x) {
-    float4 a = v[2 * (size_t)m], b = v[2 * (size_t)m + 1];
-    v[2 * (size_t)m] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
-    v[2 * (size_t)m + 1] = make_float4(b.x * s, b.y * s, b.z * s, b.w * s);
-  }
+__global__ void k_scale_vis(int M, const uint16_t* __restrict__ vblk, const float* __restrict__ cb,
+                            float4* __restrict__ v) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const float s = cb[vblk[m]];
+  const float4 a = v[2 * (size_t)m], b = v[2 * (size_t)m + 1];
+  v[2 * (size_t)m] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+  v[2 * (size_t)m + 1] = make_float4(b.x * s, b.y * s, b.z * s, b.w * s);
 }
 
 cudaError_t scale_vis(Handle* h, float2* v) {
-  if (h->nchunks == 0) return cudaSuccess;
-  k_scale_vis<<<h->nchunks, 256, 0, h->stream>>>(h->chunk_start, h->chunk_block, h->cb, reinterpret_cast<float4*>(v));
-  return cudaGetLastError();
-}
-
-__global__ void k_vis_norms(const int32_t* __restrict__ chunk_start, const float4* __restrict__ v,
-                            double* __restrict__ part) {
-  __shared__ double sh[32];
-  const int ch = blockIdx.x;
-  double s = 0.0;
-  for (int m = chunk_start[ch] + threadIdx.x; m < chunk_start[ch + 1]; m += blockDim.x) {
-    const float4 a = v[2 * (size_t)m], b = v[2 * (size_t)m + 1];
-    s += (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w + b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
-  }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
-    part[ch] = r;
-  }
-}
-
-cudaError_t vis_norms(Handle* h, const float2* v, double* dev_out) {
-  if (h->nchunks == 0) return cudaSuccess;
-  k_vis_norms<<<h->nchunks, 256, 0, h->stream>>>(h->chunk_start, reinterpret_cast<const float4*>(v), dev_out);
+  if (h->M == 0) return cudaSuccess;
+  k_scale_vis<<<(h->M + 255) / 256, 256, 0, h->stream>>>(h->M, h->vblk, h->cb, reinterpret_cast<float4*>(v));
   return cudaGetLastError();
 }
 

@@ -214,6 +214,43 @@ constexpr int kPs = kCImax + 2;                  // 25
 
 __device__ __forceinline__ int wrap1(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
 
+// ---- bulk-copy (TMA) and mbarrier helpers (inline PTX, sm_90+).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Bounded wait on phase `parity`: false (and the caller raises the error flag) if it never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// 4-byte asynchronous global->shared copies (cp.async), grouped and awaited per group.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Rows: lo/hi[r][k] = sum_j h/g[j] in[r][2k + j], k in [0, TO).
 template <int LF>
 __device__ __forceinline__ void ana_rows(const float* __restrict__ in_s, float* __restrict__ lo_s,
@@ -273,7 +310,8 @@ template <int LF>
 __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const float* __restrict__ hi_s, int bi,
                                          int map, int n, int hm, int oy0, int ox0, int last, float* __restrict__ coef,
                                          float* __restrict__ thr, float* __restrict__ approx_out, int mode,
-                                         float scale, float gamma, float delta) {
+                                         float scale, float gamma, float delta, const float* __restrict__ st_a,
+                                         const float* __restrict__ st_t) {
   constexpr int b = LF / 2 - 1;
   const size_t base = ((size_t)map * kBases + (bi + 1)) * (size_t)n * n;
   for (int u = threadIdx.x; u < kTO * kTO / 4; u += blockDim.x) {
@@ -286,12 +324,14 @@ __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const f
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 a_hl = z, a_lh = z, a_hh = z, a_ll = z, t_hl = z, t_lh = z, t_hh = z, t_ll = z;
     if (mode == SARA_DUAL) {
-      a_hl = *reinterpret_cast<const float4*>(coef + i_hl);
-      a_lh = *reinterpret_cast<const float4*>(coef + i_lh);
-      a_hh = *reinterpret_cast<const float4*>(coef + i_hh);
-      t_hl = *reinterpret_cast<const float4*>(thr + i_hl);
-      t_lh = *reinterpret_cast<const float4*>(thr + i_lh);
-      t_hh = *reinterpret_cast<const float4*>(thr + i_hh);
+      // Staged by the bulk-copy engine: [subband][row][32].
+      const int so = ky * kTO + kx0;
+      a_hl = *reinterpret_cast<const float4*>(st_a + so);
+      a_lh = *reinterpret_cast<const float4*>(st_a + kTO * kTO + so);
+      a_hh = *reinterpret_cast<const float4*>(st_a + 2 * kTO * kTO + so);
+      t_hl = *reinterpret_cast<const float4*>(st_t + so);
+      t_lh = *reinterpret_cast<const float4*>(st_t + kTO * kTO + so);
+      t_hh = *reinterpret_cast<const float4*>(st_t + 2 * kTO * kTO + so);
       if (last) {
         a_ll = *reinterpret_cast<const float4*>(coef + i_ll);
         t_ll = *reinterpret_cast<const float4*>(thr + i_ll);
@@ -315,21 +355,45 @@ __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const f
   }
 }
 
-template <int LF>
-__device__ __forceinline__ void ana_basis(const float* in_s, float* lo_s, float* hi_s, int bi, int map, int n, int hm,
-                                          int oy0, int ox0, int last, float* coef, float* thr, float* approx_out,
-                                          int mode, float scale, float gamma, float delta) {
-  ana_rows<LF>(in_s, lo_s, hi_s);
-  __syncthreads();
-  ana_cols<LF>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta);
-  __syncthreads();
+template <int RS>
+__device__ __forceinline__ void load_in_tile_t(const float* __restrict__ src, int m, int oy0, int ox0,
+                                               float* __restrict__ in_s) {
+  // Rows of RS floats starting at an even column: float2 loads (periodic wrap only at the last tile).
+  for (int i = threadIdx.x; i < RS * (RS / 2); i += blockDim.x) {
+    const int r = i / (RS / 2), c = 2 * (i - r * (RS / 2));
+    int y = 2 * oy0 + r, x = 2 * ox0 + c;
+    if (y >= m) y -= m;
+    if (x >= m) x -= m;
+    const float2 v = *reinterpret_cast<const float2*>(src + (size_t)y * m + x);
+    in_s[r * kPin + c] = v.x;
+    in_s[r * kPin + c + 1] = v.y;
+  }
 }
 
-__device__ __forceinline__ void ana_dispatch(int bi, const float* in_s, float* lo_s, float* hi_s, int map, int n,
-                                             int hm, int oy0, int ox0, int last, float* coef, float* thr,
-                                             float* approx_out, int mode, float scale, float gamma, float delta) {
-#define PS_ANA(LFv) ana_basis<LFv>(in_s, lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, \
-                                   scale, gamma, delta)
+template <int LF>
+__device__ __forceinline__ void ana_basis(const float* src, int m, float* in_s, float* lo_s, float* hi_s, int bi,
+                                          int map, int n, int hm, int oy0, int ox0, int last, float* coef, float* thr,
+                                          float* approx_out, int mode, float scale, float gamma, float delta,
+                                          const float* st_a, const float* st_t, uint64_t* bar, int* err) {
+  load_in_tile_t<2 * kTO + LF - 2>(src, m, oy0, ox0, in_s);
+  __syncthreads();
+  ana_rows<LF>(in_s, lo_s, hi_s);
+  __syncthreads();
+  if (mode == SARA_DUAL && !mbar_wait(bar, 0)) {
+    atomicExch(err, 1);
+    return;   // copies that never completed: leave this tile unchanged (host reports PS_ETIMEOUT)
+  }
+  ana_cols<LF>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, st_a,
+               st_t);
+}
+
+__device__ __forceinline__ void ana_dispatch(int bi, const float* src, int m, float* in_s, float* lo_s, float* hi_s,
+                                             int map, int n, int hm, int oy0, int ox0, int last, float* coef,
+                                             float* thr, float* approx_out, int mode, float scale, float gamma,
+                                             float delta, const float* st_a, const float* st_t, uint64_t* bar,
+                                             int* err) {
+#define PS_ANA(LFv) ana_basis<LFv>(src, m, in_s, lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, \
+                                   mode, scale, gamma, delta, st_a, st_t, bar, err)
   switch (bi) {
     case 0: PS_ANA(2); break;
     case 1: PS_ANA(4); break;
@@ -343,60 +407,92 @@ __device__ __forceinline__ void ana_dispatch(int bi, const float* in_s, float* l
 #undef PS_ANA
 }
 
-__device__ __forceinline__ void load_in_tile(const float* __restrict__ src, int m, int oy0, int ox0, int RS,
-                                             float* __restrict__ in_s) {
-  for (int i = threadIdx.x; i < RS * RS; i += blockDim.x) {
-    const int r = i / RS, c = i - r * RS;
-    int y = 2 * oy0 + r, x = 2 * ox0 + c;
-    if (y >= m) y -= m;
-    if (x >= m) x -= m;
-    in_s[r * kPin + c] = src[(size_t)y * m + x];
+// Shared-memory layout of the fast analysis kernels (floats): input tile, row-filtered
+// low/high tiles, the staged A and gamma W rows of the three detail subbands, mbarrier.
+constexpr int kStage = 3 * kTO * kTO;
+constexpr int kAnaFloats = kInSize + 2 * kRSmax * kPlo + 2 * kStage;
+
+// The first 3 * 32 * 2 threads each start one bulk copy of this tile's A and gamma W
+// detail rows (3 subbands x 32 rows x 128 B) so they arrive while the rows are
+// filtered; thread 0 sets the expected byte count (the barrier's transaction count
+// may run ahead of it).
+__device__ __forceinline__ void stage_epilogue(const float* coef, const float* thr, size_t base, int n, int hm,
+                                               int oy0, int ox0, float* st_a, float* st_t, uint64_t* bar) {
+  if (threadIdx.x == 0) mbar_expect_tx(bar, 2u * kStage * sizeof(float));
+  const int k = threadIdx.x;
+  if (k < 2 * 3 * kTO) {
+    const int arr = k / (3 * kTO), kk = k - arr * (3 * kTO);
+    const int sb = kk / kTO, r = kk - sb * kTO;
+    const int Y = oy0 + r;
+    const size_t off = sb == 0 ? base + (size_t)Y * n + hm + ox0
+                               : (sb == 1 ? base + (size_t)(hm + Y) * n + ox0 : base + (size_t)(hm + Y) * n + hm + ox0);
+    float* dst = (arr ? st_t : st_a) + sb * kTO * kTO + r * kTO;
+    bulk_g2s(dst, (arr ? thr : coef) + off, kTO * sizeof(float), bar);
   }
+}
+
+struct AnaSmem {
+  float *in_s, *lo_s, *hi_s, *st_a, *st_t;
+  uint64_t* bar;
+};
+__device__ __forceinline__ AnaSmem ana_smem(float4* sma) {
+  AnaSmem a;
+  a.in_s = reinterpret_cast<float*>(sma);
+  a.lo_s = a.in_s + kInSize;
+  a.hi_s = a.lo_s + kRSmax * kPlo;
+  a.st_a = a.hi_s + kRSmax * kPlo;
+  a.st_t = a.st_a + kStage;
+  a.bar = reinterpret_cast<uint64_t*>(a.st_t + kStage);
+  return a;
 }
 
 // Level-1 analysis: input is the map itself; one basis per CTA (grid.y).
 __global__ void __launch_bounds__(256, 3) k_ana_l1(const float* __restrict__ X, int n, int last, float* __restrict__ coef,
-                                                float* __restrict__ thr, float* __restrict__ approx_out, int mode,
-                                                float scale, float gamma, float delta) {
+                                                   float* __restrict__ thr, float* __restrict__ approx_out, int mode,
+                                                   float scale, float gamma, float delta, int* err) {
   extern __shared__ float4 sma[];
-  float* in_s = reinterpret_cast<float*>(sma);
-  float* lo_s = in_s + kInSize;
-  float* hi_s = lo_s + kRSmax * kPlo;
+  const AnaSmem S = ana_smem(sma);
   const int bi = blockIdx.y, map = blockIdx.z;
   const int hm = n >> 1, tilesx = hm / kTO;
   const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
-  load_in_tile(X + (size_t)map * n * n, n, oy0, ox0, 2 * kTO + 2 * bi, in_s);
+  if (threadIdx.x == 0) mbar_init(S.bar, 1);
   __syncthreads();
-  ana_dispatch(bi, in_s, lo_s, hi_s, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta);
+  if (mode == SARA_DUAL)
+    stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, S.st_a, S.st_t, S.bar);
+  ana_dispatch(bi, X + (size_t)map * n * n, n, S.in_s, S.lo_s, S.hi_s, map, n, hm, oy0, ox0, last, coef, thr,
+               approx_out, mode, scale, gamma, delta, S.st_a, S.st_t, S.bar, err);
 }
 
 // Levels >= 2 with half size >= 32: one basis per CTA (grid.y).
 __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ approx_in, int m, int n, int last,
-                                                float* __restrict__ coef, float* __restrict__ thr,
-                                                float* __restrict__ approx_out, int mode, float scale, float gamma,
-                                                float delta) {
+                                                   float* __restrict__ coef, float* __restrict__ thr,
+                                                   float* __restrict__ approx_out, int mode, float scale, float gamma,
+                                                   float delta, int* err) {
   extern __shared__ float4 sma[];
-  float* in_s = reinterpret_cast<float*>(sma);
-  float* lo_s = in_s + kInSize;
-  float* hi_s = lo_s + kRSmax * kPlo;
+  const AnaSmem S = ana_smem(sma);
   const int bi = blockIdx.y, map = blockIdx.z;
   const int hm = m >> 1, tilesx = hm / kTO;
   const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
-  load_in_tile(approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, oy0, ox0, 2 * kTO + 2 * bi, in_s);
+  if (threadIdx.x == 0) mbar_init(S.bar, 1);
   __syncthreads();
-  ana_dispatch(bi, in_s, lo_s, hi_s, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta);
+  if (mode == SARA_DUAL)
+    stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, S.st_a, S.st_t, S.bar);
+  ana_dispatch(bi, approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, S.in_s, S.lo_s, S.hi_s, map, n, hm, oy0,
+               ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, S.st_a, S.st_t, S.bar, err);
 }
 
-// Synthesis of one basis on a TI x TI output tile: loads the four subband tiles
-// (with the filter halo), filters along y then x, adds the result to acc[4]
-// (this thread's four outputs out[r][c0 .. c0+3], r = tid / 8, c0 = 4 (tid % 8)).
+// Synthesis of one basis on a TI x TI output tile, split in two steps so the
+// next basis' coefficients can be in flight (cp.async) while this one is filtered:
+//   syn_load     copies the four subband tiles (with the filter halo, periodic wrap);
+//   syn_compute  filters along y then x and adds to acc[4], this thread's outputs
+//                out[r][c0 .. c0+3] with r = tid / 8, c0 = 4 (tid % 8).
+constexpr int kS4 = 4 * kCImax * kPc;            // one set of four subband tiles
+
 template <int LF>
-__device__ __forceinline__ void syn_basis(const float* __restrict__ cb, const float* __restrict__ apx, int n, int m,
-                                          int oy0, int ox0, float* __restrict__ s4, float* __restrict__ s_lo,
-                                          float* __restrict__ s_hi, float acc[4]) {
+__device__ __forceinline__ void syn_load(const float* __restrict__ cb, const float* __restrict__ apx, int n, int m,
+                                         int oy0, int ox0, float* __restrict__ s4) {
   constexpr int half = LF / 2 - 1;
   constexpr int CI = kTI / 2 + half;
-  constexpr int b = LF / 2 - 1;
   const int hm = m >> 1;
   float* s_ll = s4;
   float* s_lh = s4 + kCImax * kPc;
@@ -406,12 +502,23 @@ __device__ __forceinline__ void syn_basis(const float* __restrict__ cb, const fl
   for (int i = threadIdx.x; i < CI * CI; i += blockDim.x) {
     const int r = i / CI, c = i - r * CI;
     const int Yk = wrap1(ky0 + r, hm), Xk = wrap1(kx0 + c, hm);
-    s_ll[r * kPc + c] = apx ? apx[(size_t)Yk * hm + Xk] : cb[(size_t)Yk * n + Xk];
-    s_hl[r * kPc + c] = cb[(size_t)Yk * n + hm + Xk];
-    s_lh[r * kPc + c] = cb[(size_t)(hm + Yk) * n + Xk];
-    s_hh[r * kPc + c] = cb[(size_t)(hm + Yk) * n + hm + Xk];
+    cp_async4(s_ll + r * kPc + c, apx ? apx + (size_t)Yk * hm + Xk : cb + (size_t)Yk * n + Xk);
+    cp_async4(s_hl + r * kPc + c, cb + (size_t)Yk * n + hm + Xk);
+    cp_async4(s_lh + r * kPc + c, cb + (size_t)(hm + Yk) * n + Xk);
+    cp_async4(s_hh + r * kPc + c, cb + (size_t)(hm + Yk) * n + hm + Xk);
   }
-  __syncthreads();
+}
+
+template <int LF>
+__device__ __forceinline__ void syn_compute(const float* __restrict__ s4, float* __restrict__ s_lo,
+                                            float* __restrict__ s_hi, float acc[4]) {
+  constexpr int half = LF / 2 - 1;
+  constexpr int CI = kTI / 2 + half;
+  constexpr int b = LF / 2 - 1;
+  const float* s_ll = s4;
+  const float* s_lh = s4 + kCImax * kPc;
+  const float* s_hl = s_lh + kCImax * kPc;
+  const float* s_hh = s_hl + kCImax * kPc;
   // Along y: lo[r][c] = sum_{j = r mod 2} h[j] ll[(r - j)/2 + half][c] + g[j] lh[...]; coefficient
   // row r0/2 + i feeds output row r0 + t through tap j = t - 2 (i - half).
   for (int u = threadIdx.x; u < CI * (kTI / 4); u += blockDim.x) {
@@ -437,55 +544,74 @@ __device__ __forceinline__ void syn_basis(const float* __restrict__ cb, const fl
     }
   }
   __syncthreads();
-  {
-    const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
 #pragma unroll
-    for (int i = 0; i < half + 2; ++i) {
-      const float vlo = s_lo[r * kPs + c0 / 2 + i], vhi = s_hi[r * kPs + c0 / 2 + i];
+  for (int i = 0; i < half + 2; ++i) {
+    const float vlo = s_lo[r * kPs + c0 / 2 + i], vhi = s_hi[r * kPs + c0 / 2 + i];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int j = t - 2 * (i - half);
-        if (j >= 0 && j < LF) acc[t] = fmaf(c_h[b][j], vlo, fmaf(c_g[b][j], vhi, acc[t]));
-      }
+    for (int t = 0; t < 4; ++t) {
+      const int j = t - 2 * (i - half);
+      if (j >= 0 && j < LF) acc[t] = fmaf(c_h[b][j], vlo, fmaf(c_g[b][j], vhi, acc[t]));
     }
   }
-  __syncthreads();
 }
 
-__device__ __forceinline__ void syn_dispatch(int bi, const float* cb, const float* apx, int n, int m, int oy0,
-                                             int ox0, float* s4, float* s_lo, float* s_hi, float acc[4]) {
-#define PS_SYN(LFv) syn_basis<LFv>(cb, apx, n, m, oy0, ox0, s4, s_lo, s_hi, acc)
-  switch (bi) {
-    case 0: PS_SYN(2); break;
-    case 1: PS_SYN(4); break;
-    case 2: PS_SYN(6); break;
-    case 3: PS_SYN(8); break;
-    case 4: PS_SYN(10); break;
-    case 5: PS_SYN(12); break;
-    case 6: PS_SYN(14); break;
-    default: PS_SYN(16); break;
+#define PS_SWITCH_LF(bi, CALL)    \
+  switch (bi) {                   \
+    case 0: CALL(2); break;       \
+    case 1: CALL(4); break;       \
+    case 2: CALL(6); break;       \
+    case 3: CALL(8); break;       \
+    case 4: CALL(10); break;      \
+    case 5: CALL(12); break;      \
+    case 6: CALL(14); break;      \
+    default: CALL(16); break;     \
   }
-#undef PS_SYN
+
+__device__ __forceinline__ void syn_load_dispatch(int bi, const float* cb, const float* apx, int n, int m, int oy0,
+                                                  int ox0, float* s4) {
+#define PS_L(LFv) syn_load<LFv>(cb, apx, n, m, oy0, ox0, s4)
+  PS_SWITCH_LF(bi, PS_L)
+#undef PS_L
+}
+__device__ __forceinline__ void syn_compute_dispatch(int bi, const float* s4, float* s_lo, float* s_hi, float acc[4]) {
+#define PS_C(LFv) syn_compute<LFv>(s4, s_lo, s_hi, acc)
+  PS_SWITCH_LF(bi, PS_C)
+#undef PS_C
 }
 
-constexpr int kSynSmemFloats = 4 * kCImax * kPc + 2 * kTI * kPs;
+constexpr int kSynSmemFloats = 2 * kS4 + 2 * kTI * kPs;
 
 // Finest level (m = n): all eight bases plus Dirac summed in registers -> Psi A.
+// Basis bi+1's tiles are copied asynchronously while basis bi is filtered.
 __global__ void __launch_bounds__(256, 3) k_syn_fine(const float* __restrict__ coef, const float* __restrict__ approx_in,
-                                                  int coarsest, int n, float* __restrict__ out) {
+                                                     int coarsest, int n, float* __restrict__ out) {
   __shared__ __align__(16) float sm_s[kSynSmemFloats];
-  float* s4 = sm_s;
-  float* s_lo = sm_s + 4 * kCImax * kPc;
+  float* s4b[2] = {sm_s, sm_s + kS4};
+  float* s_lo = sm_s + 2 * kS4;
   float* s_hi = s_lo + kTI * kPs;
   const int map = blockIdx.z;
   const int tilesx = n / kTI;
   const int oy0 = (blockIdx.x / tilesx) * kTI, ox0 = (blockIdx.x % tilesx) * kTI;
   const int hm = n >> 1;
+  auto cbp = [&](int bi) { return coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n; };
+  auto apxp = [&](int bi) {
+    return coarsest ? (const float*)nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
+  };
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  syn_load_dispatch(0, cbp(0), apxp(0), n, n, oy0, ox0, s4b[0]);
+  cp_async_commit();
   for (int bi = 0; bi < kDb; ++bi) {
-    const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
-    const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
-    syn_dispatch(bi, cb, apx, n, n, oy0, ox0, s4, s_lo, s_hi, acc);
+    if (bi + 1 < kDb) {
+      syn_load_dispatch(bi + 1, cbp(bi + 1), apxp(bi + 1), n, n, oy0, ox0, s4b[(bi + 1) & 1]);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    syn_compute_dispatch(bi, s4b[bi & 1], s_lo, s_hi, acc);
+    __syncthreads();
   }
   const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
   const size_t o = (size_t)(oy0 + r) * n + ox0 + c0;
@@ -497,10 +623,10 @@ __global__ void __launch_bounds__(256, 3) k_syn_fine(const float* __restrict__ c
 
 // Coarser levels with output side m >= 32: one basis per CTA (grid.y), output to approximation scratch.
 __global__ void __launch_bounds__(256, 4) k_syn_lv(const float* __restrict__ coef, const float* __restrict__ approx_in,
-                                                int coarsest, int m, int n, float* __restrict__ approx_out) {
-  __shared__ __align__(16) float sm_s[kSynSmemFloats];
+                                                   int coarsest, int m, int n, float* __restrict__ approx_out) {
+  __shared__ __align__(16) float sm_s[kS4 + 2 * kTI * kPs];
   float* s4 = sm_s;
-  float* s_lo = sm_s + 4 * kCImax * kPc;
+  float* s_lo = sm_s + kS4;
   float* s_hi = s_lo + kTI * kPs;
   const int bi = blockIdx.y, map = blockIdx.z;
   const int tilesx = m / kTI;
@@ -509,14 +635,18 @@ __global__ void __launch_bounds__(256, 4) k_syn_lv(const float* __restrict__ coe
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
   const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
-  syn_dispatch(bi, cb, apx, n, m, oy0, ox0, s4, s_lo, s_hi, acc);
+  syn_load_dispatch(bi, cb, apx, n, m, oy0, ox0, s4);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  syn_compute_dispatch(bi, s4, s_lo, s_hi, acc);
   const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
   *reinterpret_cast<float4*>(approx_out + ((size_t)map * kDb + bi) * (size_t)m * m + (size_t)(oy0 + r) * m + ox0 + c0) =
       make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
-static_assert(kInSize % 4 == 0 && (kRSmax * kPlo) % 4 == 0 && kPlo % 4 == 0, "float4 rows of lo_s/hi_s");
-static size_t fast_analysis_smem() { return (size_t)(kInSize + 2 * kRSmax * kPlo) * sizeof(float); }
+static_assert((kInSize + 2 * kRSmax * kPlo) % 4 == 0 && kStage % 4 == 0, "16-byte aligned stage buffers");
+static size_t fast_analysis_smem() { return (size_t)kAnaFloats * sizeof(float) + 16; }
 
 static size_t analysis_smem(int TO) {
   const int RS = 2 * TO + kMaxTaps - 2;
@@ -536,12 +666,12 @@ cudaError_t configure_kernels() {
   e = cudaFuncSetAttribute((const void*)k_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)synthesis_smem(32));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute((const void*)k_ana_l1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)fast_analysis_smem());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute((const void*)k_ana_lv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)fast_analysis_smem());
-  if (e != cudaSuccess) return e;
+  for (const void* f : {(const void*)k_ana_l1, (const void*)k_ana_lv}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_analysis_smem());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
   return configure_nufft_kernels();
 }
 
@@ -567,11 +697,11 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
     if (hm >= kTO && l == 1) {
       dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
       k_ana_l1<<<grid, 256, fast_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[(l - 1) & 1], mode, scale,
-                                                              gamma, delta);
+                                                              gamma, delta, h->dev_flags);
     } else if (hm >= kTO) {
       dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
       k_ana_lv<<<grid, 256, fast_analysis_smem(), h->stream>>>(in, m, n, l == L, coef, thr, buf[(l - 1) & 1], mode,
-                                                              scale, gamma, delta);
+                                                              scale, gamma, delta, h->dev_flags);
     } else {
       dim3 grid((hm / TO) * (hm / TO), kDb, 4);
       k_analysis<<<grid, 256, analysis_smem(TO), h->stream>>>(in, in_map, in_basis, m, TO, n, l == L, coef, thr,
