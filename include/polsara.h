@@ -199,6 +199,28 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms);
 /* Number of kernel launches in one iteration of the handle's current mode. */
 int32_t ps_kernels_per_iteration(const ps_handle* h);
 
+/* Allocation-free variant of ps_apply_psi: S = Psi A (Section 4.1 synthesis) for
+ * callers that cannot call cudaMalloc, such as code whose device memory is all
+ * owned by another allocator (a framework's caching allocator or a fixed
+ * pre-reserved pool) or that must not risk an allocation failing or stalling
+ * mid-run. The paper has no counterpart of this entry point.
+ *   A       device pointer, 4 x 9 x n*n floats in the coefficient layout
+ *   S       device pointer, 4 x n*n floats (output)
+ *   n       power of two, 16 <= n <= 256 (the limit of the static scratch)
+ *   levels  n divisible by 2^levels
+ *   cuda_stream  cudaStream_t to launch on (NULL: the legacy default stream)
+ * Needs no handle and allocates nothing: the per-level scratch is a file-scope
+ * device array of 2 x 32 x 128^2 floats (4 MiB) that every GPU loading the library
+ * holds until process exit. The first call on a device (with that device current)
+ * looks up the array's device address and uploads the filter taps; make that first
+ * call before capturing a stream. All calls share the one array and leave their
+ * intermediate values in it; it needs no clearing, but calls that overlap on the
+ * GPU (different streams, or different host threads on the same device) race on it
+ * and must be serialised by the caller. Pointers must be 16-byte aligned; sizes
+ * beyond the limit return PS_EINVAL with a message in ps_last_error(NULL).
+ * Asynchronous: the result is ready when the stream is synchronised. */
+ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, int32_t levels, void* cuda_stream);
+
 /* Synchronise the handle's stream; reports a pending CUDA error. */
 ps_status ps_synchronize(ps_handle* h);
 

@@ -73,6 +73,7 @@ _SIGS = {
     "ps_apply_psi_adjoint": (_I32, [_H, _P, _P, _I32]),
     "ps_apply_psi": (_I32, [_H, _P, _P, _I32]),
     "ps_wavelet_filters": (_I32, [_P]),
+    "ps_apply_psi_static": (_I32, [_P, _P, _I32, _I32, _P]),
     "ps_profile_stages": (_I32, [_H, _I32, _P]),
     "ps_kernels_per_iteration": (_I32, [_H]),
     "ps_synchronize": (_I32, [_H]),
@@ -257,6 +258,16 @@ def ps_apply_psi_adjoint(h, S, A) -> None:
 
 def ps_apply_psi(h, A, S) -> None:
     _op("ps_apply_psi", h, A, S, np.float32, np.float32)
+
+
+def ps_apply_psi_static(A, S, n: int, levels: int, stream=None) -> None:
+    """Allocation-free Psi A; A and S must be CUDA tensors (device pointers)."""
+    pa, da, ka = _arg(A, np.float32)
+    ps_, ds, ks = _arg(S, np.float32, writable=True)
+    if not (da and ds):
+        raise ValueError("ps_apply_psi_static takes device tensors only")
+    st = ctypes.c_void_p(int(stream)) if stream else None
+    _check(None, lib().ps_apply_psi_static(pa, ps_, int(n), int(levels), st))
 
 
 def ps_wavelet_filters() -> np.ndarray:

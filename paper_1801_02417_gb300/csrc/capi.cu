@@ -33,6 +33,10 @@ cudaError_t configure_kernels();
 
 static std::string g_create_error;
 
+namespace ps {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace ps
+
 static ps_status fail(Handle* h, ps_status st, const std::string& msg) {
   if (h) h->err = msg;
   else g_create_error = msg;

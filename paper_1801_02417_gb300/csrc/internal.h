@@ -102,6 +102,9 @@ struct Handle {
   int graph_mode = -1;
 };
 
+// Message returned by ps_last_error(NULL) (calls without a handle).
+void set_global_error(const std::string& msg);
+
 // Host-side constants.
 void daubechies_filters(double h[kDb][kMaxTaps]);          // db1..db8 scaling filters
 double es_beta(int W);

@@ -15,6 +15,9 @@
 // sums the eight bases and the Dirac part in registers and writes Psi A once.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <string>
+
 #include "internal.h"
 
 namespace ps {
@@ -711,10 +714,11 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
   return cudaGetLastError();
 }
 
-cudaError_t sara_synthesis(Handle* h, const float* coef, float* out) {
-  const int n = h->n, L = h->L;
+// Psi A on `stream` with `approx` as the per-level approximation scratch
+// (2 x 32 x (n/2)^2 floats).
+static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx) {
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
-  float* buf[2] = {h->approx, h->approx + quarter};
+  float* buf[2] = {approx, approx + quarter};
   for (int l = L; l >= 1; --l) {
     const int m = n >> (l - 1);
     const int TI = m < 32 ? m : 32;
@@ -722,15 +726,84 @@ cudaError_t sara_synthesis(Handle* h, const float* coef, float* out) {
     const float* ain = (l == L) ? nullptr : buf[l & 1];
     float* aout = (l == 1) ? nullptr : buf[(l - 1) & 1];
     if (m >= kTI && l == 1) {
-      k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, h->stream>>>(coef, ain, l == L, n, out);
+      k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, stream>>>(coef, ain, l == L, n, out);
     } else if (m >= kTI) {
-      k_syn_lv<<<dim3(tiles, kDb, 4), 256, 0, h->stream>>>(coef, ain, l == L, m, n, aout);
+      k_syn_lv<<<dim3(tiles, kDb, 4), 256, 0, stream>>>(coef, ain, l == L, m, n, aout);
     } else {
       dim3 grid(tiles, l == 1 ? 1 : kDb, 4);
-      k_synthesis<<<grid, 256, synthesis_smem(TI), h->stream>>>(coef, ain, l == L, m, TI, n, l == 1, aout, out);
+      k_synthesis<<<grid, 256, synthesis_smem(TI), stream>>>(coef, ain, l == L, m, TI, n, l == 1, aout, out);
     }
   }
   return cudaGetLastError();
 }
+
+cudaError_t sara_synthesis(Handle* h, const float* coef, float* out) {
+  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free synthesis (ps_apply_psi_static). Its level scratch lives in
+// this file-scope device array, sized for images up to kStaticMaxN; every GPU
+// that loads the library holds it until the process exits.
+constexpr int kStaticMaxN = 256;
+constexpr size_t kStaticScratchFloats = 2ull * kDb * 4 * (kStaticMaxN / 2) * (kStaticMaxN / 2);   // 4 MiB
+static __device__ __align__(256) float g_static_scratch[kStaticScratchFloats];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static float* g_static_ptr[kMaxDevices] = {};    // device address of g_static_scratch, per device
+
+}  // namespace ps
+
+#pragma GCC visibility push(default)
+extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, int32_t levels, void* cuda_stream) {
+  using namespace ps;
+  auto bad = [](const std::string& m) {
+    set_global_error("apply_psi_static: " + m);
+    return PS_EINVAL;
+  };
+  if (n < 16 || n > kStaticMaxN || (n & (n - 1)) != 0)
+    return bad("n must be a power of two in [16, " + std::to_string(kStaticMaxN) + "] (static scratch limit)");
+  if (levels < 1 || (n % (1 << levels)) != 0) return bad("levels must satisfy n divisible by 2^levels");
+  if (!A || !S || ((uintptr_t)A & 15u) || ((uintptr_t)S & 15u))
+    return bad("A and S must be non-null, 16-byte aligned device pointers");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_global_error(std::string("apply_psi_static: no usable current device: ") + cudaGetErrorString(e));
+    return PS_ECUDA;
+  }
+  float* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      // Set-up on this device, once: the scratch's device address and the filter taps.
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess) {
+        set_global_error(std::string("apply_psi_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return PS_ECUDA;
+      }
+      double filt[kDb][kMaxTaps];
+      daubechies_filters(filt);
+      e = upload_filters(filt);
+      if (e != cudaSuccess) {
+        set_global_error(std::string("apply_psi_static: filter upload: ") + cudaGetErrorString(e));
+        return PS_ECUDA;
+      }
+      g_static_ptr[dev] = static_cast<float*>(p);
+    }
+    scratch = g_static_ptr[dev];
+  }
+  e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("apply_psi_static: launch: ") + cudaGetErrorString(e));
+    return PS_ECUDA;
+  }
+  return PS_OK;
+}
+#pragma GCC visibility pop
+
+namespace ps {
 
 }  // namespace ps
