@@ -94,6 +94,20 @@ def phi_adjoint(B: np.ndarray, uv: np.ndarray, w: np.ndarray, n: int) -> np.ndar
     return np.real(G)
 
 
+def phi_adjoint_at(B: np.ndarray, uv: np.ndarray, w: np.ndarray, n: int, pixels: np.ndarray) -> np.ndarray:
+    """phi^dagger(B) at selected pixels only: (4, P) for pixels (P, 2) given as (p, q).
+
+    Direct sum over the rows: Re sum_m exp(+i (omega_u,m x + omega_v,m y)) w_m [B L^H]_{m, s}.
+    """
+    X = B @ np.conj(L_MIX).T                                   # (M, 4) columns per Stokes map
+    out = np.empty((4, len(pixels)))
+    for i, (p, q) in enumerate(pixels):
+        x, y = q - n / 2, p - n / 2
+        e = np.exp(1j * (uv[:, 0] * x + uv[:, 1] * y)) * w
+        out[:, i] = np.real(e @ X)
+    return out
+
+
 def phi_dense(uv: np.ndarray, w: np.ndarray, n: int) -> np.ndarray:
     """Dense real matrix of phi acting on vec(S) (4N reals) -> real/imag parts of vec(Y) (8M).
 

@@ -1,0 +1,116 @@
+"""Parity at the benchmark's full size: 1024 x 1024 4-Stokes, 2,000,000 rows, 32 blocks, 6 levels.
+
+The oracle cannot run whole iterations at this size (its direct DFT costs
+~8e12 complex MACs per phi), so outputs are compared where the oracle can
+compute them one by one: phi on sampled rows, phi^dagger on sampled pixels, the
+SARA transforms on whole maps, and the per-pixel primal/epigraph step of one
+iteration at sampled pixels. Same tolerances as the small-size parity tests.
+"""
+import numpy as np
+import pytest
+
+from oracle import measurement as meas
+from oracle import primal_dual as opd
+from oracle import prox
+from oracle import wavelets as wav
+from paper_1801_02417_gb300 import binding as B
+from paper_1801_02417_gb300 import inputs
+from paper_1801_02417_gb300.solver import PolarizedSARA
+
+pytestmark = pytest.mark.gpu
+
+WL = inputs.WORKLOADS["img1024_m2m"]
+
+
+@pytest.fixture(scope="module")
+def big():
+    from paper_1801_02417_gb300 import _build
+    _build.build_library()
+    uv = inputs.uv_coverage(WL)
+    w = inputs.visibility_weights(WL.M, WL.seed, 0.2).astype(np.float32)
+    truth = inputs.stokes_source(WL.n, WL.seed, WL.n_compact).astype(np.float32)
+    rng = np.random.default_rng(5)
+    Y = (rng.normal(size=(WL.M, 4)) + 1j * rng.normal(size=(WL.M, 4))).astype(np.complex64)
+    off = inputs.block_offsets(WL.M, WL.nblocks)
+    eps = np.full(WL.nblocks, 1e3)
+    s = PolarizedSARA(WL.n, WL.levels)
+    s.set_measurements(uv, Y, w, off, eps)
+    yield {"s": s, "uv": uv, "w": w, "truth": truth, "Y": Y, "off": off, "eps": eps, "rng": rng}
+    s.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def test_phi_on_sampled_rows(big):
+    s, uv, w = big["s"], big["uv"], big["w"]
+    out = np.empty((WL.M, 4), np.complex64)
+    B.ps_apply_phi(s.h, big["truth"], out)
+    rows = np.sort(big["rng"].choice(WL.M, size=96, replace=False))
+    ref = meas.phi(big["truth"].astype(np.float64), uv[rows], w[rows].astype(np.float64))
+    assert _rel(out[rows], ref) <= 1e-5
+
+
+def test_phi_adjoint_on_sampled_pixels(big):
+    s, uv, w, Y = big["s"], big["uv"], big["w"], big["Y"]
+    img = np.empty((4, WL.n, WL.n), np.float32)
+    B.ps_apply_phi_adjoint(s.h, Y, img)
+    pix = np.stack([big["rng"].integers(0, WL.n, 12), big["rng"].integers(0, WL.n, 12)], axis=1)
+    pix = np.concatenate([pix, [[0, 0], [WL.n - 1, WL.n - 1], [WL.n // 2, WL.n // 2]]])
+    ref = meas.phi_adjoint_at(Y.astype(np.complex128), uv, w.astype(np.float64), WL.n, pix)
+    got = img[:, pix[:, 0], pix[:, 1]]
+    assert _rel(got, ref) <= 1e-5
+
+
+def test_sara_transforms_full_maps(big):
+    s = big["s"]
+    S = big["truth"]
+    A = np.empty((4, 9, WL.n, WL.n), np.float32)
+    B.ps_apply_psi_adjoint(s.h, S, A)
+    ref = wav.psi_adjoint(S[:1].astype(np.float64), WL.levels)[0]
+    assert _rel(A[0], ref) <= 1e-6
+    back = np.empty((4, WL.n, WL.n), np.float32)
+    B.ps_apply_psi(s.h, A, back)
+    ref_back = wav.psi(A[2:3].astype(np.float64), WL.levels)[0]
+    assert _rel(back[2], ref_back) <= 1e-6
+
+
+def test_one_iteration_per_pixel_step_at_sampled_pixels(big):
+    """S', Z', C', D' of one iteration at sampled pixels, from the oracle's Psi A and phi^dagger B there."""
+    s, uv, w = big["s"], big["uv"], big["w"]
+    n, M = WL.n, WL.M
+    rng = np.random.default_rng(11)
+    st = {"S": (0.1 * rng.normal(size=(4, n, n))).astype(np.float32),
+          "Z": (0.1 * rng.normal(size=(2, n, n))).astype(np.float32),
+          "A": (0.01 * rng.normal(size=(4, 9, n, n))).astype(np.float32),
+          "B": (1e-3 * (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4)))).astype(np.complex64),
+          "C": (0.1 * rng.normal(size=(4, n, n))).astype(np.float32),
+          "D": (0.1 * rng.normal(size=(2, n, n))).astype(np.float32)}
+    s.set_sara_weights(None, 0.05)
+    s.set_state(st)
+    s.set_mode(B.PS_POLARIZED)
+    par = s.params()
+    s.pd_iterate(1)
+    got = s.get_state()
+    pix = np.stack([rng.integers(0, n, 10), rng.integers(0, n, 10)], axis=1)
+    # Oracle pieces at those pixels: Psi A (whole maps, then sampled) and phi^dagger B.
+    PsiA = wav.psi(st["A"].astype(np.float64), WL.levels)[:, pix[:, 0], pix[:, 1]]
+    AdjB = meas.phi_adjoint_at(st["B"].astype(np.complex128), uv, w.astype(np.float64), n, pix)
+    S0 = st["S"][:, pix[:, 0], pix[:, 1]].astype(np.float64)
+    C0 = st["C"][:, pix[:, 0], pix[:, 1]].astype(np.float64)
+    Z0 = st["Z"][:, pix[:, 0], pix[:, 1]].astype(np.float64)
+    D0 = st["D"][:, pix[:, 0], pix[:, 1]].astype(np.float64)
+    tau, r3 = par["tau"], par["rho3"]
+    S1 = prox.proj_U(S0 - tau * (PsiA + AdjB + C0))
+    Z1 = prox.proj_V(Z0 - tau * D0)
+    Sb, Zb = 2 * S1 - S0, 2 * Z1 - Z0
+    Ct, Dt = C0 + r3 * Sb, D0 + r3 * Zb
+    c1, d1 = prox.proj_E1(Ct[0] / r3, Dt[0] / r3)
+    R2, d2 = prox.proj_E2(Ct[1:4] / r3, Dt[1] / r3)
+    C1 = np.concatenate([(Ct[0] - r3 * c1)[None], Ct[1:4] - r3 * R2])
+    D1 = np.stack([Dt[0] - r3 * d1, Dt[1] - r3 * d2])
+    assert _rel(got["S"][:, pix[:, 0], pix[:, 1]], S1) <= 2e-5
+    assert _rel(got["Z"][:, pix[:, 0], pix[:, 1]], Z1) <= 2e-5
+    assert _rel(got["C"][:, pix[:, 0], pix[:, 1]], C1) <= 2e-5
+    assert _rel(got["D"][:, pix[:, 0], pix[:, 1]], D1) <= 2e-5

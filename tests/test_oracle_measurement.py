@@ -112,3 +112,12 @@ def test_chi2_epsilon_two_sigma_coverage():
     assert 0.955 <= frac <= 0.995, frac
     # Mean of ||E||^2 is 8M sigma^2/2 = 4 M sigma^2.
     assert abs(eps ** 2 - (4 * M * sigma ** 2 + 2 * math.sqrt(16 * M) * sigma ** 2 / 2)) < 1e-9
+
+
+def test_pixel_sampled_adjoint_matches_full_adjoint():
+    rng, uv, w = _rand_problem(n=10, M=40, seed=6)
+    B = rng.normal(size=(40, 4)) + 1j * rng.normal(size=(40, 4))
+    full = meas.phi_adjoint(B, uv, w, 10)
+    pix = np.array([[0, 0], [3, 7], [9, 9], [5, 5]])
+    got = meas.phi_adjoint_at(B, uv, w, 10, pix)
+    assert np.allclose(got, full[:, pix[:, 0], pix[:, 1]], atol=1e-12)
