@@ -160,91 +160,130 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // Interpolate the packed spectra at +u and -u, unpack the four Stokes spectra,
-// mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. Rows are stored in
-// tap-centre-cell order, so the lanes of a warp mostly read the same spectrum
-// cells (L1 broadcasts) while the row data streams sequentially. Per-block sums of
-// ||B~/rho2 - Y||^2 (DUAL) or ||Y - phi X||^2 (RESID) are combined per warp over
-// lanes of the same block, then through shared-memory FP64 accumulators into
-// global FP64 atomics (block_sum, cleared by the caller).
+// mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. One CTA per gridding
+// work item (rows whose tap centres lie in one kGridTile^2 tile): the spectrum
+// cells every tap of the item can touch at +u, and the mirrored cells at -u, are
+// staged in shared memory once; each thread then interpolates one row with taps at
+// fixed offsets from its centre. Per-block sums of ||B~/rho2 - Y||^2 (DUAL) or
+// ||Y - phi X||^2 (RESID) are combined per warp over lanes of the same block, then
+// through shared-memory FP64 accumulators into global FP64 atomics (block_sum,
+// cleared by the caller).
 template <int W>
-__global__ void __launch_bounds__(256, 3) k_degrid(
-    const float4* __restrict__ rec, const float4* __restrict__ G, int Wd, int off, int full, int K, float beta,
-    int mode, float2* __restrict__ R, const float2* __restrict__ Yv, const float* __restrict__ cb, float inv_rho2,
-    const uint16_t* __restrict__ vblk, int M, int nblocks, double* __restrict__ block_sum, float2* __restrict__ out) {
-  extern __shared__ double bsum[];
+__global__ void __launch_bounds__(256) k_degrid(
+    const GridItem* __restrict__ items, const float4* __restrict__ rec, const float4* __restrict__ G, int Wd,
+    int off, int full, int K, float beta, int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
+    const float* __restrict__ cb, float inv_rho2, const uint16_t* __restrict__ vblk, int nblocks,
+    double* __restrict__ block_sum, float2* __restrict__ out) {
+  constexpr int TS = kGridTile;
+  constexpr int SS = TS + W - 1;
   constexpr int hw = W / 2;
+  extern __shared__ float4 smd[];
+  float4* Gp = smd;                 // +u cells: grid rows/cols ty*TS - hw + [0, SS)
+  float4* Gn = smd + SS * SS;       // -u cells: mirrored rows/cols -(ty*TS + TS-1) - hw + [0, SS)
+  double* bsum = reinterpret_cast<double*>(smd + 2 * SS * SS);
+  const GridItem it = items[blockIdx.x];
   const bool reduce = (mode != DEG_APPLY);
   if (reduce)
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) bsum[b] = 0.0;
-  __syncthreads();
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  int blk = -1;
-  double e2 = 0.0;
-  if (m < M) {
-    float fx, fy, w;
-    int cx, cy;
-    unpack_rec(rec[m], fx, fy, w, cx, cy);
-    float wx[W], wy[W];
-    es_weights<W>(fx, beta, wx);
-    es_weights<W>(fy, beta, wy);
-    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
-#pragma unroll
-    for (int jy = 0; jy < W; ++jy) {
-      const float4* rowp = G + (size_t)gidx(cy - hw + jy, off, full, K) * Wd;
-      const float4* rown = G + (size_t)gidx(-cy - hw + jy, off, full, K) * Wd;
-      float4 ap = make_float4(0.f, 0.f, 0.f, 0.f), an = ap;
-#pragma unroll
-      for (int jx = 0; jx < W; ++jx) {
-        ap = f4fma(wx[jx], __ldg(rowp + gidx(cx - hw + jx, off, full, K)), ap);
-        an = f4fma(wx[W - 1 - jx], __ldg(rown + gidx(-cx - hw + jx, off, full, K)), an);
-      }
-      sp = f4fma(wy[jy], ap, sp);
-      sn = f4fma(wy[W - 1 - jy], an, sn);
-    }
-    // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
-    const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
-    const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
-    float4 v01 = make_float4(w * (FIr + FQr), w * (FIi + FQi), w * sp.z, w * sp.w);   // RR, RL = G2(u)
-    float4 v23 = make_float4(w * sn.z, -w * sn.w, w * (FIr - FQr), w * (FIi - FQi));  // LR = conj G2(-u), LL
-    float4* R4 = reinterpret_cast<float4*>(R);
-    const float4* Y4 = reinterpret_cast<const float4*>(Yv);
-    if (mode == DEG_APPLY) {
-      float4* o4 = reinterpret_cast<float4*>(out);
-      o4[2 * (size_t)m] = v01;
-      o4[2 * (size_t)m + 1] = v23;
+  // Grid frequency (k) of local row 0: +u region starts at tile origin - hw; the -u region
+  // holds frequencies -(centre) - hw + j for every centre of the tile.
+  const int ky0 = it.ty * TS - hw - (full ? 0 : off), kx0 = it.tx * TS - hw - (full ? 0 : off);
+  const int nky0 = -(it.ty * TS + TS - 1 - (full ? 0 : off)) - hw, nkx0 = -(it.tx * TS + TS - 1 - (full ? 0 : off)) - hw;
+  for (int i = threadIdx.x; i < SS * SS; i += blockDim.x) {
+    const int ly = i / SS, lx = i - (i / SS) * SS;
+    int py = ky0 + ly, px = kx0 + lx, ny = nky0 + ly, nx = nkx0 + lx;
+    float4 vp = make_float4(0.f, 0.f, 0.f, 0.f), vn = vp;
+    if (full) {
+      vp = G[(size_t)(py & (K - 1)) * Wd + (px & (K - 1))];
+      vn = G[(size_t)(ny & (K - 1)) * Wd + (nx & (K - 1))];
     } else {
-      blk = vblk[m];
-      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
-      if (mode == DEG_DUAL) {
-        const float cs = cb[blk] * inv_rho2;
-        const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
-        v01 = f4sub(f4fma(cs, r0, v01), y0);
-        v23 = f4sub(f4fma(cs, r1, v23), y1);
-        R4[2 * (size_t)m] = v01;
-        R4[2 * (size_t)m + 1] = v23;
-      } else {
-        v01 = f4sub(y0, v01);
-        v23 = f4sub(y1, v23);
-        if (out) {
-          float4* o4 = reinterpret_cast<float4*>(out);
-          o4[2 * (size_t)m] = v01;
-          o4[2 * (size_t)m + 1] = v23;
+      py += off; px += off; ny += off; nx += off;
+      if (py >= 0 && py < Wd && px >= 0 && px < Wd) vp = G[(size_t)py * Wd + px];
+      if (ny >= 0 && ny < Wd && nx >= 0 && nx < Wd) vn = G[(size_t)ny * Wd + nx];
+    }
+    Gp[i] = vp;
+    Gn[i] = vn;
+  }
+  __syncthreads();
+  float4* R4 = reinterpret_cast<float4*>(R);
+  const float4* Y4 = reinterpret_cast<const float4*>(Yv);
+  for (int base = it.vstart; base < it.vend; base += blockDim.x) {
+    const int m = base + threadIdx.x;
+    int blk = -1;
+    double e2 = 0.0;
+    if (m < it.vend) {
+      float fx, fy, w;
+      int cx, cy;
+      unpack_rec(rec[m], fx, fy, w, cx, cy);
+      float wx[W], wy[W];
+      es_weights<W>(fx, beta, wx);
+      es_weights<W>(fy, beta, wy);
+      // Local centre within the tile (tap j of +u at local j + lc; of -u at local (TS-1-lc) + j).
+      const int lcy = gidx(cy, off, full, K) - it.ty * TS, lcx = gidx(cx, off, full, K) - it.tx * TS;
+      const float4* gp = Gp + lcy * SS + lcx;
+      const float4* gn = Gn + (TS - 1 - lcy) * SS + (TS - 1 - lcx);
+      float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
+#pragma unroll
+      for (int jy = 0; jy < W; ++jy) {
+        float4 ap = make_float4(0.f, 0.f, 0.f, 0.f), an = ap;
+#pragma unroll
+        for (int jx = 0; jx < W; ++jx) {
+          ap = f4fma(wx[jx], gp[jy * SS + jx], ap);
+          an = f4fma(wx[W - 1 - jx], gn[jy * SS + jx], an);
         }
+        sp = f4fma(wy[jy], ap, sp);
+        sn = f4fma(wy[W - 1 - jy], an, sn);
       }
-      e2 = (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
-           (double)(v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
+      // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
+      const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
+      const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
+      float4 v01 = make_float4(w * (FIr + FQr), w * (FIi + FQi), w * sp.z, w * sp.w);   // RR, RL = G2(u)
+      float4 v23 = make_float4(w * sn.z, -w * sn.w, w * (FIr - FQr), w * (FIi - FQi));  // LR = conj G2(-u), LL
+      if (mode == DEG_APPLY) {
+        float4* o4 = reinterpret_cast<float4*>(out);
+        o4[2 * (size_t)m] = v01;
+        o4[2 * (size_t)m + 1] = v23;
+      } else {
+        blk = vblk[m];
+        const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
+        if (mode == DEG_DUAL) {
+          const float cs = cb[blk] * inv_rho2;
+          const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
+          v01 = f4sub(f4fma(cs, r0, v01), y0);
+          v23 = f4sub(f4fma(cs, r1, v23), y1);
+          R4[2 * (size_t)m] = v01;
+          R4[2 * (size_t)m + 1] = v23;
+        } else {
+          v01 = f4sub(y0, v01);
+          v23 = f4sub(y1, v23);
+          if (out) {
+            float4* o4 = reinterpret_cast<float4*>(out);
+            o4[2 * (size_t)m] = v01;
+            o4[2 * (size_t)m + 1] = v23;
+          }
+        }
+        e2 = (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
+             (double)(v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
+      }
+    }
+    if (reduce) {
+      // Lanes holding the same block add their terms; the lowest such lane updates shared memory.
+      const unsigned peers = __match_any_sync(0xffffffffu, blk);
+      double sum = 0.0;
+      for (unsigned p = peers; p; p &= p - 1) sum += __shfl_sync(peers, e2, __ffs(p) - 1);
+      if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bsum[blk], sum);
     }
   }
   if (reduce) {
-    // Lanes holding the same block add their terms; the lowest such lane updates shared memory.
-    const unsigned peers = __match_any_sync(0xffffffffu, blk);
-    double sum = 0.0;
-    for (unsigned p = peers; p; p &= p - 1) sum += __shfl_sync(peers, e2, __ffs(p) - 1);
-    if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bsum[blk], sum);
     __syncthreads();
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
       if (bsum[b] != 0.0) atomicAdd(&block_sum[b], bsum[b]);
   }
+}
+
+template <int W>
+static constexpr size_t degrid_smem_tiles() {
+  return (size_t)2 * (kGridTile + W - 1) * (kGridTile + W - 1) * sizeof(float4);
 }
 
 // Per-block factor c_b of B = c_b R after the l2-ball step (Algorithm 1 step 8):
@@ -466,9 +505,9 @@ cudaError_t configure_nufft_kernels() {
   if ((e = set_smem((const void*)k_grid<7>, grid_smem<7>())) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_grid<9>, grid_smem<9>())) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
-  if ((e = set_smem((const void*)k_degrid<5>, 2048 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_degrid<7>, 2048 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_degrid<9>, 2048 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_degrid<5>, degrid_smem_tiles<5>() + 2048 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_degrid<7>, degrid_smem_tiles<7>() + 2048 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_degrid<9>, degrid_smem_tiles<9>() + 2048 * sizeof(double))) != cudaSuccess) return e;
   return set_smem((const void*)k_adj_cols, sm2);
 }
 
@@ -483,10 +522,10 @@ cudaError_t nufft_forward_grid(Handle* h, const float* X) {
 template <int W>
 static void launch_degrid(Handle* h, int mode, float2* out) {
   const GridGeom& g = h->g;
-  const size_t sm = (size_t)h->nblocks * sizeof(double);
-  k_degrid<W><<<(h->M + 255) / 256, 256, sm, h->stream>>>(h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode, h->R,
-                                                          h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->M,
-                                                          h->nblocks, h->block_sum, out);
+  const size_t sm = degrid_smem_tiles<W>() + (size_t)h->nblocks * sizeof(double);
+  k_degrid<W><<<h->nitems, 256, sm, h->stream>>>(h->items, h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode, h->R,
+                                                 h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->nblocks,
+                                                 h->block_sum, out);
 }
 
 cudaError_t nufft_degrid(Handle* h, int mode, float2* out) {

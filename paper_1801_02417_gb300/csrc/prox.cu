@@ -53,6 +53,17 @@ __device__ __forceinline__ void proj_e2(float r1, float r2, float r3, float d, f
   }
 }
 
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void setc(float4& v, int k, float x) {
+  if (k == 0) v.x = x;
+  else if (k == 1) v.y = x;
+  else if (k == 2) v.z = x;
+  else v.w = x;
+}
+
+// One thread = four consecutive pixels (float4 on every plane).
 __global__ void __launch_bounds__(kSweepThreads) k_primal(
     int N, int mode, float tau, float rho1, float rho3, float* __restrict__ S, float* __restrict__ Z,
     float* __restrict__ C, float* __restrict__ D, const float* __restrict__ PsiA, const float* __restrict__ Adj,
@@ -60,61 +71,84 @@ __global__ void __launch_bounds__(kSweepThreads) k_primal(
     double* __restrict__ part) {
   __shared__ double sh[kSweepThreads / 32][8];
   float dss[4] = {0.f, 0.f, 0.f, 0.f}, ss[4] = {0.f, 0.f, 0.f, 0.f};
-  const int base = blockIdx.x * (kSweepThreads * kSweepPix) + threadIdx.x;
+  const int i = 4 * (blockIdx.x * kSweepThreads + threadIdx.x);
   const float inv_r3 = 1.0f / rho3;
   const float r1_3 = rho1 * (1.0f / 3.0f);
-#pragma unroll
-  for (int t = 0; t < kSweepPix; ++t) {
-    const int i = base + t * kSweepThreads;
-    if (i >= N) break;
-    float xb[4];
+  if (i < N) {
+    float4 xb[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const size_t o = (size_t)c * N + i;
-      float grad = Adj[o];
-      if (mode != PS_NNLS) grad += PsiA[o];
-      if (mode == PS_POLARIZED) grad += C[o];
-      const float so = S[o];
-      float sn = so - tau * grad;                       // step 3 (P_U: real already)
-      if (mode != PS_POLARIZED && c == 0) sn = fmaxf(sn, 0.f);   // P_U'
-      xb[c] = 2.f * sn - so;
-      dss[c] += (sn - so) * (sn - so);
-      ss[c] += so * so;
-      S[o] = sn;
-      Xb[o] = xb[c];
-      if (mode != PS_NNLS) {                            // Dirac part of steps 5-6
+      float4 g = ld4(Adj + o);
+      if (mode != PS_NNLS) {
+        const float4 p = ld4(PsiA + o);
+        g = make_float4(g.x + p.x, g.y + p.y, g.z + p.z, g.w + p.w);
+      }
+      if (mode == PS_POLARIZED) {
+        const float4 q = ld4(C + o);
+        g = make_float4(g.x + q.x, g.y + q.y, g.z + q.z, g.w + q.w);
+      }
+      const float4 so = ld4(S + o);
+      float4 sn = make_float4(so.x - tau * g.x, so.y - tau * g.y, so.z - tau * g.z, so.w - tau * g.w);   // step 3
+      if (mode != PS_POLARIZED && c == 0)                                                              // P_U'
+        sn = make_float4(fmaxf(sn.x, 0.f), fmaxf(sn.y, 0.f), fmaxf(sn.z, 0.f), fmaxf(sn.w, 0.f));
+      xb[c] = make_float4(2.f * sn.x - so.x, 2.f * sn.y - so.y, 2.f * sn.z - so.z, 2.f * sn.w - so.w);
+      dss[c] += (sn.x - so.x) * (sn.x - so.x) + (sn.y - so.y) * (sn.y - so.y) + (sn.z - so.z) * (sn.z - so.z) +
+                (sn.w - so.w) * (sn.w - so.w);
+      ss[c] += so.x * so.x + so.y * so.y + so.z * so.z + so.w * so.w;
+      st4(S + o, sn);
+      st4(Xb + o, xb[c]);
+      if (mode != PS_NNLS) {                                            // Dirac part of steps 5-6
         const size_t ao = (size_t)c * cstride + i;
-        const float t = T[ao];
-        A[ao] = fminf(fmaxf(fmaf(r1_3, xb[c], A[ao]), -t), t);
+        const float4 t = ld4(T + ao), a = ld4(A + ao);
+        st4(A + ao, make_float4(fminf(fmaxf(fmaf(r1_3, xb[c].x, a.x), -t.x), t.x),
+                                fminf(fmaxf(fmaf(r1_3, xb[c].y, a.y), -t.y), t.y),
+                                fminf(fmaxf(fmaf(r1_3, xb[c].z, a.z), -t.z), t.z),
+                                fminf(fmaxf(fmaf(r1_3, xb[c].w, a.w), -t.w), t.w)));
       }
     }
     if (mode == PS_POLARIZED) {
-      // Step 4: Z = P_V(Z - tau D).
-      const float z1o = Z[i], z2o = Z[(size_t)N + i];
-      float z1 = z1o - tau * D[i], z2 = z2o - tau * D[(size_t)N + i];
-      if (z1 + z2 > 0.f) {
-        const float a = 0.5f * (z1 - z2);
-        z2 = 0.5f * (z2 - z1);
-        z1 = a;
-      }
-      Z[i] = z1;
-      Z[(size_t)N + i] = z2;
-      const float zb1 = 2.f * z1 - z1o, zb2 = 2.f * z2 - z2o;
-      // Steps 9-12.
-      float ct[4];
+      const float4 z1o = ld4(Z + i), z2o = ld4(Z + (size_t)N + i);
+      const float4 d1o = ld4(D + i), d2o = ld4(D + (size_t)N + i);
+      float4 c0 = ld4(C + i), c1 = ld4(C + (size_t)N + i), c2 = ld4(C + 2 * (size_t)N + i),
+             c3 = ld4(C + 3 * (size_t)N + i);
+      float4 z1n, z2n, d1n, d2n;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) ct[c] = C[(size_t)c * N + i] + rho3 * xb[c];
-      const float dt1 = D[i] + rho3 * zb1, dt2 = D[(size_t)N + i] + rho3 * zb2;
-      float pc, pd;
-      proj_e1(ct[0] * inv_r3, dt1 * inv_r3, pc, pd);
-      C[i] = ct[0] - rho3 * pc;
-      D[i] = dt1 - rho3 * pd;
-      float p1, p2, p3, pd2;
-      proj_e2(ct[1] * inv_r3, ct[2] * inv_r3, ct[3] * inv_r3, dt2 * inv_r3, p1, p2, p3, pd2);
-      C[(size_t)N + i] = ct[1] - rho3 * p1;
-      C[2 * (size_t)N + i] = ct[2] - rho3 * p2;
-      C[3 * (size_t)N + i] = ct[3] - rho3 * p3;
-      D[(size_t)N + i] = dt2 - rho3 * pd2;
+      for (int k = 0; k < 4; ++k) {
+        // Step 4: Z = P_V(Z - tau D).
+        const float za = comp(z1o, k), zb = comp(z2o, k);
+        float z1 = za - tau * comp(d1o, k), z2 = zb - tau * comp(d2o, k);
+        if (z1 + z2 > 0.f) {
+          const float a = 0.5f * (z1 - z2);
+          z2 = 0.5f * (z2 - z1);
+          z1 = a;
+        }
+        setc(z1n, k, z1);
+        setc(z2n, k, z2);
+        const float zb1 = 2.f * z1 - za, zb2 = 2.f * z2 - zb;
+        // Steps 9-12.
+        const float ct0 = comp(c0, k) + rho3 * comp(xb[0], k), ct1 = comp(c1, k) + rho3 * comp(xb[1], k);
+        const float ct2 = comp(c2, k) + rho3 * comp(xb[2], k), ct3 = comp(c3, k) + rho3 * comp(xb[3], k);
+        const float dt1 = comp(d1o, k) + rho3 * zb1, dt2 = comp(d2o, k) + rho3 * zb2;
+        float pc, pd;
+        proj_e1(ct0 * inv_r3, dt1 * inv_r3, pc, pd);
+        setc(c0, k, ct0 - rho3 * pc);
+        setc(d1n, k, dt1 - rho3 * pd);
+        float p1, p2, p3, pd2;
+        proj_e2(ct1 * inv_r3, ct2 * inv_r3, ct3 * inv_r3, dt2 * inv_r3, p1, p2, p3, pd2);
+        setc(c1, k, ct1 - rho3 * p1);
+        setc(c2, k, ct2 - rho3 * p2);
+        setc(c3, k, ct3 - rho3 * p3);
+        setc(d2n, k, dt2 - rho3 * pd2);
+      }
+      st4(Z + i, z1n);
+      st4(Z + (size_t)N + i, z2n);
+      st4(D + i, d1n);
+      st4(D + (size_t)N + i, d2n);
+      st4(C + i, c0);
+      st4(C + (size_t)N + i, c1);
+      st4(C + 2 * (size_t)N + i, c2);
+      st4(C + 3 * (size_t)N + i, c3);
     }
   }
   // FP64 partials for the relative-change statistic.
