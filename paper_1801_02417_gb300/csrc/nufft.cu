@@ -129,7 +129,7 @@ __device__ __forceinline__ void es_weights(float f, float beta, float* wt) {
   for (int j = 0; j < W; ++j) {
     const float z = (f + (float)(hw - j)) * inv;
     const float s = 1.0f - z * z;
-    wt[j] = s > 0.f ? __expf(beta * (sqrtf(s) - 1.0f)) : 0.f;
+    wt[j] = s > 0.f ? __expf(beta * (s * rsqrtf(s) - 1.0f)) : 0.f;
   }
 }
 
@@ -301,35 +301,37 @@ __global__ void k_block_scale(const double* __restrict__ block_sum, const double
 // Gridding (adjoint of the interpolation), Alg. 1 step 3's phi^dagger.
 // Rows are stored sorted by tap-centre cell. One CTA owns a work item:
 // up to kGridItem visibilities whose centres lie in one kGridTile^2 tile.
-//  1. Each thread stages one visibility as a row of shared memory: the
-//     conj(L)-mixed values x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR,
-//     x_V = i (LR - RL) scaled by c_b w_m, then its W x and W y kernel weights.
+//  1. Each thread stages one visibility in shared memory: the conj(L)-mixed
+//     values x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL)
+//     scaled by c_b w_m (two float4), and its W x and W y kernel weights (planes
+//     with an odd stride, so lanes reading different taps hit different banks).
 //  2. Visibilities sharing a centre cell (a chunk of <= 32) touch the same W x W
 //     cells. One warp takes one chunk; lane l owns kernel cells l, l+32, ... and
-//     accumulates their 8 channels over the chunk in registers (the staged row is
-//     read as a broadcast), then adds them once to a shared-memory tile.
+//     accumulates their 8 channels over the chunk in registers (two rows per
+//     step, channel values read as broadcasts), then adds them once to a
+//     channel-planar shared-memory tile.
 //  3. The tile (with halo) is added to the global accumulator.
 // Channels are gridded at +u only; k_adj_cols forms the -u half by Hermitian
 // symmetrisation.
-template <int W>
-__host__ __device__ constexpr int grid_row() { return (8 + 2 * W + 3) / 4 * 4; }
+constexpr int kGridV = kGridItem + 1;   // odd stride of the staged per-row fields (conflict-free)
 
 template <int W>
 __global__ void __launch_bounds__(256) k_grid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
-    const float4* __restrict__ rec, const float2* __restrict__ vin,
-    const float* __restrict__ cb, int use_scale, int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
+    const float4* __restrict__ rec, const float2* __restrict__ vin, const float* __restrict__ cb, int use_scale,
+    int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
   constexpr int TS = kGridTile;
   constexpr int SS = TS + W - 1;
+  constexpr int NC = SS * SS;                    // cells of the tile with halo
   constexpr int hw = W / 2;
-  constexpr int V = kGridItem;
-  constexpr int P = grid_row<W>();
-  constexpr int CPL = (W * W + 31) / 32;          // kernel cells per lane
+  constexpr int CPL = (W * W + 31) / 32;         // kernel cells per lane
   extern __shared__ float4 smg[];
-  float* acc = reinterpret_cast<float*>(smg);   // SS*SS*8
-  float* st = acc + SS * SS * 8;                // V rows of P floats: x[8], wx[W], wy[W]
+  float4* x4 = smg;                              // kGridItem x 2: mixed, scaled channels of each row
+  float* acc = reinterpret_cast<float*>(smg + 2 * kGridItem);   // 8 planes of NC cells
+  float* wxs = acc + 8 * NC;                     // W planes of kGridV
+  float* wys = wxs + W * kGridV;                 // W planes of kGridV
   const GridItem it = items[blockIdx.x];
-  for (int i = threadIdx.x; i < SS * SS * 8; i += blockDim.x) acc[i] = 0.f;
+  for (int i = threadIdx.x; i < 8 * NC; i += blockDim.x) acc[i] = 0.f;
   const int nv = it.vend - it.vstart;
   const float4* v4 = reinterpret_cast<const float4*>(vin);
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
@@ -339,29 +341,31 @@ __global__ void __launch_bounds__(256) k_grid(
     unpack_rec(rec[idx], fx, fy, w, cx, cy);
     const float sc = (use_scale ? cb[vblk[idx]] : 1.0f) * w;
     const float4 b0 = v4[2 * (size_t)idx], b1 = v4[2 * (size_t)idx + 1];   // RR, RL | LR, LL
-    float* row = st + j * P;
-    *reinterpret_cast<float4*>(row) =
-        make_float4(sc * (b0.x + b1.z), sc * (b0.y + b1.w), sc * (b0.x - b1.z), sc * (b0.y - b1.w));
-    *reinterpret_cast<float4*>(row + 4) =
-        make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
+    // x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL).
+    x4[2 * j] = make_float4(sc * (b0.x + b1.z), sc * (b0.y + b1.w), sc * (b0.x - b1.z), sc * (b0.y - b1.w));
+    x4[2 * j + 1] = make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
     float wx[W], wy[W];
     es_weights<W>(fx, beta, wx);
     es_weights<W>(fy, beta, wy);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-      row[8 + k] = wx[k];
-      row[8 + W + k] = wy[k];
+      wxs[k * kGridV + j] = wx[k];
+      wys[k * kGridV + j] = wy[k];
     }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nc = it.cend - it.cstart;
-  int cjx[CPL], cjy[CPL];
+  const float* wxl[CPL];
+  const float* wyl[CPL];
+  int coff[CPL];
 #pragma unroll
   for (int q = 0; q < CPL; ++q) {
     const int cell = lane + 32 * q;
-    cjy[q] = cell < W * W ? cell / W : 0;
-    cjx[q] = cell < W * W ? cell - (cell / W) * W : 0;
+    const int jy = cell < W * W ? cell / W : 0, jx = cell < W * W ? cell - (cell / W) * W : 0;
+    wxl[q] = wxs + jx * kGridV;
+    wyl[q] = wys + jy * kGridV;
+    coff[q] = jy * SS + jx;
   }
   for (int c = warp; c < nc; c += nwarps) {
     const int pk = chunks[it.cstart + c];
@@ -371,34 +375,48 @@ __global__ void __launch_bounds__(256) k_grid(
     for (int q = 0; q < CPL; ++q)
 #pragma unroll
       for (int ch = 0; ch < 8; ++ch) a[q][ch] = 0.f;
-    for (int v = v0; v < v0 + cnt; ++v) {
-      const float* row = st + v * P;
-      const float4 x0 = *reinterpret_cast<const float4*>(row);
-      const float4 x1 = *reinterpret_cast<const float4*>(row + 4);
+    int v = v0;
+    for (; v + 1 < v0 + cnt; v += 2) {
+      const float4 x0 = x4[2 * v], x1 = x4[2 * v + 1], y0 = x4[2 * v + 2], y1 = x4[2 * v + 3];
 #pragma unroll
       for (int q = 0; q < CPL; ++q) {
-        const float k = row[8 + cjx[q]] * row[8 + W + cjy[q]];
-        a[q][0] = fmaf(k, x0.x, a[q][0]);
-        a[q][1] = fmaf(k, x0.y, a[q][1]);
-        a[q][2] = fmaf(k, x0.z, a[q][2]);
-        a[q][3] = fmaf(k, x0.w, a[q][3]);
-        a[q][4] = fmaf(k, x1.x, a[q][4]);
-        a[q][5] = fmaf(k, x1.y, a[q][5]);
-        a[q][6] = fmaf(k, x1.z, a[q][6]);
-        a[q][7] = fmaf(k, x1.w, a[q][7]);
+        const float k0 = wxl[q][v] * wyl[q][v], k1 = wxl[q][v + 1] * wyl[q][v + 1];
+        a[q][0] = fmaf(k1, y0.x, fmaf(k0, x0.x, a[q][0]));
+        a[q][1] = fmaf(k1, y0.y, fmaf(k0, x0.y, a[q][1]));
+        a[q][2] = fmaf(k1, y0.z, fmaf(k0, x0.z, a[q][2]));
+        a[q][3] = fmaf(k1, y0.w, fmaf(k0, x0.w, a[q][3]));
+        a[q][4] = fmaf(k1, y1.x, fmaf(k0, x1.x, a[q][4]));
+        a[q][5] = fmaf(k1, y1.y, fmaf(k0, x1.y, a[q][5]));
+        a[q][6] = fmaf(k1, y1.z, fmaf(k0, x1.z, a[q][6]));
+        a[q][7] = fmaf(k1, y1.w, fmaf(k0, x1.w, a[q][7]));
       }
     }
+    if (v < v0 + cnt) {
+      const float4 x0 = x4[2 * v], x1 = x4[2 * v + 1];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float k0 = wxl[q][v] * wyl[q][v];
+        a[q][0] = fmaf(k0, x0.x, a[q][0]);
+        a[q][1] = fmaf(k0, x0.y, a[q][1]);
+        a[q][2] = fmaf(k0, x0.z, a[q][2]);
+        a[q][3] = fmaf(k0, x0.w, a[q][3]);
+        a[q][4] = fmaf(k0, x1.x, a[q][4]);
+        a[q][5] = fmaf(k0, x1.y, a[q][5]);
+        a[q][6] = fmaf(k0, x1.z, a[q][6]);
+        a[q][7] = fmaf(k0, x1.w, a[q][7]);
+      }
+    }
+    const int cbase = ly * SS + lx;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
       if (lane + 32 * q < W * W) {
-        float* dst = acc + ((ly + cjy[q]) * SS + (lx + cjx[q])) * 8;
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) atomicAdd(dst + ch, a[q][ch]);
+        for (int ch = 0; ch < 8; ++ch) atomicAdd(acc + ch * NC + cbase + coff[q], a[q][ch]);
       }
     }
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < SS * SS; c += blockDim.x) {
+  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
     const int ly = c / SS, lx = c - (c / SS) * SS;
     int gy = it.ty * TS - hw + ly, gx = it.tx * TS - hw + lx;
     if (full) {
@@ -407,9 +425,8 @@ __global__ void __launch_bounds__(256) k_grid(
     } else if (gy < 0 || gy >= Wd || gx < 0 || gx >= Wd) {
       continue;
     }
-    const float* a = acc + c * 8;
-    const float4 lo = make_float4(a[0], a[1], a[2], a[3]);
-    const float4 hi = make_float4(a[4], a[5], a[6], a[7]);
+    const float4 lo = make_float4(acc[0 * NC + c], acc[1 * NC + c], acc[2 * NC + c], acc[3 * NC + c]);
+    const float4 hi = make_float4(acc[4 * NC + c], acc[5 * NC + c], acc[6 * NC + c], acc[7 * NC + c]);
     float4* dst = Acc + 2 * ((size_t)gy * Wd + gx);
     if (lo.x != 0.f || lo.y != 0.f || lo.z != 0.f || lo.w != 0.f) atomicAdd(dst, lo);
     if (hi.x != 0.f || hi.y != 0.f || hi.z != 0.f || hi.w != 0.f) atomicAdd(dst + 1, hi);
@@ -418,7 +435,8 @@ __global__ void __launch_bounds__(256) k_grid(
 
 template <int W>
 static constexpr size_t grid_smem() {
-  return (size_t)((kGridTile + W - 1) * (kGridTile + W - 1) * 8 + kGridItem * grid_row<W>()) * sizeof(float);
+  return (size_t)2 * kGridItem * sizeof(float4) +
+         (size_t)(8 * (kGridTile + W - 1) * (kGridTile + W - 1) + 2 * W * kGridV) * sizeof(float);
 }
 
 // Hermitian symmetrisation + inverse column FFTs for the column pair (kx, -kx).

@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
 // next basis' coefficients can be in flight (cp.async) while this one is filtered:
 //   syn_load     copies the four subband tiles (with the filter halo, periodic wrap);
 //   syn_compute  filters along y then x and adds to acc[4], this thread's outputs
-//                out[r][c0 .. c0+3] with r = tid / 8, c0 = 4 (tid % 8).
+//                out[r][c0 .. c0+3] with r = tid % 32, c0 = 4 (tid / 32).
 constexpr int kS4 = 4 * kCImax * kPc;            // one set of four subband tiles
 
 template <int LF>
@@ -547,7 +547,9 @@ __device__ __forceinline__ void syn_compute(const float* __restrict__ s4, float*
     }
   }
   __syncthreads();
-  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  // Along x: warp w owns output columns 4w .. 4w+3 of all 32 rows (row = lane), so the
+  // 32 lanes read 32 different rows at an odd pitch (no bank conflicts).
+  const int r = threadIdx.x & 31, c0 = (threadIdx.x >> 5) * 4;
 #pragma unroll
   for (int i = 0; i < half + 2; ++i) {
     const float vlo = s_lo[r * kPs + c0 / 2 + i], vhi = s_hi[r * kPs + c0 / 2 + i];
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(256, 3) k_syn_fine(const float* __restrict__ c
     syn_compute_dispatch(bi, s4b[bi & 1], s_lo, s_hi, acc);
     __syncthreads();
   }
-  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  const int r = threadIdx.x & 31, c0 = (threadIdx.x >> 5) * 4;
   const size_t o = (size_t)(oy0 + r) * n + ox0 + c0;
   const float4 d = *reinterpret_cast<const float4*>(coef + (size_t)map * kBases * n * n + o);
   const float k = 1.0f / 3.0f;
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(256, 4) k_syn_lv(const float* __restrict__ coe
   cp_async_wait<0>();
   __syncthreads();
   syn_compute_dispatch(bi, s4, s_lo, s_hi, acc);
-  const int r = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+  const int r = threadIdx.x & 31, c0 = (threadIdx.x >> 5) * 4;
   *reinterpret_cast<float4*>(approx_out + ((size_t)map * kDb + bi) * (size_t)m * m + (size_t)(oy0 + r) * m + ox0 + c0) =
       make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
