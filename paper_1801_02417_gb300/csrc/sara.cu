@@ -489,7 +489,14 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
 //   syn_load     copies the four subband tiles (with the filter halo, periodic wrap);
 //   syn_compute  filters along y then x and adds to acc[4], this thread's outputs
 //                out[r][c0 .. c0+3] with r = tid % 32, c0 = 4 (tid / 32).
-constexpr int kS4 = 4 * kCImax * kPc;            // one set of four subband tiles
+// Each subband tile is loaded as rows of 32 floats starting 8 columns left of the
+// tile's coefficient origin (16-byte aligned), covering every halo width.
+constexpr int kSRow = 36;                         // floats per staged row (16-byte aligned pitch)
+constexpr int kSTile = kCImax * kSRow;            // one subband tile
+constexpr int kS4 = 4 * kSTile;                   // one set of four subband tiles
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
 template <int LF>
 __device__ __forceinline__ void syn_load(const float* __restrict__ cb, const float* __restrict__ apx, int n, int m,
@@ -497,18 +504,18 @@ __device__ __forceinline__ void syn_load(const float* __restrict__ cb, const flo
   constexpr int half = LF / 2 - 1;
   constexpr int CI = kTI / 2 + half;
   const int hm = m >> 1;
-  float* s_ll = s4;
-  float* s_lh = s4 + kCImax * kPc;
-  float* s_hl = s_lh + kCImax * kPc;
-  float* s_hh = s_hl + kCImax * kPc;
-  const int ky0 = oy0 / 2 - half, kx0 = ox0 / 2 - half;
-  for (int i = threadIdx.x; i < CI * CI; i += blockDim.x) {
-    const int r = i / CI, c = i - r * CI;
-    const int Yk = wrap1(ky0 + r, hm), Xk = wrap1(kx0 + c, hm);
-    cp_async4(s_ll + r * kPc + c, apx ? apx + (size_t)Yk * hm + Xk : cb + (size_t)Yk * n + Xk);
-    cp_async4(s_hl + r * kPc + c, cb + (size_t)Yk * n + hm + Xk);
-    cp_async4(s_lh + r * kPc + c, cb + (size_t)(hm + Yk) * n + Xk);
-    cp_async4(s_hh + r * kPc + c, cb + (size_t)(hm + Yk) * n + hm + Xk);
+  const int ky0 = oy0 / 2 - half, kxa = ox0 / 2 - 8;     // kxa: 16-byte aligned start column
+  // CI rows x 8 chunks of 4 floats, for each of the four subbands (chunks never straddle the wrap).
+  for (int i = threadIdx.x; i < 4 * CI * 8; i += blockDim.x) {
+    const int sb = i / (CI * 8), rc = i - sb * (CI * 8);
+    const int r = rc >> 3, k = rc & 7;
+    const int Yk = wrap1(ky0 + r, hm), Xk = wrap1(kxa + 4 * k, hm);
+    const float* src;
+    if (sb == 0) src = apx ? apx + (size_t)Yk * hm + Xk : cb + (size_t)Yk * n + Xk;   // LL
+    else if (sb == 1) src = cb + (size_t)(hm + Yk) * n + Xk;                         // LH (x-low, y-high)
+    else if (sb == 2) src = cb + (size_t)Yk * n + hm + Xk;                           // HL (x-high, y-low)
+    else src = cb + (size_t)(hm + Yk) * n + hm + Xk;                                 // HH
+    cp_async16(s4 + sb * kSTile + r * kSRow + 4 * k, src);
   }
 }
 
@@ -518,10 +525,10 @@ __device__ __forceinline__ void syn_compute(const float* __restrict__ s4, float*
   constexpr int half = LF / 2 - 1;
   constexpr int CI = kTI / 2 + half;
   constexpr int b = LF / 2 - 1;
-  const float* s_ll = s4;
-  const float* s_lh = s4 + kCImax * kPc;
-  const float* s_hl = s_lh + kCImax * kPc;
-  const float* s_hh = s_hl + kCImax * kPc;
+  const float* s_ll = s4 + (8 - half);             // column c of the halo tile = staged column c + 8 - half
+  const float* s_lh = s4 + kSTile + (8 - half);
+  const float* s_hl = s4 + 2 * kSTile + (8 - half);
+  const float* s_hh = s4 + 3 * kSTile + (8 - half);
   // Along y: lo[r][c] = sum_{j = r mod 2} h[j] ll[(r - j)/2 + half][c] + g[j] lh[...]; coefficient
   // row r0/2 + i feeds output row r0 + t through tap j = t - 2 (i - half).
   for (int u = threadIdx.x; u < CI * (kTI / 4); u += blockDim.x) {
@@ -529,7 +536,7 @@ __device__ __forceinline__ void syn_compute(const float* __restrict__ s4, float*
     float lo[4] = {0.f, 0.f, 0.f, 0.f}, hi[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < half + 2; ++i) {
-      const int o = (r0 / 2 + i) * kPc + c;
+      const int o = (r0 / 2 + i) * kSRow + c;
       const float vll = s_ll[o], vlh = s_lh[o], vhl = s_hl[o], vhh = s_hh[o];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
