@@ -192,6 +192,73 @@ def cpu_threads() -> int:
     return os.cpu_count() or 1
 
 
+# ------------------------------------------------------------------ batched and served
+def draw_requests(count: int, seed: int):
+    """Independent problems of the batched workload: sizes 64/128/256/512 with weights
+    0.4/0.3/0.2/0.1, M uniform in [2k, 200k], input SNR uniform in [20, 40] dB."""
+    from paper_1801_02417_gb300.serve import SIZE_MIX, synthesize_problem
+    rng = np.random.default_rng(seed)
+    sizes = [n for n, _ in SIZE_MIX]
+    probs = [p for _, p in SIZE_MIX]
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes, p=probs))
+        M = int(rng.integers(2000, 200001))
+        nb = 1 if M < 50000 else 4
+        out.append(synthesize_problem(n, 4, M, seed + 100 + i, nb, snr_db=float(rng.uniform(20, 40))))
+    return out
+
+
+def batched_measure(problems, iters: int) -> dict:
+    """All problems advanced by one graph launch per iteration vs the same problems one after another."""
+    import torch
+    from paper_1801_02417_gb300 import binding as B
+    from paper_1801_02417_gb300.solver import PolarizedSARA
+
+    def start(p):
+        s = PolarizedSARA(p.n, p.levels)
+        s.set_measurements(p.uv, p.vis, p.weights, p.offsets, p.eps)
+        s.set_sara_weights(None, p.gamma)
+        return s
+    seq = 0.0
+    for p in problems:
+        with start(p) as s:
+            s.pd_iterate(3)
+            s.synchronize()
+            t = time.perf_counter()
+            s.pd_iterate(iters)
+            s.synchronize()
+            seq += time.perf_counter() - t
+    ss = [start(p) for p in problems]
+    b = B.ps_batch_create([s.h for s in ss])
+    try:
+        B.ps_batch_iterate(b, 3)
+        B.ps_batch_synchronize(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        B.ps_batch_iterate(b, iters)
+        B.ps_batch_synchronize(b)
+        bat = time.perf_counter() - t
+    finally:
+        B.ps_batch_destroy(b)
+        for s in ss:
+            s.close()
+    k = len(problems)
+    return {"problems": k, "iterations": iters, "sizes": sorted({p.n for p in problems}),
+            "batched_s": bat, "sequential_s": seq, "speedup": seq / bat,
+            "solve_iters_per_s_batched": k * iters / bat, "solve_iters_per_s_sequential": k * iters / seq}
+
+
+def served_measure(pool, rate: float, duration: float, seed: int) -> dict:
+    from paper_1801_02417_gb300.serve import Policy, Server, request_stream, summarize
+    reqs = request_stream(rate, duration, seed, pool)
+    pol = Policy(rel_tol=1e-4, max_iter=2000, reweights=5, check_every=20)
+    cont = summarize(Server(hbm_budget=64 << 30, max_active=32, policy=pol).run(reqs))
+    solo = summarize(Server(hbm_budget=64 << 30, max_active=1, policy=pol).run(reqs))
+    return {"rate_per_s": rate, "duration_s": duration, "requests": len(reqs),
+            "continuous_batching": cont, "one_at_a_time": solo}
+
+
 # ------------------------------------------------------------------ arms
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -343,6 +410,14 @@ def run_own(args) -> None:
                "d2h_bytes_per_step": int(out_p.numel() * 4),
                "note": "host->device measurements (sort, power iteration) once, then per step one iteration + Stokes read-back"}
 
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        s.close()
+        pool = draw_requests(args.batch, seed=wl.seed + 50)
+        batched = batched_measure(pool, iters=50)
+        served = served_measure(pool, rate=args.serve_rate, duration=args.serve_seconds, seed=wl.seed + 60)
+        s = None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(n, L, uv, w.astype(np.float64), M, budget_s=20.0)
@@ -373,9 +448,12 @@ def run_own(args) -> None:
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
-    s.close()
+    if s is not None:
+        s.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -388,6 +466,10 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--batch", type=int, default=32, help="problems in the batched measurement")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

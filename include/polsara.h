@@ -221,6 +221,32 @@ int32_t ps_kernels_per_iteration(const ps_handle* h);
  * Asynchronous: the result is ready when the stream is synchronised. */
 ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, int32_t levels, void* cuda_stream);
 
+/* Replace the measurements Y of the current coverage (same rows, same caller
+ * order, same blocks and radii) without re-sorting or re-estimating ||phi||: for a
+ * new noise realisation or observation on the same uv tracks. The state is kept. */
+ps_status ps_set_visibilities(ps_handle* h, const float* vis, int32_t device_ptrs);
+
+/* Relative change ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| of the last iteration for the
+ * four maps (Eq. stop_crit), from FP64 partials the iteration already wrote; cheaper
+ * than ps_compute_stats. Synchronises the handle's stream. */
+ps_status ps_get_rel_change(ps_handle* h, double* out4);
+
+/* max_j |[Psi^dagger S]_j| over all four maps (FP32 values, exact maximum): the scale
+ * from which reweighting schedules pick delta (Eq. weights). Synchronises. */
+ps_status ps_max_abs_analysis(ps_handle* h, double* out);
+
+/* Batches (many independent problems advanced together). One CUDA graph holds one
+ * iteration of every handle of the batch, each on its own stream, forked from and
+ * joined back to the batch stream, so one launch advances all problems and their
+ * kernels overlap on the device. Handles keep their own state, mode and step sizes;
+ * they must have distinct streams and measurements set. The graph is rebuilt when a
+ * handle's mode or state changes. The batch does not own the handles. */
+typedef struct ps_batch ps_batch;
+ps_status ps_batch_create(ps_handle* const* handles, int32_t count, void* cuda_stream, ps_batch** out);
+ps_status ps_batch_iterate(ps_batch* b, int32_t n_iter);   /* asynchronous on the batch stream */
+ps_status ps_batch_synchronize(ps_batch* b);
+void ps_batch_destroy(ps_batch* b);
+
 /* Synchronise the handle's stream; reports a pending CUDA error. */
 ps_status ps_synchronize(ps_handle* h);
 

@@ -74,6 +74,13 @@ _SIGS = {
     "ps_apply_psi": (_I32, [_H, _P, _P, _I32]),
     "ps_wavelet_filters": (_I32, [_P]),
     "ps_apply_psi_static": (_I32, [_P, _P, _I32, _I32, _P]),
+    "ps_set_visibilities": (_I32, [_H, _P, _I32]),
+    "ps_get_rel_change": (_I32, [_H, _P]),
+    "ps_max_abs_analysis": (_I32, [_H, ctypes.POINTER(_F64)]),
+    "ps_batch_create": (_I32, [_P, _I32, _P, ctypes.POINTER(_H)]),
+    "ps_batch_iterate": (_I32, [_H, _I32]),
+    "ps_batch_synchronize": (_I32, [_H]),
+    "ps_batch_destroy": (None, [_H]),
     "ps_profile_stages": (_I32, [_H, _I32, _P]),
     "ps_kernels_per_iteration": (_I32, [_H]),
     "ps_synchronize": (_I32, [_H]),
@@ -275,6 +282,43 @@ def ps_wavelet_filters() -> np.ndarray:
     st = lib().ps_wavelet_filters(ctypes.c_void_p(out.ctypes.data))
     _check(None, st)
     return out
+
+
+def ps_set_visibilities(h, vis) -> None:
+    p, d, k = _arg(vis, np.complex64)
+    _check(h, lib().ps_set_visibilities(h, p, d))
+
+
+def ps_get_rel_change(h) -> np.ndarray:
+    out = np.zeros(4, dtype=np.float64)
+    _check(h, lib().ps_get_rel_change(h, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def ps_max_abs_analysis(h) -> float:
+    v = _F64()
+    _check(h, lib().ps_max_abs_analysis(h, ctypes.byref(v)))
+    return v.value
+
+
+def ps_batch_create(handles, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = _H()
+    s = ctypes.c_void_p(int(stream)) if stream else None
+    _check(None, lib().ps_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(handles), s, ctypes.byref(b)))
+    return b
+
+
+def ps_batch_iterate(b, n_iter: int) -> None:
+    _check(None, lib().ps_batch_iterate(b, int(n_iter)))
+
+
+def ps_batch_synchronize(b) -> None:
+    _check(None, lib().ps_batch_synchronize(b))
+
+
+def ps_batch_destroy(b) -> None:
+    lib().ps_batch_destroy(b)
 
 
 STAGES = ("primal", "analysis", "synthesis", "fwd_fft", "degrid", "ball", "grid", "adj_fft")

@@ -140,6 +140,7 @@ static ps_status reset_state(Handle* h) {
   }
   h->derived_valid = true;   // Psi 0 = 0, phi^dagger 0 = 0
   h->iterations = 0;
+  ++h->version;
   return PS_OK;
 }
 
@@ -606,6 +607,7 @@ ps_status ps_set_mode(ps_handle* h, int32_t mode) {
   h->cfg.mode = mode;
   set_default_steps(h);
   drop_graph(h);
+  ++h->version;
   return PS_OK;
 }
 
@@ -704,6 +706,7 @@ ps_status ps_set_state(ps_handle* h, const ps_state_view* v) {
   }
   if (!dp) CK(h, cudaStreamSynchronize(h->stream));
   h->derived_valid = false;
+  ++h->version;
   return PS_OK;
 }
 
@@ -901,6 +904,49 @@ int32_t ps_kernels_per_iteration(const ps_handle* h) {
   return k;
 }
 
+ps_status ps_set_visibilities(ps_handle* h, const float* vis, int32_t device_ptrs) {
+  if (!h || !vis) return h ? fail(h, PS_EINVAL, "set_visibilities: null pointer") : PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "set_visibilities: call ps_set_measurements first");
+  CHECK_ALIGN(h, vis, device_ptrs, "set_visibilities");
+  if (h->M == 0) return PS_OK;
+  ps_status st = stage_in(h, vis, 4 * (size_t)h->M * sizeof(float2), device_ptrs, h->vtmp);
+  if (st != PS_OK) return st;
+  CK(h, ps::gather_vis(h, h->vtmp, h->Y));
+  if (!device_ptrs) CK(h, cudaStreamSynchronize(h->stream));
+  return PS_OK;
+}
+
+ps_status ps_get_rel_change(ps_handle* h, double* out4) {
+  if (!h || !out4) return h ? fail(h, PS_EINVAL, "get_rel_change: null output") : PS_EINVAL;
+  const int nb = sweep_blocks_host(h->N);
+  std::vector<double> part(8 * (size_t)nb);
+  CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < 4; ++c) {
+    double num = 0, den = 0;
+    for (int b = 0; b < nb; ++b) {
+      num += part[8 * (size_t)b + c];
+      den += part[8 * (size_t)b + 4 + c];
+    }
+    out4[c] = den > 0 ? std::sqrt(num / den) : INFINITY;
+  }
+  return check_flags(h);
+}
+
+ps_status ps_max_abs_analysis(ps_handle* h, double* out) {
+  if (!h || !out) return h ? fail(h, PS_EINVAL, "max_abs_analysis: null output") : PS_EINVAL;
+  ps_status st = ensure_tmp36(h);
+  if (st != PS_OK) return st;
+  double* dres = h->red + (size_t)h->red_cap - 600;
+  CK(h, ps::dirac_apply(h, h->S, h->tmp36, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+  CK(h, ps::sara_analysis(h, h->S, h->tmp36, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+  CK(h, ps::max_abs(h, h->tmp36, 36 * (size_t)h->N, dres + 8));
+  CK(h, cudaMemcpyAsync(h->red_host, dres + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  *out = h->red_host[0];
+  return check_flags(h);
+}
+
 ps_status ps_wavelet_filters(double* out) {
   if (!out) return PS_EINVAL;
   double h[ps::kDb][ps::kMaxTaps];
@@ -910,4 +956,155 @@ ps_status ps_wavelet_filters(double* out) {
 }
 
 }  // extern "C"
+struct ps_batch {
+  std::vector<Handle*> hs;
+  std::vector<uint64_t> versions;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t graph = nullptr;
+};
+
+static ps_status batch_fail(cudaError_t e, const char* what) {
+  ps::set_global_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? PS_ENOMEM : PS_ECUDA;
+}
+
+extern "C" void ps_batch_destroy(ps_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+extern "C" ps_status ps_batch_create(ps_handle* const* handles, int32_t count, void* cuda_stream, ps_batch** out) {
+  if (!handles || !out || count < 1) {
+    ps::set_global_error("batch_create: need at least one handle and an output pointer");
+    return PS_EINVAL;
+  }
+  *out = nullptr;
+  ps_batch* b = new ps_batch();
+  for (int i = 0; i < count; ++i) {
+    Handle* h = handles[i];
+    if (!h || !h->have_meas) {
+      ps_batch_destroy(b);
+      ps::set_global_error("batch_create: every handle needs ps_set_measurements first");
+      return PS_ESTATE;
+    }
+    for (Handle* o : b->hs)
+      if (o == h || o->stream == h->stream) {
+        ps_batch_destroy(b);
+        ps::set_global_error("batch_create: handles must be distinct and on distinct streams");
+        return PS_EINVAL;
+      }
+    b->hs.push_back(h);
+    b->versions.push_back(0);
+  }
+  cudaError_t e;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    ps_batch_destroy(b);
+    return batch_fail(e, "batch_create: stream");
+  } else {
+    b->own_stream = true;
+  }
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) {
+    ps_batch_destroy(b);
+    return batch_fail(e, "batch_create: event");
+  }
+  b->join.resize(count, nullptr);
+  for (int i = 0; i < count; ++i)
+    if ((e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming)) != cudaSuccess) {
+      ps_batch_destroy(b);
+      return batch_fail(e, "batch_create: event");
+    }
+  *out = b;
+  return PS_OK;
+}
+
+// Capture one iteration of every handle: fork from the batch stream, one_iteration on
+// each handle's stream, join back.
+static ps_status batch_build(ps_batch* b) {
+  for (Handle* h : b->hs) {
+    if (!h->derived_valid) {
+      ps_status st = compute_derived(h);
+      if (st != PS_OK) {
+        ps::set_global_error("batch: " + h->err);
+        return st;
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return batch_fail(e, "batch: handle stream");
+  }
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return batch_fail(e, "batch: begin capture");
+  cudaError_t err = cudaEventRecord(b->fork, b->stream);
+  for (size_t i = 0; i < b->hs.size() && err == cudaSuccess; ++i) {
+    Handle* h = b->hs[i];
+    err = cudaStreamWaitEvent(h->stream, b->fork, 0);
+    if (err == cudaSuccess) err = one_iteration(h);
+    if (err == cudaSuccess) err = cudaEventRecord(b->join[i], h->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  }
+  e = cudaStreamEndCapture(b->stream, &graph);
+  if (err != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return batch_fail(err != cudaSuccess ? err : e, "batch: capture");
+  }
+  e = cudaGraphInstantiate(&b->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return batch_fail(e, "batch: instantiate");
+  for (size_t i = 0; i < b->hs.size(); ++i) b->versions[i] = b->hs[i]->version;
+  return PS_OK;
+}
+
+extern "C" ps_status ps_batch_iterate(ps_batch* b, int32_t n_iter) {
+  if (!b || n_iter < 0) {
+    ps::set_global_error("batch_iterate: bad arguments");
+    return PS_EINVAL;
+  }
+  if (n_iter == 0) return PS_OK;
+  bool stale = (b->graph == nullptr);
+  for (size_t i = 0; i < b->hs.size(); ++i) stale = stale || (b->versions[i] != b->hs[i]->version);
+  if (stale) {
+    // The handles' streams may have pending work of their own: order it before the graph.
+    for (Handle* h : b->hs) {
+      cudaError_t e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return batch_fail(e, "batch: handle stream");
+    }
+    ps_status st = batch_build(b);
+    if (st != PS_OK) return st;
+  }
+  for (int i = 0; i < n_iter; ++i) {
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return batch_fail(e, "batch: graph launch");
+  }
+  for (Handle* h : b->hs) h->iterations += n_iter;
+  return PS_OK;
+}
+
+extern "C" ps_status ps_batch_synchronize(ps_batch* b) {
+  if (!b) return PS_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return batch_fail(e, "batch: synchronize");
+  for (Handle* h : b->hs) {
+    ps_status st = check_flags(h);
+    if (st != PS_OK) {
+      ps::set_global_error("batch: " + h->err);
+      return st;
+    }
+  }
+  return PS_OK;
+}
+
 #pragma GCC visibility pop

@@ -100,6 +100,7 @@ struct Handle {
   // CUDA graph of one iteration.
   cudaGraphExec_t graph = nullptr;
   int graph_mode = -1;
+  uint64_t version = 1;       // bumped when mode, state or measurements change (batch graphs rebuild)
 };
 
 // Message returned by ps_last_error(NULL) (calls without a handle).
@@ -133,6 +134,7 @@ cudaError_t dirac_apply(Handle* h, const float* X, float* coef, float* thr, int 
 cudaError_t reduce_dot(Handle* h, const float* a, const float* b, size_t len, double* dev_out);
 cudaError_t violation_count(Handle* h, const float* S, double zeta, double* dev_out);
 cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* dev_out);
+cudaError_t max_abs(Handle* h, const float* c, size_t len, double* dev_out);
 cudaError_t scale_copy(Handle* h, const float* x, float* y, size_t len, double s);
 cudaError_t gather_vis(Handle* h, const float2* user, float2* sorted);
 cudaError_t scatter_vis(Handle* h, const float2* sorted, float2* user);

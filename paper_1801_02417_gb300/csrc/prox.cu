@@ -300,6 +300,37 @@ cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* 
   return cudaGetLastError();
 }
 
+__global__ void k_maxabs_partial(const float* __restrict__ c, size_t len, float* __restrict__ part) {
+  __shared__ float sh[32];
+  float m = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(c[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
+    part[blockIdx.x] = r;
+  }
+}
+
+__global__ void k_max_partials(const float* __restrict__ part, int np, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int i = 0; i < np; ++i) r = fmaxf(r, part[i]);
+    *out = (double)r;
+  }
+}
+
+cudaError_t max_abs(Handle* h, const float* c, size_t len, double* dev_out) {
+  float* part = reinterpret_cast<float*>(h->red + (size_t)h->red_cap - 2 * kRedBlocks);
+  k_maxabs_partial<<<kRedBlocks, 256, 0, h->stream>>>(c, len, part);
+  k_max_partials<<<1, 32, 0, h->stream>>>(part, kRedBlocks, dev_out);
+  return cudaGetLastError();
+}
+
 __global__ void k_scale_copy(const float* __restrict__ x, float* __restrict__ y, size_t len, double s) {
   const float sf = (float)s;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)

@@ -1,0 +1,239 @@
+"""Continuous-batching solve server for Polarized SARA requests.
+
+Requests (independent imaging problems) arrive over time. The server admits
+them in arrival order while their estimated device footprint
+(`ps_estimate_bytes`) fits the memory budget and a slot is free, prepares each
+admitted problem on a worker thread (handle creation, row sorting, power
+iteration), and keeps every active problem's primal/dual state resident on the
+GPU. Each scheduler tick launches `check_every` iterations of every active
+problem on its own CUDA stream, so the kernels of different problems overlap on
+the device, then evaluates each problem's stopping rule (relative change of
+Eq. stop_crit) and advances its Algorithm 2 phase: an NNLS cycle, then up to
+`reweights` reweighted cycles of Algorithm 1. Finished problems return their
+Stokes maps and free their memory, which admits the next requests.
+
+All arithmetic runs in libpolsara.so; this module only schedules C ABI calls.
+"""
+from __future__ import annotations
+
+import concurrent.futures
+import dataclasses
+import statistics
+import threading
+import time
+
+import numpy as np
+
+from . import binding as B
+from .solver import PolarizedSARA
+
+
+@dataclasses.dataclass
+class Problem:
+    n: int
+    levels: int
+    uv: np.ndarray             # (M, 2) float64, rad/pixel
+    vis: np.ndarray            # (M, 4) complex64
+    weights: np.ndarray | None
+    offsets: np.ndarray        # (nblocks + 1,)
+    eps: np.ndarray            # (nblocks,)
+    gamma: float
+
+    def footprint(self) -> int:
+        return B.ps_estimate_bytes(self.n, self.levels, self.uv.shape[0])
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    iterations: int
+    S: np.ndarray
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclasses.dataclass
+class Policy:
+    rel_tol: float = 1e-4          # Eq. stop_crit tolerance per cycle
+    max_iter: int = 2000           # per request
+    reweights: int = 5             # reweighted cycles after the NNLS cycle
+    check_every: int = 20          # iterations between stop-rule checks
+    delta_factor: float = 0.1      # delta^(1) = factor * max |Psi^dagger S_nnls|
+    delta_decay: float = 0.5
+
+
+class _Active:
+    def __init__(self, rid, prob: Problem, solver: PolarizedSARA, arrival: float, admitted: float, policy: Policy):
+        self.rid, self.prob, self.s = rid, prob, solver
+        self.arrival, self.admitted = arrival, admitted
+        self.policy = policy
+        self.cycle = 0               # 0 = NNLS, 1..reweights = reweighted cycles
+        self.in_cycle = 0
+        self.used = 0
+        self.delta = None
+        self.per_cycle = max(policy.check_every, policy.max_iter // (policy.reweights + 1))
+
+    def launch(self) -> int:
+        k = min(self.policy.check_every, self.per_cycle - self.in_cycle, self.policy.max_iter - self.used)
+        if k > 0:
+            self.s.pd_iterate(k)
+            self.in_cycle += k
+            self.used += k
+        return k
+
+    def advance(self) -> bool:
+        """Check the stop rule after the launched iterations; True when the request is done."""
+        rel = B.ps_get_rel_change(self.s.h)
+        cycle_done = (float(np.max(rel[:3])) <= self.policy.rel_tol or self.in_cycle >= self.per_cycle)
+        if self.used >= self.policy.max_iter:
+            return True
+        if not cycle_done:
+            return False
+        if self.cycle >= self.policy.reweights:
+            return True
+        if self.cycle == 0:
+            self.delta = self.policy.delta_factor * B.ps_max_abs_analysis(self.s.h)
+            self.s.set_sara_weights(None, self.prob.gamma)
+            self.s.set_mode(B.PS_POLARIZED)
+        else:
+            self.delta *= self.policy.delta_decay
+        self.s.reweight(self.delta)
+        self.cycle += 1
+        self.in_cycle = 0
+        return False
+
+
+class Server:
+    """Admission by device footprint, resident state, and overlapping per-problem streams."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 64, policy: Policy | None = None, prep_workers: int = 2):
+        self.budget = int(hbm_budget)
+        self.max_active = int(max_active)
+        self.policy = policy or Policy()
+        self.prep_workers = prep_workers
+
+    @staticmethod
+    def _prepare(prob: Problem) -> PolarizedSARA:
+        s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS)
+        s.set_measurements(prob.uv, prob.vis, prob.weights, prob.offsets, prob.eps)
+        return s
+
+    def run(self, requests: list[tuple[float, Problem]]) -> list[Result]:
+        """Serve requests given as (arrival offset in seconds, problem), in real time."""
+        order = sorted(range(len(requests)), key=lambda i: requests[i][0])
+        pending = list(order)
+        t0 = time.perf_counter()
+        in_use = 0
+        preparing: dict = {}
+        active: list[_Active] = []
+        results: list[Result] = []
+        lock = threading.Lock()
+        with concurrent.futures.ThreadPoolExecutor(self.prep_workers) as pool:
+            while pending or preparing or active:
+                now = time.perf_counter() - t0
+                # Admission in arrival order: footprint within budget and a free slot.
+                while pending and requests[pending[0]][0] <= now:
+                    rid = pending[0]
+                    fp = requests[rid][1].footprint()
+                    if len(active) + len(preparing) >= self.max_active or (in_use + fp > self.budget and in_use > 0):
+                        break
+                    pending.pop(0)
+                    in_use += fp
+                    preparing[pool.submit(self._prepare, requests[rid][1])] = (rid, fp, now)
+                for fut in [f for f in preparing if f.done()]:
+                    rid, fp, adm = preparing.pop(fut)
+                    active.append(_Active(rid, requests[rid][1], fut.result(), requests[rid][0], adm, self.policy))
+                if not active:
+                    if preparing:
+                        concurrent.futures.wait(list(preparing), timeout=0.05,
+                                                return_when=concurrent.futures.FIRST_COMPLETED)
+                    elif pending:
+                        time.sleep(max(0.0, min(0.05, requests[pending[0]][0] - (time.perf_counter() - t0))))
+                    continue
+                # One tick: launch every active problem (each on its own stream), then check them.
+                for a in active:
+                    a.launch()
+                still = []
+                for a in active:
+                    if a.advance():
+                        S = a.s.get_stokes()
+                        with lock:
+                            results.append(Result(a.rid, a.arrival, a.admitted, time.perf_counter() - t0,
+                                                  a.used, S))
+                        a.s.close()
+                        in_use -= a.prob.footprint()
+                    else:
+                        still.append(a)
+                active = still
+        return results
+
+
+def summarize(results: list[Result]) -> dict:
+    if not results:
+        return {"solves": 0}
+    lat = sorted(r.latency for r in results)
+    span = max(r.finished for r in results) - min(r.arrival for r in results)
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+    return {"solves": len(results), "solves_per_s": len(results) / span if span > 0 else None,
+            "p50_s": pct(50), "p99_s": pct(99), "mean_s": statistics.mean(lat),
+            "iterations_mean": statistics.mean(r.iterations for r in results)}
+
+
+def chi2_epsilon(M_b: int, sigma: float) -> float:
+    """l2-ball radius of Section 5.1: eps^2 = (8M + 2 sqrt(16M)) sigma^2 / 2."""
+    dof = 8.0 * M_b
+    return float(np.sqrt((dof + 2.0 * np.sqrt(2.0 * dof)) * sigma * sigma / 2.0))
+
+
+def synthesize_problem(n: int, levels: int, M: int, seed: int, nblocks: int = 1, snr_db: float = 30.0,
+                       n_compact: int = 0, gamma_factor: float = 1e-3) -> Problem:
+    """A seeded request whose clean visibilities come from the library's own phi.
+
+    uv tracks and the source come from `inputs`; the noise matches `snr_db`; the
+    l2 radii are the chi^2 bounds; gamma = gamma_factor * max |Psi^dagger phi^dagger Y|.
+    """
+    from . import inputs
+    stations = 8
+    pairs = stations * (stations - 1) // 2
+    while pairs * 16 < M:
+        stations += 2
+        pairs = stations * (stations - 1) // 2
+    wl = inputs.Workload("request", n, M, stations, M // pairs + 2, levels, nblocks, 0, 0, snr_db, n_compact, seed)
+    uv = inputs.uv_coverage(wl)
+    w = np.ones(M, np.float32)
+    truth = inputs.stokes_source(n, seed, n_compact).astype(np.float32)
+    off = inputs.block_offsets(M, nblocks)
+    with PolarizedSARA(n, levels) as s:
+        s.set_measurements(uv, np.zeros((M, 4), np.complex64), w, off, np.ones(nblocks))
+        clean = np.empty((M, 4), np.complex64)
+        B.ps_apply_phi(s.h, truth, clean)
+        sigma = inputs.sigma_for_snr(clean, snr_db)
+        Y = (clean + inputs.complex_noise(M, sigma, seed)).astype(np.complex64)
+        B.ps_set_visibilities(s.h, Y)
+        dirty = np.empty((4, n, n), np.float32)
+        B.ps_apply_phi_adjoint(s.h, Y, dirty)
+        s.set_state({"S": dirty})
+        gamma = gamma_factor * B.ps_max_abs_analysis(s.h)
+    eps = np.array([chi2_epsilon(int(off[b + 1] - off[b]), sigma) for b in range(nblocks)])
+    return Problem(n, levels, uv, Y, w, off, eps, gamma)
+
+
+SIZE_MIX = ((64, 0.4), (128, 0.3), (256, 0.2), (512, 0.1))
+
+
+def request_stream(rate: float, duration: float, seed: int, pool: list[Problem]) -> list[tuple[float, Problem]]:
+    """Poisson arrivals at `rate` per second over `duration` seconds, each a draw from `pool`."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            return out
+        out.append((t, pool[int(rng.integers(len(pool)))]))

@@ -117,8 +117,7 @@ class PolarizedSARA:
         per = sch.iterations // (sch.reweights + 1)
         self.set_mode(B.PS_NNLS)
         self.pd_iterate(per)
-        S = self.get_stokes()
-        delta = sch.delta_factor * float(np.max(np.abs(self.psi_adjoint(S))))
+        delta = sch.delta_factor * B.ps_max_abs_analysis(self.h)
         self.set_sara_weights(W0, sch.gamma)
         self.set_mode(B.PS_POLARIZED)
         for _ in range(sch.reweights):
@@ -141,12 +140,11 @@ class PolarizedSARA:
                 self.pd_iterate(step)
                 k += step
                 used += step
-                if float(np.max(self.stats()["rel_change"][:3])) <= rel_tol:
+                if float(np.max(B.ps_get_rel_change(self.h)[:3])) <= rel_tol:
                     break
         self.set_mode(B.PS_NNLS)
         cycle()
-        S = self.get_stokes()
-        delta = delta_factor * float(np.max(np.abs(self.psi_adjoint(S))))
+        delta = delta_factor * B.ps_max_abs_analysis(self.h)
         self.set_sara_weights(None, gamma)
         self.set_mode(B.PS_POLARIZED)
         for _ in range(reweights):
