@@ -158,22 +158,20 @@ static ps_status compute_derived(Handle* h) {
 }
 
 // One iteration of Algorithm 1. With `ev` (PS_NSTAGES + 1 events) the stage
-// boundaries are recorded on the stream for ps_profile_stages.
-static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
+// boundaries are recorded on the stream for ps_profile_stages (stages run in order).
+// Without it, after the per-pixel sweep the SARA chain (steps 5-6 and the next
+// Psi A) runs on the handle's second stream beside the NUFFT chain (steps 7-8 and
+// the next phi^dagger B): both only read 2S'-S and write disjoint buffers, and the
+// two join before the iteration ends.
+static cudaError_t sara_chain(Handle* h) {
+  cudaError_t e = ps::sara_analysis(h, h->Xb, h->A, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f);
+  if (e != cudaSuccess) return e;
+  return ps::sara_synthesis(h, h->A, h->PsiA);
+}
+
+static cudaError_t nufft_chain(Handle* h, cudaEvent_t* ev) {
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], h->stream) : cudaSuccess; };
   cudaError_t e;
-  if ((e = mark(PS_STAGE_PRIMAL)) != cudaSuccess) return e;
-  if ((e = ps::primal_sweep(h)) != cudaSuccess) return e;
-  if ((e = mark(PS_STAGE_ANALYSIS)) != cudaSuccess) return e;
-  if (h->mode != PS_NNLS) {
-    e = ps::sara_analysis(h, h->Xb, h->A, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f);
-    if (e != cudaSuccess) return e;
-  }
-  if ((e = mark(PS_STAGE_SYNTHESIS)) != cudaSuccess) return e;
-  if (h->mode != PS_NNLS) {
-    e = ps::sara_synthesis(h, h->A, h->PsiA);
-    if (e != cudaSuccess) return e;
-  }
   if ((e = mark(PS_STAGE_FWD_FFT)) != cudaSuccess) return e;
   if (h->M > 0 && (e = ps::nufft_forward_grid(h, h->Xb)) != cudaSuccess) return e;
   if ((e = mark(PS_STAGE_DEGRID)) != cudaSuccess) return e;
@@ -185,6 +183,34 @@ static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
   if ((e = mark(PS_STAGE_ADJ_FFT)) != cudaSuccess) return e;
   if (h->M > 0 && (e = ps::nufft_adjoint_image(h, h->Adj)) != cudaSuccess) return e;
   return mark(PS_NSTAGES);
+}
+
+static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], h->stream) : cudaSuccess; };
+  cudaError_t e;
+  if ((e = mark(PS_STAGE_PRIMAL)) != cudaSuccess) return e;
+  if ((e = ps::primal_sweep(h)) != cudaSuccess) return e;
+  const bool sara = (h->mode != PS_NNLS);
+  if (ev || !sara || h->M == 0 || !h->aux) {
+    if ((e = mark(PS_STAGE_ANALYSIS)) != cudaSuccess) return e;
+    if (sara && (e = ps::sara_analysis(h, h->Xb, h->A, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f)) !=
+                    cudaSuccess)
+      return e;
+    if ((e = mark(PS_STAGE_SYNTHESIS)) != cudaSuccess) return e;
+    if (sara && (e = ps::sara_synthesis(h, h->A, h->PsiA)) != cudaSuccess) return e;
+    return nufft_chain(h, ev);
+  }
+  if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0)) != cudaSuccess) return e;
+  cudaStream_t main = h->stream;
+  h->stream = h->aux;                     // the SARA launchers use h->stream
+  e = sara_chain(h);
+  cudaError_t e2 = cudaEventRecord(h->ev_join, h->aux);
+  h->stream = main;
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  if ((e = nufft_chain(h, nullptr)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(h->stream, h->ev_join, 0);
 }
 
 static ps_status build_graph(Handle* h) {
@@ -258,6 +284,12 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
     }
     h->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    h->err = "ps_create: auxiliary stream/events";
+    return bail(PS_ECUDA);
+  }
   cudaError_t e = ps::configure_kernels();
   if (e != cudaSuccess) {
     h->err = std::string("configure kernels: ") + cudaGetErrorString(e);
@@ -319,6 +351,9 @@ void ps_destroy(ps_handle* h) {
   dfree(h, h->red, (size_t)h->red_cap);
   dfree(h, h->dev_flags, 4);
   if (h->red_host) cudaFreeHost(h->red_host);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -48,6 +48,8 @@ struct Handle {
   ps_config cfg{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t aux = nullptr;       // second stream: SARA chain runs beside the NUFFT chain in graphs
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   int n = 0, N = 0, L = 0, mode = PS_POLARIZED;
   double tau = 0, rho1 = 1, rho2 = 1, rho3 = 1, opnorm_sq = 0, gamma = 1;
