@@ -44,24 +44,51 @@ __device__ __forceinline__ float4 cmul2(float4 a, float2 w) {
 }
 __device__ __forceinline__ int bitrev(int i, int logK) { return (int)(__brev((unsigned)i) >> (32 - logK)); }
 
-// In-place radix-2 decimation-in-time FFT of K float4 (two complex sequences)
-// held in shared memory in bit-reversed order; output in natural order.
-// INV selects exp(+2 pi i jk/K) (no 1/K normalisation).
+// In-place decimation-in-time FFT of K float4 (two complex sequences) held in
+// shared memory in bit-reversed order; output in natural order. INV selects
+// exp(+2 pi i jk/K) (no 1/K normalisation). Radix-2 stages s and s+1 are done
+// together by one thread on the four elements a, a+h, a+2h, a+3h (h = 2^s, bits s
+// and s+1 of a clear), so there is one shared-memory pass and one barrier per two
+// stages; an odd stage count ends with a plain radix-2 stage.
+template <bool INV>
+__device__ __forceinline__ float2 twiddle(const float2* tw, int idx) {
+  float2 w = tw[idx];
+  if (INV) w.y = -w.y;
+  return w;
+}
+
 template <bool INV>
 __device__ void fft_smem(float4* buf, const float2* tw, int K, int logK) {
-  for (int s = 0; s < logK; ++s) {
+  int s = 0;
+  for (; s + 1 < logK; s += 2) {
     const int hs = 1 << s;
-    const int step = K >> (s + 1);
+    for (int g = threadIdx.x; g < (K >> 2); g += blockDim.x) {
+      const int pos = g & (hs - 1);
+      const int a = ((g >> s) << (s + 2)) + pos;
+      const float2 w0 = twiddle<INV>(tw, pos * (K >> (s + 1)));          // stage s
+      const float2 w1 = twiddle<INV>(tw, pos * (K >> (s + 2)));          // stage s+1, pair (a, a+2h)
+      const float2 w2 = twiddle<INV>(tw, (pos + hs) * (K >> (s + 2)));   // stage s+1, pair (a+h, a+3h)
+      const float4 x0 = buf[a], x1 = buf[a + hs], x2 = buf[a + 2 * hs], x3 = buf[a + 3 * hs];
+      const float4 t1 = cmul2(x1, w0), t3 = cmul2(x3, w0);
+      const float4 y0 = f4add(x0, t1), y1 = f4sub(x0, t1), y2 = f4add(x2, t3), y3 = f4sub(x2, t3);
+      const float4 u2 = cmul2(y2, w1), u3 = cmul2(y3, w2);
+      buf[a] = f4add(y0, u2);
+      buf[a + 2 * hs] = f4sub(y0, u2);
+      buf[a + hs] = f4add(y1, u3);
+      buf[a + 3 * hs] = f4sub(y1, u3);
+    }
+    __syncthreads();
+  }
+  if (s < logK) {
+    const int hs = 1 << s;
     for (int b = threadIdx.x; b < (K >> 1); b += blockDim.x) {
       const int pos = b & (hs - 1);
       const int i0 = ((b >> s) << (s + 1)) + pos;
-      const int i1 = i0 + hs;
-      float2 w = tw[pos * step];
-      if (INV) w.y = -w.y;
+      const float2 w = twiddle<INV>(tw, pos * (K >> (s + 1)));
       const float4 u = buf[i0];
-      const float4 v = cmul2(buf[i1], w);
+      const float4 v = cmul2(buf[i0 + hs], w);
       buf[i0] = f4add(u, v);
-      buf[i1] = f4sub(u, v);
+      buf[i0 + hs] = f4sub(u, v);
     }
     __syncthreads();
   }
