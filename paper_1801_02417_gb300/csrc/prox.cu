@@ -64,7 +64,7 @@ __device__ __forceinline__ void setc(float4& v, int k, float x) {
 }
 
 // One thread = four consecutive pixels (float4 on every plane).
-__global__ void __launch_bounds__(kSweepThreads) k_primal(
+__global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
     int N, int mode, float tau, float rho1, float rho3, float* __restrict__ S, float* __restrict__ Z,
     float* __restrict__ C, float* __restrict__ D, const float* __restrict__ PsiA, const float* __restrict__ Adj,
     float* __restrict__ Xb, float* __restrict__ A, const float* __restrict__ T, size_t cstride,
@@ -151,12 +151,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_primal(
       st4(C + 3 * (size_t)N + i, c3);
     }
   }
-  // FP64 partials for the relative-change statistic.
+  // Partials for the relative-change statistic: FP32 within a warp (at most 128
+  // terms), FP64 across warps and CTAs.
   double v[8];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    v[c] = warp_sum((double)dss[c]);
-    v[4 + c] = warp_sum((double)ss[c]);
+    v[c] = (double)warp_sum(dss[c]);
+    v[4 + c] = (double)warp_sum(ss[c]);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0)
