@@ -657,6 +657,268 @@ __global__ void __launch_bounds__(256, 4) k_syn_lv(const float* __restrict__ coe
       make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
+// ---------------------------------------------------------------------------
+// Synthesis for levels with output side m >= 64: 64 x 64 output tiles.
+//   * The four subband tiles of one basis (rows of 40 coefficients starting 8
+//     columns left of the tile's coefficient origin, with the filter halo) are
+//     staged by bulk copies, one per row (two where the row wraps around the
+//     periodic left edge), completing on an mbarrier; the finest-level kernel
+//     double-buffers them so basis b+1 is in flight while basis b is filtered.
+//   * Along y, each thread computes two adjacent columns x four rows of the
+//     low/high row-filtered tiles with packed FP32x2 FMAs and stores them
+//     column-major ([column][row]).
+//   * Along x, each thread owns a 4 x 4 output block; the column-major
+//     intermediates give it two rows per 64-bit operand, so the taps are again
+//     packed FP32x2 FMAs with the coefficient duplicated in both halves.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 f2pack(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr int kT2 = 64;                                  // output tile side
+constexpr int kC2Rows = kT2 / 2 + kMaxTaps / 2 - 1;      // 39 coefficient rows (db8 halo)
+constexpr int kC2Cols = kT2 / 2 + 8;                     // 40 staged columns: [ox0/2 - 8, ox0/2 + 32)
+constexpr int kC2Pitch = 52;                             // staged row pitch (2 x 52 = 8 mod 32 banks)
+constexpr int kC2Sub = kC2Rows * kC2Pitch;               // one subband tile
+constexpr int kC2Set = 4 * kC2Sub;                       // LL, LH, HL, HH
+constexpr int kLoPitch = kT2 + 4;                        // column-major intermediates: [column][row]
+constexpr int kLoSize = kC2Cols * kLoPitch;
+static_assert(kC2Sub % 4 == 0 && kLoSize % 4 == 0, "16-byte aligned synthesis buffers");
+
+// Issue the bulk copies of basis `half` (db(half+1)) for the tile at (oy0, ox0):
+// subband sb row r <- coefficient row (oy0/2 - half + r) mod hm, columns
+// [ox0/2 - 8, ox0/2 + 32) mod hm. Thread 0 posts the byte count; any thread may
+// start copies before or after it (the barrier's transaction count may run ahead).
+__device__ __forceinline__ void syn2_issue(int half, const float* __restrict__ cb, const float* __restrict__ apx,
+                                           int n, int hm, int oy0, int ox0, float* __restrict__ s4, uint64_t* bar) {
+  const int CI = kT2 / 2 + half;
+  const int ky0 = oy0 / 2 - half, kxa = ox0 / 2 - 8;
+  if (threadIdx.x == 0) mbar_expect_tx(bar, (uint32_t)(4 * CI * kC2Cols * sizeof(float)));
+  for (int k = threadIdx.x; k < 4 * CI; k += blockDim.x) {
+    const int sb = k / CI, r = k - sb * CI;
+    const int Yk = wrap1(ky0 + r, hm);
+    const float* row;
+    if (sb == 0) row = apx ? apx + (size_t)Yk * hm : cb + (size_t)Yk * n;   // LL
+    else if (sb == 1) row = cb + (size_t)(hm + Yk) * n;                     // LH (x-low, y-high)
+    else if (sb == 2) row = cb + (size_t)Yk * n + hm;                       // HL (x-high, y-low)
+    else row = cb + (size_t)(hm + Yk) * n + hm;                             // HH
+    float* dst = s4 + sb * kC2Sub + r * kC2Pitch;
+    fence_proxy_async();
+    if (kxa >= 0) {
+      bulk_g2s(dst, row + kxa, kC2Cols * sizeof(float), bar);
+    } else {   // left edge: columns hm-8 .. hm-1, then 0 .. 31
+      bulk_g2s(dst, row + hm - 8, 8 * sizeof(float), bar);
+      bulk_g2s(dst + 8, row, (kC2Cols - 8) * sizeof(float), bar);
+    }
+  }
+}
+
+// Along y for basis LF: lo/hi at output rows 4 rg + t (t = 0..3) and staged columns
+// c, c + 1, from coefficient rows 2 rg + i (i = 0 .. half + 1) through tap
+// j = t - 2 (i - half). Columns start at the even column at or left of 8 - half.
+template <int LF>
+__device__ __forceinline__ void syn2_ypass(const float* __restrict__ s4, float* __restrict__ loT,
+                                           float* __restrict__ hiT) {
+  constexpr int half = LF / 2 - 1;
+  constexpr int cs = (8 - half) & ~1;
+  constexpr int NCP = (kC2Cols - cs) / 2;
+  for (int u = threadIdx.x; u < NCP * (kT2 / 4); u += blockDim.x) {
+    const int cp = u % NCP, rg = u / NCP;
+    const int c = cs + 2 * cp;
+    u64 lo[4], hi[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) lo[t] = hi[t] = 0ull;
+#pragma unroll
+    for (int i = 0; i < half + 2; ++i) {
+      const int o = (2 * rg + i) * kC2Pitch + c;
+      const u64 vll = *reinterpret_cast<const u64*>(s4 + o);
+      const u64 vlh = *reinterpret_cast<const u64*>(s4 + kC2Sub + o);
+      const u64 vhl = *reinterpret_cast<const u64*>(s4 + 2 * kC2Sub + o);
+      const u64 vhh = *reinterpret_cast<const u64*>(s4 + 3 * kC2Sub + o);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = t - 2 * (i - half);
+        if (j >= 0 && j < LF) {
+          const u64 ph = f2pack(c_h[half][j], c_h[half][j]), pg = f2pack(c_g[half][j], c_g[half][j]);
+          lo[t] = ffma2(ph, vll, ffma2(pg, vlh, lo[t]));
+          hi[t] = ffma2(ph, vhl, ffma2(pg, vhh, hi[t]));
+        }
+      }
+    }
+    float l0[4], l1[4], h0[4], h1[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      f2unpack(lo[t], l0[t], l1[t]);
+      f2unpack(hi[t], h0[t], h1[t]);
+    }
+    *reinterpret_cast<float4*>(loT + c * kLoPitch + 4 * rg) = make_float4(l0[0], l0[1], l0[2], l0[3]);
+    *reinterpret_cast<float4*>(loT + (c + 1) * kLoPitch + 4 * rg) = make_float4(l1[0], l1[1], l1[2], l1[3]);
+    *reinterpret_cast<float4*>(hiT + c * kLoPitch + 4 * rg) = make_float4(h0[0], h0[1], h0[2], h0[3]);
+    *reinterpret_cast<float4*>(hiT + (c + 1) * kLoPitch + 4 * rg) = make_float4(h1[0], h1[1], h1[2], h1[3]);
+  }
+}
+
+// Along x for basis LF, accumulated into this thread's 4 x 4 block: rows 4 rq .. 4 rq + 3,
+// columns 4 cg + t; acc[2t] holds rows (4rq, 4rq+1), acc[2t+1] rows (4rq+2, 4rq+3).
+// Output column 4 cg + t reads staged column 8 - half + 2 cg + i through tap t - 2 (i - half).
+template <int LF>
+__device__ __forceinline__ void syn2_xpass(const float* __restrict__ loT, const float* __restrict__ hiT,
+                                           u64 acc[8]) {
+  constexpr int half = LF / 2 - 1;
+  const int rq = threadIdx.x & 15, cg = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < half + 2; ++i) {
+    const int col = 2 * cg + (8 - half) + i;
+    const ulonglong2 vlo = *reinterpret_cast<const ulonglong2*>(loT + col * kLoPitch + 4 * rq);
+    const ulonglong2 vhi = *reinterpret_cast<const ulonglong2*>(hiT + col * kLoPitch + 4 * rq);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int j = t - 2 * (i - half);
+      if (j >= 0 && j < LF) {
+        const u64 ph = f2pack(c_h[half][j], c_h[half][j]), pg = f2pack(c_g[half][j], c_g[half][j]);
+        acc[2 * t] = ffma2(ph, vlo.x, ffma2(pg, vhi.x, acc[2 * t]));
+        acc[2 * t + 1] = ffma2(ph, vlo.y, ffma2(pg, vhi.y, acc[2 * t + 1]));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void syn2_ypass_dispatch(int bi, const float* s4, float* loT, float* hiT) {
+#define PS_Y(LFv) syn2_ypass<LFv>(s4, loT, hiT)
+  PS_SWITCH_LF(bi, PS_Y)
+#undef PS_Y
+}
+__device__ __forceinline__ void syn2_xpass_dispatch(int bi, const float* loT, const float* hiT, u64 acc[8]) {
+#define PS_X(LFv) syn2_xpass<LFv>(loT, hiT, acc)
+  PS_SWITCH_LF(bi, PS_X)
+#undef PS_X
+}
+
+// Row rr (0..3) of this thread's 4 x 4 block.
+__device__ __forceinline__ float4 syn2_row(const u64 acc[8], int rr) {
+  float v[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    float a, b;
+    f2unpack(acc[2 * t + (rr >> 1)], a, b);
+    v[t] = (rr & 1) ? b : a;
+  }
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+static size_t syn2_smem(int sets) { return (size_t)(sets * kC2Set + 2 * kLoSize) * sizeof(float) + 16; }
+
+// After a bounded wait gave up somewhere in the CTA: raise the flag (when given),
+// give the copies still in flight a bounded chance to land, and let the caller return.
+__device__ __forceinline__ void syn2_abort(uint64_t* b0, uint32_t p0, uint64_t* b1, uint32_t p1, int* err) {
+  if (threadIdx.x == 0) {
+    if (err) atomicExch(err, 1);
+    (void)mbar_wait(b0, p0);
+    if (b1) (void)mbar_wait(b1, p1);
+  }
+  __syncthreads();
+}
+
+// Finest level (m = n >= 64): the eight bases plus the Dirac part summed in registers -> Psi A.
+__global__ void __launch_bounds__(256, 2) k_syn2_fine(const float* __restrict__ coef,
+                                                      const float* __restrict__ approx_in, int coarsest, int n,
+                                                      float* __restrict__ out, int* err) {
+  extern __shared__ float4 sm2[];
+  float* const s4 = reinterpret_cast<float*>(sm2);   // two sets: basis b in set b & 1
+  float* loT = s4 + 2 * kC2Set;
+  float* hiT = loT + kLoSize;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hiT + kLoSize);
+  const int map = blockIdx.z, tilesx = n / kT2;
+  const int oy0 = (blockIdx.x / tilesx) * kT2, ox0 = (blockIdx.x % tilesx) * kT2;
+  const int hm = n >> 1;
+  const float* cmap = coef + (size_t)map * kBases * n * n;
+  auto cbp = [&](int bi) { return cmap + (size_t)(bi + 1) * n * n; };
+  auto apxp = [&](int bi) {
+    return coarsest ? (const float*)nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  syn2_issue(0, cbp(0), apxp(0), n, hm, oy0, ox0, s4, &bar[0]);
+  u64 acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0ull;
+  for (int bi = 0; bi < kDb; ++bi) {
+    // Buffer (bi+1)&1 last fed the y-pass of basis bi-1, which ended at a barrier.
+    if (bi + 1 < kDb)
+      syn2_issue(bi + 1, cbp(bi + 1), apxp(bi + 1), n, hm, oy0, ox0, s4 + ((bi + 1) & 1) * kC2Set,
+                 &bar[(bi + 1) & 1]);
+    const bool ok = mbar_wait(&bar[bi & 1], (bi >> 1) & 1);
+    // Also orders the previous x-pass' reads of loT/hiT before this y-pass writes them.
+    if (__syncthreads_or(!ok)) {
+      syn2_abort(&bar[bi & 1], (bi >> 1) & 1, bi + 1 < kDb ? &bar[(bi + 1) & 1] : nullptr, ((bi + 1) >> 1) & 1,
+                 err);
+      return;
+    }
+    syn2_ypass_dispatch(bi, s4 + (bi & 1) * kC2Set, loT, hiT);
+    __syncthreads();
+    syn2_xpass_dispatch(bi, loT, hiT, acc);
+  }
+  const int rq = threadIdx.x & 15, cg = threadIdx.x >> 4;
+  const float k3 = 1.0f / 3.0f;
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const size_t o = (size_t)(oy0 + 4 * rq + rr) * n + ox0 + 4 * cg;
+    const float4 d = *reinterpret_cast<const float4*>(cmap + o);
+    const float4 s = syn2_row(acc, rr);
+    *reinterpret_cast<float4*>(out + (size_t)map * n * n + o) =
+        make_float4((d.x + s.x) * k3, (d.y + s.y) * k3, (d.z + s.z) * k3, (d.w + s.w) * k3);
+  }
+}
+
+// Coarser levels with output side m >= 64: one basis per CTA (grid.y), output to approximation scratch.
+__global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ coef, const float* __restrict__ approx_in,
+                                                    int coarsest, int m, int n, float* __restrict__ approx_out,
+                                                    int* err) {
+  extern __shared__ float4 sm2[];
+  float* s4 = reinterpret_cast<float*>(sm2);
+  float* loT = s4 + kC2Set;
+  float* hiT = loT + kLoSize;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hiT + kLoSize);
+  const int bi = blockIdx.y, map = blockIdx.z, tilesx = m / kT2;
+  const int oy0 = (blockIdx.x / tilesx) * kT2, ox0 = (blockIdx.x % tilesx) * kT2;
+  const int hm = m >> 1;
+  const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
+  const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  syn2_issue(bi, cb, apx, n, hm, oy0, ox0, s4, bar);
+  const bool ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    syn2_abort(bar, 0, nullptr, 0, err);
+    return;
+  }
+  syn2_ypass_dispatch(bi, s4, loT, hiT);
+  __syncthreads();
+  u64 acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0ull;
+  syn2_xpass_dispatch(bi, loT, hiT, acc);
+  const int rq = threadIdx.x & 15, cg = threadIdx.x >> 4;
+  float* dst = approx_out + ((size_t)map * kDb + bi) * (size_t)m * m;
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr)
+    *reinterpret_cast<float4*>(dst + (size_t)(oy0 + 4 * rq + rr) * m + ox0 + 4 * cg) = syn2_row(acc, rr);
+}
+
 static_assert((kInSize + 2 * kRSmax * kPlo) % 4 == 0 && kStage % 4 == 0, "16-byte aligned stage buffers");
 static size_t fast_analysis_smem() { return (size_t)kAnaFloats * sizeof(float) + 16; }
 
@@ -681,6 +943,14 @@ cudaError_t configure_kernels() {
   for (const void* f : {(const void*)k_ana_l1, (const void*)k_ana_lv}) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_analysis_smem());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaFuncSetAttribute((const void*)k_syn2_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn2_smem(2));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)k_syn2_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn2_smem(1));
+  if (e != cudaSuccess) return e;
+  for (const void* f : {(const void*)k_syn2_fine, (const void*)k_syn2_lv}) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
@@ -724,8 +994,9 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
 }
 
 // Psi A on `stream` with `approx` as the per-level approximation scratch
-// (2 x 32 x (n/2)^2 floats).
-static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx) {
+// (2 x 32 x (n/2)^2 floats); `err` (may be null) receives the bounded-wait flag.
+static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx,
+                                    int* err) {
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
   float* buf[2] = {approx, approx + quarter};
   for (int l = L; l >= 1; --l) {
@@ -734,7 +1005,12 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
     const int tiles = (m / TI) * (m / TI);
     const float* ain = (l == L) ? nullptr : buf[l & 1];
     float* aout = (l == 1) ? nullptr : buf[(l - 1) & 1];
-    if (m >= kTI && l == 1) {
+    if (m >= kT2 && l == 1) {
+      k_syn2_fine<<<dim3((m / kT2) * (m / kT2), 1, 4), 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err);
+    } else if (m >= kT2) {
+      k_syn2_lv<<<dim3((m / kT2) * (m / kT2), kDb, 4), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
+                                                                                     err);
+    } else if (m >= kTI && l == 1) {
       k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, stream>>>(coef, ain, l == L, n, out);
     } else if (m >= kTI) {
       k_syn_lv<<<dim3(tiles, kDb, 4), 256, 0, stream>>>(coef, ain, l == L, m, n, aout);
@@ -747,7 +1023,7 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
 }
 
 cudaError_t sara_synthesis(Handle* h, const float* coef, float* out) {
-  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx);
+  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->dev_flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -800,11 +1076,16 @@ extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, in
         set_global_error(std::string("apply_psi_static: filter upload: ") + cudaGetErrorString(e));
         return PS_ECUDA;
       }
+      e = configure_kernels();   // shared-memory limits of the kernels (function attributes, no allocation)
+      if (e != cudaSuccess) {
+        set_global_error(std::string("apply_psi_static: kernel attributes: ") + cudaGetErrorString(e));
+        return PS_ECUDA;
+      }
       g_static_ptr[dev] = static_cast<float*>(p);
     }
     scratch = g_static_ptr[dev];
   }
-  e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch);
+  e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, nullptr);
   if (e != cudaSuccess) {
     set_global_error(std::string("apply_psi_static: launch: ") + cudaGetErrorString(e));
     return PS_ECUDA;
