@@ -22,8 +22,12 @@
 
 namespace ps {
 
-__constant__ float c_h[kDb][kMaxTaps];
-__constant__ float c_g[kDb][kMaxTaps];
+__constant__ __align__(16) float c_h[kDb][kMaxTaps];
+__constant__ __align__(16) float c_g[kDb][kMaxTaps];
+// The same taps duplicated in both halves of a 64-bit word, the operand of packed
+// FP32x2 FMAs that apply one tap to two neighbouring samples.
+__constant__ __align__(16) float2 c_hd[kDb][kMaxTaps];
+__constant__ __align__(16) float2 c_gd[kDb][kMaxTaps];
 
 cudaError_t upload_filters(const double h[kDb][kMaxTaps]) {
   float hf[kDb][kMaxTaps], gf[kDb][kMaxTaps];
@@ -34,10 +38,51 @@ cudaError_t upload_filters(const double h[kDb][kMaxTaps]) {
       gf[b][j] = j < Lf ? (float)(((j & 1) ? -1.0 : 1.0) * h[b][Lf - 1 - j]) : 0.f;
     }
   }
+  float2 hd[kDb][kMaxTaps], gd[kDb][kMaxTaps];
+  for (int b = 0; b < kDb; ++b)
+    for (int j = 0; j < kMaxTaps; ++j) {
+      hd[b][j] = make_float2(hf[b][j], hf[b][j]);
+      gd[b][j] = make_float2(gf[b][j], gf[b][j]);
+    }
   cudaError_t e = cudaMemcpyToSymbol(c_h, hf, sizeof(hf));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_g, gf, sizeof(gf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_g, gf, sizeof(gf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hd, hd, sizeof(hd));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gd, gd, sizeof(gd));
+  return e;
 }
+
+// ---- Packed FP32x2 arithmetic (two lanes of one 64-bit register pair).
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 f2pack(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// A tap pair as one 64-bit FMA operand: {c[j], c[j+1]} (j even) or a duplicated tap.
+__device__ __forceinline__ u64 cpair(const float* c) { return *reinterpret_cast<const u64*>(c); }
+__device__ __forceinline__ u64 cdup(const float2& c) { return *reinterpret_cast<const u64*>(&c); }
+
+// Calls CALL(LF) with the compile-time filter length of basis bi (db1..db8).
+#define PS_SWITCH_LF(bi, CALL)    \
+  switch (bi) {                   \
+    case 0: CALL(2); break;       \
+    case 1: CALL(4); break;       \
+    case 2: CALL(6); break;       \
+    case 3: CALL(8); break;       \
+    case 4: CALL(10); break;      \
+    case 5: CALL(12); break;      \
+    case 6: CALL(14); break;      \
+    default: CALL(16); break;     \
+  }
 
 __device__ __forceinline__ void sara_epilogue(int mode, float val, size_t idx, float* coef, float* thr, float scale,
                                               float gamma, float delta) {
@@ -207,12 +252,12 @@ __global__ void __launch_bounds__(256) k_synthesis(const float* __restrict__ coe
 // four outputs from registers (inputs read once from shared memory per strip).
 constexpr int kTO = 32;                          // analysis output tile (per subband)
 constexpr int kRSmax = 2 * kTO + kMaxTaps - 2;   // 78: input tile side for db8
-constexpr int kPin = kRSmax | 1;                 // odd pitch: conflict-free row reads
+constexpr int kA2Cols = 2 * kTO + 16;            // 80 staged input columns (covers 2 TO + 14 for db8)
+constexpr int kA2Pitch = kA2Cols + 4;            // 84 = 20 mod 32 banks: row-parallel 16-byte reads conflict-free
+constexpr int kA2In = kRSmax * kA2Pitch;         // input tile
 constexpr int kPlo = kTO + 4;                    // row-filtered tiles (16-byte aligned rows)
-constexpr int kInSize = (kRSmax * kPin + 3) / 4 * 4;   // input tile, padded so lo_s starts 16-byte aligned
 constexpr int kTI = 32;                          // synthesis output tile
 constexpr int kCImax = kTI / 2 + kMaxTaps / 2 - 1;   // 23
-constexpr int kPc = kCImax | 1;                  // 23 (odd)
 constexpr int kPs = kCImax + 2;                  // 25
 
 __device__ __forceinline__ int wrap1(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
@@ -254,29 +299,40 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Rows: lo/hi[r][k] = sum_j h/g[j] in[r][2k + j], k in [0, TO).
+// Rows: lo/hi[r][k] = sum_j h/g[j] in[r][2k + j], k in [0, TO). Each thread makes
+// four outputs of one row from 16-byte reads; the taps go in pairs,
+// {c[2p], c[2p+1]} x {in[2k+2p], in[2k+2p+1]}, and the two halves are added at the end.
 template <int LF>
 __device__ __forceinline__ void ana_rows(const float* __restrict__ in_s, float* __restrict__ lo_s,
                                          float* __restrict__ hi_s) {
   constexpr int RS = 2 * kTO + LF - 2;
   constexpr int b = LF / 2 - 1;
+  constexpr int NP = LF / 2 + 3;            // sample pairs feeding four outputs
+  constexpr int NV = (NP + 1) / 2;          // 16-byte reads
   for (int u = threadIdx.x; u < RS * (kTO / 4); u += blockDim.x) {
     const int r = u % RS, k0 = (u / RS) * 4;
-    const float* row = in_s + r * kPin + 2 * k0;
-    float x[LF + 6];
+    const float* row = in_s + r * kA2Pitch + 2 * k0;
+    u64 x[2 * NV];
 #pragma unroll
-    for (int j = 0; j < LF + 6; ++j) x[j] = row[j];
+    for (int v = 0; v < NV; ++v) {
+      const ulonglong2 q = *reinterpret_cast<const ulonglong2*>(row + 4 * v);
+      x[2 * v] = q.x;
+      x[2 * v + 1] = q.y;
+    }
     float lo[4], hi[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float a = 0.f, c = 0.f;
+      u64 a = 0ull, c = 0ull;
 #pragma unroll
-      for (int j = 0; j < LF; ++j) {
-        a = fmaf(c_h[b][j], x[2 * q + j], a);
-        c = fmaf(c_g[b][j], x[2 * q + j], c);
+      for (int p = 0; p < LF / 2; ++p) {
+        a = ffma2(cpair(&c_h[b][2 * p]), x[q + p], a);
+        c = ffma2(cpair(&c_g[b][2 * p]), x[q + p], c);
       }
-      lo[q] = a;
-      hi[q] = c;
+      float a0, a1, c0, c1;
+      f2unpack(a, a0, a1);
+      f2unpack(c, c0, c1);
+      lo[q] = a0 + a1;
+      hi[q] = c0 + c1;
     }
     *reinterpret_cast<float4*>(lo_s + r * kPlo + k0) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     *reinterpret_cast<float4*>(hi_s + r * kPlo + k0) = make_float4(hi[0], hi[1], hi[2], hi[3]);
@@ -289,6 +345,12 @@ __device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
 __device__ __forceinline__ float4 f4clamp(float4 a, float4 t) {
   return make_float4(fminf(fmaxf(a.x, -t.x), t.x), fminf(fmaxf(a.y, -t.y), t.y), fminf(fmaxf(a.z, -t.z), t.z),
                      fminf(fmaxf(a.w, -t.w), t.w));
+}
+__device__ __forceinline__ float4 f4of(u64 a, u64 b) {
+  float4 r;
+  f2unpack(a, r.x, r.y);
+  f2unpack(b, r.z, r.w);
+  return r;
 }
 
 // Epilogue on four consecutive coefficients (16-byte aligned).
@@ -307,8 +369,8 @@ __device__ __forceinline__ void sara_epilogue4(int mode, float4 v, size_t idx, f
 }
 
 // Columns + epilogue for one basis: four subbands of a TO x TO tile. Each thread
-// owns four consecutive columns of one output row, so the epilogue reads and
-// writes A and gamma W as float4 (prefetched before the filtering).
+// owns four consecutive columns of one output row (two packed pairs per subband),
+// so the epilogue reads and writes A and gamma W as float4 (staged before the filtering).
 template <int LF>
 __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const float* __restrict__ hi_s, int bi,
                                          int map, int n, int hm, int oy0, int ox0, int last, float* __restrict__ coef,
@@ -324,6 +386,21 @@ __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const f
     const size_t i_lh = base + (size_t)(hm + Y) * n + X;
     const size_t i_hh = base + (size_t)(hm + Y) * n + (hm + X);
     const size_t i_ll = base + (size_t)Y * n + X;
+    u64 ll0 = 0ull, ll1 = 0ull, lh0 = 0ull, lh1 = 0ull, hl0 = 0ull, hl1 = 0ull, hh0 = 0ull, hh1 = 0ull;
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+      const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(lo_s + (2 * ky + j) * kPlo + kx0);
+      const ulonglong2 c = *reinterpret_cast<const ulonglong2*>(hi_s + (2 * ky + j) * kPlo + kx0);
+      const u64 ph = cdup(c_hd[b][j]), pg = cdup(c_gd[b][j]);
+      ll0 = ffma2(ph, a.x, ll0);
+      ll1 = ffma2(ph, a.y, ll1);
+      lh0 = ffma2(pg, a.x, lh0);
+      lh1 = ffma2(pg, a.y, lh1);
+      hl0 = ffma2(ph, c.x, hl0);
+      hl1 = ffma2(ph, c.y, hl1);
+      hh0 = ffma2(pg, c.x, hh0);
+      hh1 = ffma2(pg, c.y, hh1);
+    }
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 a_hl = z, a_lh = z, a_hh = z, a_ll = z, t_hl = z, t_lh = z, t_hh = z, t_ll = z;
     if (mode == SARA_DUAL) {
@@ -340,80 +417,41 @@ __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const f
         t_ll = *reinterpret_cast<const float4*>(thr + i_ll);
       }
     }
-    float4 ll = z, lh = z, hl = z, hh = z;
-#pragma unroll
-    for (int j = 0; j < LF; ++j) {
-      const float4 a = *reinterpret_cast<const float4*>(lo_s + (2 * ky + j) * kPlo + kx0);
-      const float4 c = *reinterpret_cast<const float4*>(hi_s + (2 * ky + j) * kPlo + kx0);
-      ll = f4fma(c_h[b][j], a, ll);
-      lh = f4fma(c_g[b][j], a, lh);
-      hl = f4fma(c_h[b][j], c, hl);
-      hh = f4fma(c_g[b][j], c, hh);
-    }
-    sara_epilogue4(mode, hl, i_hl, a_hl, t_hl, coef, thr, scale, gamma, delta);   // x-high, y-low
-    sara_epilogue4(mode, lh, i_lh, a_lh, t_lh, coef, thr, scale, gamma, delta);   // x-low, y-high
-    sara_epilogue4(mode, hh, i_hh, a_hh, t_hh, coef, thr, scale, gamma, delta);
-    if (last) sara_epilogue4(mode, ll, i_ll, a_ll, t_ll, coef, thr, scale, gamma, delta);
-    else *reinterpret_cast<float4*>(approx_out + ((size_t)map * kDb + bi) * (size_t)hm * hm + (size_t)Y * hm + X) = ll;
+    sara_epilogue4(mode, f4of(hl0, hl1), i_hl, a_hl, t_hl, coef, thr, scale, gamma, delta);   // x-high, y-low
+    sara_epilogue4(mode, f4of(lh0, lh1), i_lh, a_lh, t_lh, coef, thr, scale, gamma, delta);   // x-low, y-high
+    sara_epilogue4(mode, f4of(hh0, hh1), i_hh, a_hh, t_hh, coef, thr, scale, gamma, delta);
+    if (last) sara_epilogue4(mode, f4of(ll0, ll1), i_ll, a_ll, t_ll, coef, thr, scale, gamma, delta);
+    else
+      *reinterpret_cast<float4*>(approx_out + ((size_t)map * kDb + bi) * (size_t)hm * hm + (size_t)Y * hm + X) =
+          f4of(ll0, ll1);
   }
 }
 
-template <int RS>
-__device__ __forceinline__ void load_in_tile_t(const float* __restrict__ src, int m, int oy0, int ox0,
-                                               float* __restrict__ in_s) {
-  // Rows of RS floats starting at an even column: float2 loads (periodic wrap only at the last tile).
-  for (int i = threadIdx.x; i < RS * (RS / 2); i += blockDim.x) {
-    const int r = i / (RS / 2), c = 2 * (i - r * (RS / 2));
-    int y = 2 * oy0 + r, x = 2 * ox0 + c;
+// Input tile of one analysis CTA: RS rows from row 2 oy0 and the 80 columns from
+// column 2 ox0 (both modulo m), one bulk copy per row, two where the row wraps
+// around the periodic right edge (then the first piece is 64 columns).
+__device__ __forceinline__ void ana_issue_input(const float* __restrict__ src, int m, int oy0, int ox0, int RS,
+                                                float* __restrict__ in_s, uint64_t* bar) {
+  const int x0 = 2 * ox0;
+  const int first = min(kA2Cols, m - x0);
+  if (threadIdx.x == 0) mbar_expect_tx(bar, (uint32_t)(RS * kA2Cols * sizeof(float)));
+  for (int r = threadIdx.x; r < RS; r += blockDim.x) {
+    int y = 2 * oy0 + r;
     if (y >= m) y -= m;
-    if (x >= m) x -= m;
-    const float2 v = *reinterpret_cast<const float2*>(src + (size_t)y * m + x);
-    in_s[r * kPin + c] = v.x;
-    in_s[r * kPin + c + 1] = v.y;
+    const float* row = src + (size_t)y * m;
+    float* dst = in_s + r * kA2Pitch;
+    fence_proxy_async();
+    bulk_g2s(dst, row + x0, first * sizeof(float), bar);
+    if (first < kA2Cols) bulk_g2s(dst + first, row, (kA2Cols - first) * sizeof(float), bar);
   }
-}
-
-template <int LF>
-__device__ __forceinline__ void ana_basis(const float* src, int m, float* in_s, float* lo_s, float* hi_s, int bi,
-                                          int map, int n, int hm, int oy0, int ox0, int last, float* coef, float* thr,
-                                          float* approx_out, int mode, float scale, float gamma, float delta,
-                                          const float* st_a, const float* st_t, uint64_t* bar, int* err) {
-  load_in_tile_t<2 * kTO + LF - 2>(src, m, oy0, ox0, in_s);
-  __syncthreads();
-  ana_rows<LF>(in_s, lo_s, hi_s);
-  __syncthreads();
-  if (mode == SARA_DUAL && !mbar_wait(bar, 0)) {
-    atomicExch(err, 1);
-    return;   // copies that never completed: leave this tile unchanged (host reports PS_ETIMEOUT)
-  }
-  ana_cols<LF>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, st_a,
-               st_t);
-}
-
-__device__ __forceinline__ void ana_dispatch(int bi, const float* src, int m, float* in_s, float* lo_s, float* hi_s,
-                                             int map, int n, int hm, int oy0, int ox0, int last, float* coef,
-                                             float* thr, float* approx_out, int mode, float scale, float gamma,
-                                             float delta, const float* st_a, const float* st_t, uint64_t* bar,
-                                             int* err) {
-#define PS_ANA(LFv) ana_basis<LFv>(src, m, in_s, lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, \
-                                   mode, scale, gamma, delta, st_a, st_t, bar, err)
-  switch (bi) {
-    case 0: PS_ANA(2); break;
-    case 1: PS_ANA(4); break;
-    case 2: PS_ANA(6); break;
-    case 3: PS_ANA(8); break;
-    case 4: PS_ANA(10); break;
-    case 5: PS_ANA(12); break;
-    case 6: PS_ANA(14); break;
-    default: PS_ANA(16); break;
-  }
-#undef PS_ANA
 }
 
 // Shared-memory layout of the fast analysis kernels (floats): input tile, row-filtered
-// low/high tiles, the staged A and gamma W rows of the three detail subbands, mbarrier.
+// low/high tiles, the staged A and gamma W rows of the three detail subbands, and two
+// mbarriers (input tile, staged epilogue operands).
 constexpr int kStage = 3 * kTO * kTO;
-constexpr int kAnaFloats = kInSize + 2 * kRSmax * kPlo + 2 * kStage;
+constexpr int kAnaFloats = kA2In + 2 * kRSmax * kPlo + 2 * kStage;
+static_assert(kA2In % 4 == 0 && (kRSmax * kPlo) % 4 == 0 && kStage % 4 == 0, "16-byte aligned stage buffers");
 
 // The first 3 * 32 * 2 threads each start one bulk copy of this tile's A and gamma W
 // detail rows (3 subbands x 32 rows x 128 B) so they arrive while the rows are
@@ -436,17 +474,62 @@ __device__ __forceinline__ void stage_epilogue(const float* coef, const float* t
 
 struct AnaSmem {
   float *in_s, *lo_s, *hi_s, *st_a, *st_t;
-  uint64_t* bar;
+  uint64_t* bar;   // [0] input tile, [1] staged epilogue operands
 };
 __device__ __forceinline__ AnaSmem ana_smem(float4* sma) {
   AnaSmem a;
   a.in_s = reinterpret_cast<float*>(sma);
-  a.lo_s = a.in_s + kInSize;
+  a.lo_s = a.in_s + kA2In;
   a.hi_s = a.lo_s + kRSmax * kPlo;
   a.st_a = a.hi_s + kRSmax * kPlo;
   a.st_t = a.st_a + kStage;
   a.bar = reinterpret_cast<uint64_t*>(a.st_t + kStage);
   return a;
+}
+
+// A bounded wait gave up: raise the flag, give the copies in flight a second bounded
+// wait so none lands after the CTA has gone, and let the caller return.
+__device__ __forceinline__ void ana_abort(const AnaSmem& S, int staged, int* err) {
+  if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+    (void)mbar_wait(&S.bar[0], 0);
+    if (staged) (void)mbar_wait(&S.bar[1], 0);
+  }
+}
+
+// One basis of one tile: input copies (issued first), staged epilogue operands (dual
+// mode), rows, columns + epilogue.
+template <int LF>
+__device__ __forceinline__ void ana_basis(const float* src, int m, const AnaSmem& S, int bi, int map, int n, int hm,
+                                          int oy0, int ox0, int last, float* coef, float* thr, float* approx_out,
+                                          int mode, float scale, float gamma, float delta, int* err) {
+  ana_issue_input(src, m, oy0, ox0, 2 * kTO + LF - 2, S.in_s, &S.bar[0]);
+  if (mode == SARA_DUAL)
+    stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, S.st_a, S.st_t,
+                   &S.bar[1]);
+  const bool ok = mbar_wait(&S.bar[0], 0);
+  if (__syncthreads_or(!ok)) {
+    ana_abort(S, mode == SARA_DUAL, err);
+    return;   // this tile is left unchanged (the host reports PS_ETIMEOUT)
+  }
+  ana_rows<LF>(S.in_s, S.lo_s, S.hi_s);
+  __syncthreads();
+  if (mode == SARA_DUAL && !mbar_wait(&S.bar[1], 0)) {
+    atomicExch(err, 1);
+    (void)mbar_wait(&S.bar[1], 0);
+    return;
+  }
+  ana_cols<LF>(S.lo_s, S.hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta,
+               S.st_a, S.st_t);
+}
+
+__device__ __forceinline__ void ana_dispatch(int bi, const float* src, int m, const AnaSmem& S, int map, int n, int hm,
+                                             int oy0, int ox0, int last, float* coef, float* thr, float* approx_out,
+                                             int mode, float scale, float gamma, float delta, int* err) {
+#define PS_ANA(LFv) \
+  ana_basis<LFv>(src, m, S, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, err)
+  PS_SWITCH_LF(bi, PS_ANA)
+#undef PS_ANA
 }
 
 // Level-1 analysis: input is the map itself; one basis per CTA (grid.y).
@@ -458,12 +541,13 @@ __global__ void __launch_bounds__(256, 3) k_ana_l1(const float* __restrict__ X, 
   const int bi = blockIdx.y, map = blockIdx.z;
   const int hm = n >> 1, tilesx = hm / kTO;
   const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
-  if (threadIdx.x == 0) mbar_init(S.bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+  }
   __syncthreads();
-  if (mode == SARA_DUAL)
-    stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, S.st_a, S.st_t, S.bar);
-  ana_dispatch(bi, X + (size_t)map * n * n, n, S.in_s, S.lo_s, S.hi_s, map, n, hm, oy0, ox0, last, coef, thr,
-               approx_out, mode, scale, gamma, delta, S.st_a, S.st_t, S.bar, err);
+  ana_dispatch(bi, X + (size_t)map * n * n, n, S, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale,
+               gamma, delta, err);
 }
 
 // Levels >= 2 with half size >= 32: one basis per CTA (grid.y).
@@ -476,12 +560,13 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
   const int bi = blockIdx.y, map = blockIdx.z;
   const int hm = m >> 1, tilesx = hm / kTO;
   const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
-  if (threadIdx.x == 0) mbar_init(S.bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+  }
   __syncthreads();
-  if (mode == SARA_DUAL)
-    stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, S.st_a, S.st_t, S.bar);
-  ana_dispatch(bi, approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, S.in_s, S.lo_s, S.hi_s, map, n, hm, oy0,
-               ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, S.st_a, S.st_t, S.bar, err);
+  ana_dispatch(bi, approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, S, map, n, hm, oy0, ox0, last, coef, thr,
+               approx_out, mode, scale, gamma, delta, err);
 }
 
 // Synthesis of one basis on a TI x TI output tile, split in two steps so the
@@ -568,17 +653,6 @@ __device__ __forceinline__ void syn_compute(const float* __restrict__ s4, float*
   }
 }
 
-#define PS_SWITCH_LF(bi, CALL)    \
-  switch (bi) {                   \
-    case 0: CALL(2); break;       \
-    case 1: CALL(4); break;       \
-    case 2: CALL(6); break;       \
-    case 3: CALL(8); break;       \
-    case 4: CALL(10); break;      \
-    case 5: CALL(12); break;      \
-    case 6: CALL(14); break;      \
-    default: CALL(16); break;     \
-  }
 
 __device__ __forceinline__ void syn_load_dispatch(int bi, const float* cb, const float* apx, int n, int m, int oy0,
                                                   int ox0, float* s4) {
@@ -670,22 +744,6 @@ __global__ void __launch_bounds__(256, 4) k_syn_lv(const float* __restrict__ coe
 //   * Along x, each thread owns a 4 x 4 output block; the column-major
 //     intermediates give it two rows per 64-bit operand, so the taps are again
 //     packed FP32x2 FMAs with the coefficient duplicated in both halves.
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 f2pack(float a, float b) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(u64 v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 constexpr int kT2 = 64;                                  // output tile side
 constexpr int kC2Rows = kT2 / 2 + kMaxTaps / 2 - 1;      // 39 coefficient rows (db8 halo)
 constexpr int kC2Cols = kT2 / 2 + 8;                     // 40 staged columns: [ox0/2 - 8, ox0/2 + 32)
@@ -750,7 +808,7 @@ __device__ __forceinline__ void syn2_ypass(const float* __restrict__ s4, float* 
       for (int t = 0; t < 4; ++t) {
         const int j = t - 2 * (i - half);
         if (j >= 0 && j < LF) {
-          const u64 ph = f2pack(c_h[half][j], c_h[half][j]), pg = f2pack(c_g[half][j], c_g[half][j]);
+          const u64 ph = cdup(c_hd[half][j]), pg = cdup(c_gd[half][j]);
           lo[t] = ffma2(ph, vll, ffma2(pg, vlh, lo[t]));
           hi[t] = ffma2(ph, vhl, ffma2(pg, vhh, hi[t]));
         }
@@ -786,7 +844,7 @@ __device__ __forceinline__ void syn2_xpass(const float* __restrict__ loT, const 
     for (int t = 0; t < 4; ++t) {
       const int j = t - 2 * (i - half);
       if (j >= 0 && j < LF) {
-        const u64 ph = f2pack(c_h[half][j], c_h[half][j]), pg = f2pack(c_g[half][j], c_g[half][j]);
+        const u64 ph = cdup(c_hd[half][j]), pg = cdup(c_gd[half][j]);
         acc[2 * t] = ffma2(ph, vlo.x, ffma2(pg, vhi.x, acc[2 * t]));
         acc[2 * t + 1] = ffma2(ph, vlo.y, ffma2(pg, vhi.y, acc[2 * t + 1]));
       }
@@ -919,7 +977,6 @@ __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ co
     *reinterpret_cast<float4*>(dst + (size_t)(oy0 + 4 * rq + rr) * m + ox0 + 4 * cg) = syn2_row(acc, rr);
 }
 
-static_assert((kInSize + 2 * kRSmax * kPlo) % 4 == 0 && kStage % 4 == 0, "16-byte aligned stage buffers");
 static size_t fast_analysis_smem() { return (size_t)kAnaFloats * sizeof(float) + 16; }
 
 static size_t analysis_smem(int TO) {
