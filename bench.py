@@ -335,6 +335,9 @@ def run_own(args) -> None:
     gamma = 1e-3 * float(np.max(np.abs(s.psi_adjoint(dirty))))
     s.set_sara_weights(None, gamma)
     s.set_mode(B.PS_POLARIZED)
+    # Launch choices measured on this problem before the warm-up.
+    picks = B.ps_autotune(s.h, reps=5)
+    tuning = {k: v[0] for k, v in picks.items() if not k.startswith("reserved")}
 
     # Warm-up, then exactly K timed steps between barriers.
     s.pd_iterate(args.warmup)
@@ -434,7 +437,7 @@ def run_own(args) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "n": n, "stokes": 4, "M": M, "blocks": wl.nblocks, "levels": L,
                        "kernel_width": 7, "oversampling": 2, "grid_window": Wd,
-                       "parallelism": "replicas" if world > 1 else "single",
+                       "parallelism": "replicas" if world > 1 else "single", "tuning": tuning,
                        "l2": "no flush: per-iteration working set ~%.0f MB > 126 MB L2" % (total_bytes / 1e6),
                        "vis_iters_per_s": value * M},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -247,6 +247,32 @@ ps_status ps_batch_iterate(ps_batch* b, int32_t n_iter);   /* asynchronous on th
 ps_status ps_batch_synchronize(ps_batch* b);
 void ps_batch_destroy(ps_batch* b);
 
+/* Launch choices of the kernels (the paper runs the same operators in every
+ * iteration of Algorithm 1 and prescribes no implementation; which launch shape is
+ * fastest depends on the image size and on how the visibilities fill the uv plane,
+ * so it is measured on the handle's own problem). Values index the candidates: */
+enum {
+  PS_TUNE_SYNTHESIS = 0,  /* finest synthesis level: 0 double-buffered subband staging (2 CTAs/SM),
+                             1 single-buffered, refilled during the x-pass (4 CTAs/SM) */
+  PS_TUNE_DEGRID = 1,     /* 0 one row per thread over a work item,
+                             1 one same-cell chunk per warp (broadcast stencil reads) */
+  PS_TUNE_COUNT = 4       /* slots 2, 3 reserved (0) */
+};
+
+/* Autotuner: after ps_set_measurements, time every candidate of every PS_TUNE_*
+ * slot on the handle's data (reps launches each, CUDA events on the handle's
+ * stream, after one untimed launch) and keep the fastest. The state of the
+ * iteration is unchanged (the timed launches recompute Psi A of the current A and
+ * interpolate the current spectrum into scratch). choices (nullable) receives the
+ * PS_TUNE_COUNT picks; ms (nullable) receives, per slot, the time of the pick in
+ * milliseconds. Synchronises the stream. PS_ESTATE before measurements. */
+ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms);
+
+/* Read / force the launch choices (PS_TUNE_COUNT int32; PS_EINVAL for a value
+ * outside a slot's candidates). The defaults are 0. */
+ps_status ps_get_tuning(const ps_handle* h, int32_t* choices);
+ps_status ps_set_tuning(ps_handle* h, const int32_t* choices);
+
 /* Synchronise the handle's stream; reports a pending CUDA error. */
 ps_status ps_synchronize(ps_handle* h);
 

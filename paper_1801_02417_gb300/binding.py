@@ -86,6 +86,9 @@ _SIGS = {
     "ps_synchronize": (_I32, [_H]),
     "ps_device_bytes": (_I64, [_H]),
     "ps_estimate_bytes": (_I64, [_I32, _I32, _I64]),
+    "ps_autotune": (_I32, [_H, _I32, _P, _P]),
+    "ps_get_tuning": (_I32, [_H, _P]),
+    "ps_set_tuning": (_I32, [_H, _P]),
 }
 
 
@@ -344,3 +347,28 @@ def ps_device_bytes(h) -> int:
 
 def ps_estimate_bytes(n: int, levels: int, M: int) -> int:
     return int(lib().ps_estimate_bytes(int(n), int(levels), int(M)))
+
+
+TUNE_SLOTS = ("synthesis", "degrid", "reserved2", "reserved3")
+
+
+def ps_autotune(h, reps: int = 5) -> dict:
+    """Time every launch candidate on the handle's data and keep the fastest; returns
+    {slot: (choice, ms)}."""
+    ch = np.zeros(len(TUNE_SLOTS), dtype=np.int32)
+    ms = np.zeros(len(TUNE_SLOTS), dtype=np.float64)
+    _check(h, lib().ps_autotune(h, int(reps), ctypes.c_void_p(ch.ctypes.data), ctypes.c_void_p(ms.ctypes.data)))
+    return {k: (int(c), float(t)) for k, c, t in zip(TUNE_SLOTS, ch, ms)}
+
+
+def ps_get_tuning(h) -> list:
+    ch = np.zeros(len(TUNE_SLOTS), dtype=np.int32)
+    _check(h, lib().ps_get_tuning(h, ctypes.c_void_p(ch.ctypes.data)))
+    return ch.tolist()
+
+
+def ps_set_tuning(h, choices) -> None:
+    ch = np.ascontiguousarray(choices, dtype=np.int32)
+    if ch.size != len(TUNE_SLOTS):
+        raise ValueError(f"expected {len(TUNE_SLOTS)} tuning slots")
+    _check(h, lib().ps_set_tuning(h, ctypes.c_void_p(ch.ctypes.data)))

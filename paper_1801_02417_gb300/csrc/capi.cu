@@ -931,6 +931,91 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms) {
   return PS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: candidates per PS_TUNE_* slot, each timed on the handle's own data.
+static const int kTuneCandidates[PS_TUNE_COUNT] = {2, 2, 1, 1};
+
+// Mean milliseconds of `reps` launches of f after one untimed launch.
+extern "C++" {
+template <typename F>
+ps_status tune_time(Handle* h, int reps, F f, double* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(h, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  CK(h, e);
+  *ms = (double)t / reps;
+  return PS_OK;
+}
+}  // extern "C++"
+
+ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms) {
+  if (!h || reps < 1) return h ? fail(h, PS_EINVAL, "autotune: reps must be >= 1") : PS_EINVAL;
+  if (!h->have_meas) return fail(h, PS_ESTATE, "autotune: call ps_set_measurements first");
+  if (!h->derived_valid) {
+    ps_status st = compute_derived(h);
+    if (st != PS_OK) return st;
+  }
+  double best_ms[PS_TUNE_COUNT] = {0.0, 0.0, 0.0, 0.0};
+  auto pick = [&](int slot, auto launch) -> ps_status {
+    int best = 0;
+    double best_t = 0.0;
+    for (int v = 0; v < kTuneCandidates[slot]; ++v) {
+      h->tune[slot] = v;
+      double t = 0.0;
+      ps_status st = tune_time(h, reps, launch, &t);
+      if (st != PS_OK) return st;
+      if (v == 0 || t < best_t) {
+        best = v;
+        best_t = t;
+      }
+    }
+    h->tune[slot] = best;
+    best_ms[slot] = best_t;
+    return PS_OK;
+  };
+  // Synthesis: Psi A of the current coefficients, written where it already is.
+  ps_status st = pick(PS_TUNE_SYNTHESIS, [&] { return ps::sara_synthesis(h, h->A, h->PsiA); });
+  if (st != PS_OK) return st;
+  // Degridding: the spectrum of the current S interpolated into scratch.
+  if (h->M > 0) {
+    CK(h, ps::nufft_forward_grid(h, h->S));
+    st = pick(PS_TUNE_DEGRID, [&] { return ps::nufft_degrid(h, ps::DEG_APPLY, h->vtmp); });
+    if (st != PS_OK) return st;
+  }
+  drop_graph(h);
+  ++h->version;
+  if (choices) std::memcpy(choices, h->tune, sizeof(h->tune));
+  if (ms)
+    for (int i = 0; i < PS_TUNE_COUNT; ++i) ms[i] = best_ms[i];
+  return PS_OK;
+}
+
+ps_status ps_get_tuning(const ps_handle* h, int32_t* choices) {
+  if (!h || !choices) return PS_EINVAL;
+  std::memcpy(choices, h->tune, sizeof(h->tune));
+  return PS_OK;
+}
+
+ps_status ps_set_tuning(ps_handle* h, const int32_t* choices) {
+  if (!h || !choices) return h ? fail(h, PS_EINVAL, "set_tuning: null choices") : PS_EINVAL;
+  for (int i = 0; i < PS_TUNE_COUNT; ++i)
+    if (choices[i] < 0 || choices[i] >= kTuneCandidates[i])
+      return fail(h, PS_EINVAL, "set_tuning: slot " + std::to_string(i) + " out of range");
+  std::memcpy(h->tune, choices, sizeof(h->tune));
+  drop_graph(h);
+  ++h->version;
+  return PS_OK;
+}
+
 int32_t ps_kernels_per_iteration(const ps_handle* h) {
   if (!h) return 0;
   int k = 1;                                   // k_primal

@@ -99,6 +99,9 @@ struct Handle {
   float2 *tw = nullptr;       // K/2 twiddles exp(-2 pi i k / K)
   float *corr = nullptr;      // n de-apodisation factors 1 / phihat(2 pi x / K)
 
+  // Launch choices (PS_TUNE_* slots).
+  int32_t tune[PS_TUNE_COUNT] = {};
+
   // CUDA graph of one iteration.
   cudaGraphExec_t graph = nullptr;
   int graph_mode = -1;

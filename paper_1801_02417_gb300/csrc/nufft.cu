@@ -186,6 +186,85 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;  // valid in thread 0
 }
 
+// One row of a degridding work item (all 32 lanes of the warp call it together:
+// the block-sum combination is warp-collective). Inactive lanes add nothing.
+template <int W>
+__device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& it, const float4* __restrict__ rec,
+                                           const float4* Gp, const float4* Gn, int off, int full, int K, float beta,
+                                           int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
+                                           const float* __restrict__ cb, float inv_rho2,
+                                           const uint16_t* __restrict__ vblk, bool reduce, double* bsum,
+                                           float2* __restrict__ out) {
+  constexpr int TS = kGridTile;
+  constexpr int SS = TS + W - 1;
+  float4* R4 = reinterpret_cast<float4*>(R);
+  const float4* Y4 = reinterpret_cast<const float4*>(Yv);
+  int blk = -1;
+  double e2 = 0.0;
+  if (active) {
+    float fx, fy, w;
+    int cx, cy;
+    unpack_rec(rec[m], fx, fy, w, cx, cy);
+    float wx[W], wy[W];
+    es_weights<W>(fx, beta, wx);
+    es_weights<W>(fy, beta, wy);
+    // Local centre within the tile (tap j of +u at local j + lc; of -u at local (TS-1-lc) + j).
+    const int lcy = gidx(cy, off, full, K) - it.ty * TS, lcx = gidx(cx, off, full, K) - it.tx * TS;
+    const float4* gp = Gp + lcy * SS + lcx;
+    const float4* gn = Gn + (TS - 1 - lcy) * SS + (TS - 1 - lcx);
+    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
+#pragma unroll
+    for (int jy = 0; jy < W; ++jy) {
+      float4 ap = make_float4(0.f, 0.f, 0.f, 0.f), an = ap;
+#pragma unroll
+      for (int jx = 0; jx < W; ++jx) {
+        ap = f4fma(wx[jx], gp[jy * SS + jx], ap);
+        an = f4fma(wx[W - 1 - jx], gn[jy * SS + jx], an);
+      }
+      sp = f4fma(wy[jy], ap, sp);
+      sn = f4fma(wy[W - 1 - jy], an, sn);
+    }
+    // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
+    const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
+    const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
+    float4 v01 = make_float4(w * (FIr + FQr), w * (FIi + FQi), w * sp.z, w * sp.w);   // RR, RL = G2(u)
+    float4 v23 = make_float4(w * sn.z, -w * sn.w, w * (FIr - FQr), w * (FIi - FQi));  // LR = conj G2(-u), LL
+    if (mode == DEG_APPLY) {
+      float4* o4 = reinterpret_cast<float4*>(out);
+      o4[2 * (size_t)m] = v01;
+      o4[2 * (size_t)m + 1] = v23;
+    } else {
+      blk = vblk[m];
+      const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
+      if (mode == DEG_DUAL) {
+        const float cs = cb[blk] * inv_rho2;
+        const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
+        v01 = f4sub(f4fma(cs, r0, v01), y0);
+        v23 = f4sub(f4fma(cs, r1, v23), y1);
+        R4[2 * (size_t)m] = v01;
+        R4[2 * (size_t)m + 1] = v23;
+      } else {
+        v01 = f4sub(y0, v01);
+        v23 = f4sub(y1, v23);
+        if (out) {
+          float4* o4 = reinterpret_cast<float4*>(out);
+          o4[2 * (size_t)m] = v01;
+          o4[2 * (size_t)m + 1] = v23;
+        }
+      }
+      e2 = (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
+           (double)(v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
+    }
+  }
+  if (reduce) {
+    // Lanes holding the same block add their terms; the lowest such lane updates shared memory.
+    const unsigned peers = __match_any_sync(0xffffffffu, blk);
+    double sum = 0.0;
+    for (unsigned p = peers; p; p &= p - 1) sum += __shfl_sync(peers, e2, __ffs(p) - 1);
+    if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bsum[blk], sum);
+  }
+}
+
 // Interpolate the packed spectra at +u and -u, unpack the four Stokes spectra,
 // mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. One CTA per gridding
 // work item (rows whose tap centres lie in one kGridTile^2 tile): the spectrum
@@ -195,9 +274,9 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 // ||Y - phi X||^2 (RESID) are combined per warp over lanes of the same block, then
 // through shared-memory FP64 accumulators into global FP64 atomics (block_sum,
 // cleared by the caller).
-template <int W>
+template <int W, bool CHUNK>
 __global__ void __launch_bounds__(256) k_degrid(
-    const GridItem* __restrict__ items, const float4* __restrict__ rec, const float4* __restrict__ G, int Wd,
+    const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const float4* __restrict__ rec, const float4* __restrict__ G, int Wd,
     int off, int full, int K, float beta, int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
     const float* __restrict__ cb, float inv_rho2, const uint16_t* __restrict__ vblk, int nblocks,
     double* __restrict__ block_sum, float2* __restrict__ out) {
@@ -232,73 +311,21 @@ __global__ void __launch_bounds__(256) k_degrid(
     Gn[i] = vn;
   }
   __syncthreads();
-  float4* R4 = reinterpret_cast<float4*>(R);
-  const float4* Y4 = reinterpret_cast<const float4*>(Yv);
-  for (int base = it.vstart; base < it.vend; base += blockDim.x) {
-    const int m = base + threadIdx.x;
-    int blk = -1;
-    double e2 = 0.0;
-    if (m < it.vend) {
-      float fx, fy, w;
-      int cx, cy;
-      unpack_rec(rec[m], fx, fy, w, cx, cy);
-      float wx[W], wy[W];
-      es_weights<W>(fx, beta, wx);
-      es_weights<W>(fy, beta, wy);
-      // Local centre within the tile (tap j of +u at local j + lc; of -u at local (TS-1-lc) + j).
-      const int lcy = gidx(cy, off, full, K) - it.ty * TS, lcx = gidx(cx, off, full, K) - it.tx * TS;
-      const float4* gp = Gp + lcy * SS + lcx;
-      const float4* gn = Gn + (TS - 1 - lcy) * SS + (TS - 1 - lcx);
-      float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
-#pragma unroll
-      for (int jy = 0; jy < W; ++jy) {
-        float4 ap = make_float4(0.f, 0.f, 0.f, 0.f), an = ap;
-#pragma unroll
-        for (int jx = 0; jx < W; ++jx) {
-          ap = f4fma(wx[jx], gp[jy * SS + jx], ap);
-          an = f4fma(wx[W - 1 - jx], gn[jy * SS + jx], an);
-        }
-        sp = f4fma(wy[jy], ap, sp);
-        sn = f4fma(wy[W - 1 - jy], an, sn);
-      }
-      // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
-      const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
-      const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
-      float4 v01 = make_float4(w * (FIr + FQr), w * (FIi + FQi), w * sp.z, w * sp.w);   // RR, RL = G2(u)
-      float4 v23 = make_float4(w * sn.z, -w * sn.w, w * (FIr - FQr), w * (FIi - FQi));  // LR = conj G2(-u), LL
-      if (mode == DEG_APPLY) {
-        float4* o4 = reinterpret_cast<float4*>(out);
-        o4[2 * (size_t)m] = v01;
-        o4[2 * (size_t)m + 1] = v23;
-      } else {
-        blk = vblk[m];
-        const float4 y0 = Y4[2 * (size_t)m], y1 = Y4[2 * (size_t)m + 1];
-        if (mode == DEG_DUAL) {
-          const float cs = cb[blk] * inv_rho2;
-          const float4 r0 = R4[2 * (size_t)m], r1 = R4[2 * (size_t)m + 1];
-          v01 = f4sub(f4fma(cs, r0, v01), y0);
-          v23 = f4sub(f4fma(cs, r1, v23), y1);
-          R4[2 * (size_t)m] = v01;
-          R4[2 * (size_t)m + 1] = v23;
-        } else {
-          v01 = f4sub(y0, v01);
-          v23 = f4sub(y1, v23);
-          if (out) {
-            float4* o4 = reinterpret_cast<float4*>(out);
-            o4[2 * (size_t)m] = v01;
-            o4[2 * (size_t)m + 1] = v23;
-          }
-        }
-        e2 = (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
-             (double)(v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
-      }
+  if (CHUNK) {
+    // One same-cell chunk (<= 32 rows) per warp: every lane reads the same stencil
+    // cells, so the shared-memory gathers are broadcasts.
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int c = threadIdx.x >> 5; c < it.cend - it.cstart; c += nwarps) {
+      const int pk = chunks[it.cstart + c];
+      const int v0 = pk & 1023, cnt = (pk >> 10) & 63;
+      degrid_row<W>(it.vstart + v0 + lane, lane < cnt, it, rec, Gp, Gn, off, full, K, beta, mode, R, Yv, cb, inv_rho2,
+                    vblk, reduce, bsum, out);
     }
-    if (reduce) {
-      // Lanes holding the same block add their terms; the lowest such lane updates shared memory.
-      const unsigned peers = __match_any_sync(0xffffffffu, blk);
-      double sum = 0.0;
-      for (unsigned p = peers; p; p &= p - 1) sum += __shfl_sync(peers, e2, __ffs(p) - 1);
-      if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bsum[blk], sum);
+  } else {
+    for (int base = it.vstart; base < it.vend; base += blockDim.x) {
+      const int m = base + threadIdx.x;
+      degrid_row<W>(m, m < it.vend, it, rec, Gp, Gn, off, full, K, beta, mode, R, Yv, cb, inv_rho2, vblk, reduce, bsum,
+                    out);
     }
   }
   if (reduce) {
@@ -550,9 +577,12 @@ cudaError_t configure_nufft_kernels() {
   if ((e = set_smem((const void*)k_grid<7>, grid_smem<7>())) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_grid<9>, grid_smem<9>())) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
-  if ((e = set_smem((const void*)k_degrid<5>, degrid_smem_tiles<5>() + 2048 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_degrid<7>, degrid_smem_tiles<7>() + 2048 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_degrid<9>, degrid_smem_tiles<9>() + 2048 * sizeof(double))) != cudaSuccess) return e;
+  const void* degrids[] = {(const void*)k_degrid<5, false>, (const void*)k_degrid<7, false>,
+                           (const void*)k_degrid<9, false>, (const void*)k_degrid<5, true>,
+                           (const void*)k_degrid<7, true>,  (const void*)k_degrid<9, true>};
+  const size_t degrid_smem[] = {degrid_smem_tiles<5>(), degrid_smem_tiles<7>(), degrid_smem_tiles<9>()};
+  for (int i = 0; i < 6; ++i)
+    if ((e = set_smem(degrids[i], degrid_smem[i % 3] + 2048 * sizeof(double))) != cudaSuccess) return e;
   return set_smem((const void*)k_adj_cols, sm2);
 }
 
@@ -568,9 +598,10 @@ template <int W>
 static void launch_degrid(Handle* h, int mode, float2* out) {
   const GridGeom& g = h->g;
   const size_t sm = degrid_smem_tiles<W>() + (size_t)h->nblocks * sizeof(double);
-  k_degrid<W><<<h->nitems, 256, sm, h->stream>>>(h->items, h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode, h->R,
-                                                 h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->nblocks,
-                                                 h->block_sum, out);
+  auto kern = h->tune[PS_TUNE_DEGRID] ? k_degrid<W, true> : k_degrid<W, false>;
+  kern<<<h->nitems, 256, sm, h->stream>>>(h->items, h->gchunks, h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode,
+                                          h->R, h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->nblocks,
+                                          h->block_sum, out);
 }
 
 cudaError_t nufft_degrid(Handle* h, int mode, float2* out) {

@@ -889,12 +889,16 @@ __device__ __forceinline__ void syn2_abort(uint64_t* b0, uint32_t p0, uint64_t* 
 }
 
 // Finest level (m = n >= 64): the eight bases plus the Dirac part summed in registers -> Psi A.
-__global__ void __launch_bounds__(256, 2) k_syn2_fine(const float* __restrict__ coef,
-                                                      const float* __restrict__ approx_in, int coarsest, int n,
-                                                      float* __restrict__ out, int* err) {
+// NBUF = 2: two staging sets, basis b+1 copied while basis b is filtered (2 CTAs per SM).
+// NBUF = 1: one staging set, refilled with basis b+1 as soon as the y-pass of basis b
+// has read it, so the copy overlaps the x-pass (4 CTAs per SM hide the rest).
+template <int NBUF>
+__global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
+    k_syn2_fine(const float* __restrict__ coef, const float* __restrict__ approx_in, int coarsest, int n,
+                float* __restrict__ out, int* err) {
   extern __shared__ float4 sm2[];
-  float* const s4 = reinterpret_cast<float*>(sm2);   // two sets: basis b in set b & 1
-  float* loT = s4 + 2 * kC2Set;
+  float* const s4 = reinterpret_cast<float*>(sm2);   // staging set(s): basis b in set b % NBUF
+  float* loT = s4 + NBUF * kC2Set;
   float* hiT = loT + kLoSize;
   uint64_t* bar = reinterpret_cast<uint64_t*>(hiT + kLoSize);
   const int map = blockIdx.z, tilesx = n / kT2;
@@ -905,29 +909,33 @@ __global__ void __launch_bounds__(256, 2) k_syn2_fine(const float* __restrict__ 
   auto apxp = [&](int bi) {
     return coarsest ? (const float*)nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
   };
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-  }
+  auto set = [&](int bi) { return s4 + (bi % NBUF) * kC2Set; };
+  // Barrier of basis bi and the parity of its phase (each barrier completes once per use).
+  auto bar_of = [&](int bi) { return &bar[bi % NBUF]; };
+  auto par_of = [&](int bi) { return (uint32_t)((bi / NBUF) & 1); };
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NBUF; ++q) mbar_init(&bar[q], 1);
   __syncthreads();
-  syn2_issue(0, cbp(0), apxp(0), n, hm, oy0, ox0, s4, &bar[0]);
+  syn2_issue(0, cbp(0), apxp(0), n, hm, oy0, ox0, set(0), bar_of(0));
   u64 acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0ull;
   for (int bi = 0; bi < kDb; ++bi) {
-    // Buffer (bi+1)&1 last fed the y-pass of basis bi-1, which ended at a barrier.
-    if (bi + 1 < kDb)
-      syn2_issue(bi + 1, cbp(bi + 1), apxp(bi + 1), n, hm, oy0, ox0, s4 + ((bi + 1) & 1) * kC2Set,
-                 &bar[(bi + 1) & 1]);
-    const bool ok = mbar_wait(&bar[bi & 1], (bi >> 1) & 1);
+    // NBUF = 2: set (bi+1)&1 last fed the y-pass of basis bi-1, which ended at a barrier.
+    if (NBUF == 2 && bi + 1 < kDb) syn2_issue(bi + 1, cbp(bi + 1), apxp(bi + 1), n, hm, oy0, ox0, set(bi + 1),
+                                              bar_of(bi + 1));
+    const bool ok = mbar_wait(bar_of(bi), par_of(bi));
     // Also orders the previous x-pass' reads of loT/hiT before this y-pass writes them.
     if (__syncthreads_or(!ok)) {
-      syn2_abort(&bar[bi & 1], (bi >> 1) & 1, bi + 1 < kDb ? &bar[(bi + 1) & 1] : nullptr, ((bi + 1) >> 1) & 1,
-                 err);
+      const bool next = NBUF == 2 && bi + 1 < kDb;
+      syn2_abort(bar_of(bi), par_of(bi), next ? bar_of(bi + 1) : nullptr, next ? par_of(bi + 1) : 0u, err);
       return;
     }
-    syn2_ypass_dispatch(bi, s4 + (bi & 1) * kC2Set, loT, hiT);
+    syn2_ypass_dispatch(bi, set(bi), loT, hiT);
     __syncthreads();
+    // NBUF = 1: the set is free once every y-pass read of it has passed the barrier above.
+    if (NBUF == 1 && bi + 1 < kDb) syn2_issue(bi + 1, cbp(bi + 1), apxp(bi + 1), n, hm, oy0, ox0, set(bi + 1),
+                                              bar_of(bi + 1));
     syn2_xpass_dispatch(bi, loT, hiT, acc);
   }
   const int rq = threadIdx.x & 15, cg = threadIdx.x >> 4;
@@ -1003,11 +1011,15 @@ cudaError_t configure_kernels() {
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
-  e = cudaFuncSetAttribute((const void*)k_syn2_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn2_smem(2));
+  e = cudaFuncSetAttribute((const void*)k_syn2_fine<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syn2_smem(2));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)k_syn2_fine<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syn2_smem(1));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute((const void*)k_syn2_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn2_smem(1));
   if (e != cudaSuccess) return e;
-  for (const void* f : {(const void*)k_syn2_fine, (const void*)k_syn2_lv}) {
+  for (const void* f : {(const void*)k_syn2_fine<2>, (const void*)k_syn2_fine<1>, (const void*)k_syn2_lv}) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
@@ -1051,9 +1063,10 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
 }
 
 // Psi A on `stream` with `approx` as the per-level approximation scratch
-// (2 x 32 x (n/2)^2 floats); `err` (may be null) receives the bounded-wait flag.
+// (2 x 32 x (n/2)^2 floats); `err` (may be null) receives the bounded-wait flag;
+// `variant` is the PS_TUNE_SYNTHESIS choice of the finest level.
 static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx,
-                                    int* err) {
+                                    int* err, int variant) {
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
   float* buf[2] = {approx, approx + quarter};
   for (int l = L; l >= 1; --l) {
@@ -1063,7 +1076,9 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
     const float* ain = (l == L) ? nullptr : buf[l & 1];
     float* aout = (l == 1) ? nullptr : buf[(l - 1) & 1];
     if (m >= kT2 && l == 1) {
-      k_syn2_fine<<<dim3((m / kT2) * (m / kT2), 1, 4), 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err);
+      const dim3 grid((m / kT2) * (m / kT2), 1, 4);
+      if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err);
+      else k_syn2_fine<2><<<grid, 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err);
     } else if (m >= kT2) {
       k_syn2_lv<<<dim3((m / kT2) * (m / kT2), kDb, 4), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
                                                                                      err);
@@ -1080,7 +1095,7 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
 }
 
 cudaError_t sara_synthesis(Handle* h, const float* coef, float* out) {
-  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->dev_flags);
+  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->dev_flags, h->tune[PS_TUNE_SYNTHESIS]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1142,7 +1157,7 @@ extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, in
     }
     scratch = g_static_ptr[dev];
   }
-  e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, nullptr);
+  e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, nullptr, 0);
   if (e != cudaSuccess) {
     set_global_error(std::string("apply_psi_static: launch: ") + cudaGetErrorString(e));
     return PS_ECUDA;
