@@ -37,7 +37,8 @@ def sources() -> list[str]:
 def build_library(force: bool = False, verbose: bool = False) -> str:
     """Compile every source for sm_103a and link libpolsara.so; returns its path."""
     srcs = sources()
-    deps = srcs + [os.path.join(INCLUDE, "polsara.h"), os.path.join(CSRC, "internal.h")]
+    deps = srcs + [os.path.join(INCLUDE, "polsara.h"), os.path.join(CSRC, "internal.h"),
+            os.path.join(CSRC, "packed.cuh")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "packed.cuh"
 
 namespace ps {
 
@@ -212,18 +213,32 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
     const int lcy = gidx(cy, off, full, K) - it.ty * TS, lcx = gidx(cx, off, full, K) - it.tx * TS;
     const float4* gp = Gp + lcy * SS + lcx;
     const float4* gn = Gn + (TS - 1 - lcy) * SS + (TS - 1 - lcx);
-    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
+    // Packed FP32x2: channels (x, y) and (z, w) of each float4 cell in one FMA each.
+    u64 sp0 = 0ull, sp1 = 0ull, sn0 = 0ull, sn1 = 0ull;
 #pragma unroll
     for (int jy = 0; jy < W; ++jy) {
-      float4 ap = make_float4(0.f, 0.f, 0.f, 0.f), an = ap;
+      u64 ap0 = 0ull, ap1 = 0ull, an0 = 0ull, an1 = 0ull;
 #pragma unroll
       for (int jx = 0; jx < W; ++jx) {
-        ap = f4fma(wx[jx], gp[jy * SS + jx], ap);
-        an = f4fma(wx[W - 1 - jx], gn[jy * SS + jx], an);
+        const ulonglong2 vp = *reinterpret_cast<const ulonglong2*>(gp + jy * SS + jx);
+        const ulonglong2 vn = *reinterpret_cast<const ulonglong2*>(gn + jy * SS + jx);
+        const u64 kp = fdup(wx[jx]), kn = fdup(wx[W - 1 - jx]);
+        ap0 = ffma2(kp, vp.x, ap0);
+        ap1 = ffma2(kp, vp.y, ap1);
+        an0 = ffma2(kn, vn.x, an0);
+        an1 = ffma2(kn, vn.y, an1);
       }
-      sp = f4fma(wy[jy], ap, sp);
-      sn = f4fma(wy[W - 1 - jy], an, sn);
+      const u64 ky = fdup(wy[jy]), kny = fdup(wy[W - 1 - jy]);
+      sp0 = ffma2(ky, ap0, sp0);
+      sp1 = ffma2(ky, ap1, sp1);
+      sn0 = ffma2(kny, an0, sn0);
+      sn1 = ffma2(kny, an1, sn1);
     }
+    float4 sp, sn;
+    f2unpack(sp0, sp.x, sp.y);
+    f2unpack(sp1, sp.z, sp.w);
+    f2unpack(sn0, sn.x, sn.y);
+    f2unpack(sn1, sn.z, sn.w);
     // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
     const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
     const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
@@ -424,42 +439,41 @@ __global__ void __launch_bounds__(256) k_grid(
   for (int c = warp; c < nc; c += nwarps) {
     const int pk = chunks[it.cstart + c];
     const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
+    // a2[q][p] holds channels (2p, 2p+1) of kernel cell q: packed FP32x2 accumulation.
+    u64 a2[CPL][4];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a2[q][p] = 0ull;
+    const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x4);
+    int v = v0;
+    for (; v + 1 < v0 + cnt; v += 2) {
+      const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1], y0 = xv[2 * v + 2], y1 = xv[2 * v + 3];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const u64 k0 = fdup(wxl[q][v] * wyl[q][v]), k1 = fdup(wxl[q][v + 1] * wyl[q][v + 1]);
+        a2[q][0] = ffma2(k1, y0.x, ffma2(k0, x0.x, a2[q][0]));
+        a2[q][1] = ffma2(k1, y0.y, ffma2(k0, x0.y, a2[q][1]));
+        a2[q][2] = ffma2(k1, y1.x, ffma2(k0, x1.x, a2[q][2]));
+        a2[q][3] = ffma2(k1, y1.y, ffma2(k0, x1.y, a2[q][3]));
+      }
+    }
+    if (v < v0 + cnt) {
+      const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const u64 k0 = fdup(wxl[q][v] * wyl[q][v]);
+        a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
+        a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
+        a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
+        a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
+      }
+    }
     float a[CPL][8];
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) a[q][ch] = 0.f;
-    int v = v0;
-    for (; v + 1 < v0 + cnt; v += 2) {
-      const float4 x0 = x4[2 * v], x1 = x4[2 * v + 1], y0 = x4[2 * v + 2], y1 = x4[2 * v + 3];
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const float k0 = wxl[q][v] * wyl[q][v], k1 = wxl[q][v + 1] * wyl[q][v + 1];
-        a[q][0] = fmaf(k1, y0.x, fmaf(k0, x0.x, a[q][0]));
-        a[q][1] = fmaf(k1, y0.y, fmaf(k0, x0.y, a[q][1]));
-        a[q][2] = fmaf(k1, y0.z, fmaf(k0, x0.z, a[q][2]));
-        a[q][3] = fmaf(k1, y0.w, fmaf(k0, x0.w, a[q][3]));
-        a[q][4] = fmaf(k1, y1.x, fmaf(k0, x1.x, a[q][4]));
-        a[q][5] = fmaf(k1, y1.y, fmaf(k0, x1.y, a[q][5]));
-        a[q][6] = fmaf(k1, y1.z, fmaf(k0, x1.z, a[q][6]));
-        a[q][7] = fmaf(k1, y1.w, fmaf(k0, x1.w, a[q][7]));
-      }
-    }
-    if (v < v0 + cnt) {
-      const float4 x0 = x4[2 * v], x1 = x4[2 * v + 1];
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const float k0 = wxl[q][v] * wyl[q][v];
-        a[q][0] = fmaf(k0, x0.x, a[q][0]);
-        a[q][1] = fmaf(k0, x0.y, a[q][1]);
-        a[q][2] = fmaf(k0, x0.z, a[q][2]);
-        a[q][3] = fmaf(k0, x0.w, a[q][3]);
-        a[q][4] = fmaf(k0, x1.x, a[q][4]);
-        a[q][5] = fmaf(k0, x1.y, a[q][5]);
-        a[q][6] = fmaf(k0, x1.z, a[q][6]);
-        a[q][7] = fmaf(k0, x1.w, a[q][7]);
-      }
-    }
+      for (int p = 0; p < 4; ++p) f2unpack(a2[q][p], a[q][2 * p], a[q][2 * p + 1]);
     const int cbase = ly * SS + lx;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {

@@ -19,6 +19,7 @@
 #include <string>
 
 #include "internal.h"
+#include "packed.cuh"
 
 namespace ps {
 
@@ -51,22 +52,6 @@ cudaError_t upload_filters(const double h[kDb][kMaxTaps]) {
   return e;
 }
 
-// ---- Packed FP32x2 arithmetic (two lanes of one 64-bit register pair).
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 f2pack(float a, float b) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(u64 v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // A tap pair as one 64-bit FMA operand: {c[j], c[j+1]} (j even) or a duplicated tap.
 __device__ __forceinline__ u64 cpair(const float* c) { return *reinterpret_cast<const u64*>(c); }
 __device__ __forceinline__ u64 cdup(const float2& c) { return *reinterpret_cast<const u64*>(&c); }
