@@ -98,7 +98,7 @@ static void free_vis(Handle* h) {
   dfree(h, h->G, Wd * Wd);
   dfree(h, h->Acc, 2 * Wd * Wd);
   dfree(h, h->T2, (size_t)h->n * Wd);
-  dfree(h, h->tw, (size_t)h->g.K / 2);
+  dfree(h, h->tw, (size_t)h->g.K);
   dfree(h, h->corr, (size_t)h->n);
   h->M = h->nblocks = h->nitems = h->ngchunks = 0;
   h->g = ps::GridGeom{};
@@ -543,17 +543,19 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
             dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess && dalloc(h, &h->vblk, (size_t)M) == cudaSuccess &&
             dalloc(h, &h->T1, (size_t)h->n * Wd) == cudaSuccess && dalloc(h, &h->G, Wd * Wd) == cudaSuccess &&
             dalloc(h, &h->Acc, 2 * Wd * Wd) == cudaSuccess && dalloc(h, &h->T2, (size_t)h->n * Wd) == cudaSuccess &&
-            dalloc(h, &h->tw, (size_t)g.K / 2) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess;
+            dalloc(h, &h->tw, (size_t)g.K) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_vis(h);
     return fail(h, PS_ENOMEM, "set_measurements: device allocation failed");
   }
-  std::vector<float2> twh(g.K / 2);
-  for (int k = 0; k < g.K / 2; ++k) {
-    const double a = -2.0 * M_PI * k / g.K;
-    twh[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+  // Twiddles of radix-2 stage t (span 2^(t+1)) at [2^t - 1, 2^(t+1) - 1): exp(-2 pi i p / 2^(t+1)).
+  std::vector<float2> twh(g.K, make_float2(0.f, 0.f));
+  for (int t = 0; t < g.logK; ++t)
+    for (int p = 0; p < (1 << t); ++p) {
+      const double a = -2.0 * M_PI * p / (double)(2 << t);
+      twh[(1 << t) - 1 + p] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
   std::vector<float> corrh(h->n);
   for (int q = 0; q < h->n; ++q)
     corrh[q] = (float)(1.0 / ps::es_fourier(2.0 * M_PI * (q - h->n / 2) / g.K, g.W, g.beta));

@@ -18,6 +18,7 @@ constexpr int kGridTile = 16;    // gridding tile side (cells)
 constexpr int kChunk = 1024;     // visibilities per reduction chunk
 constexpr int kGridItem = 512;   // visibilities per gridding work item
 constexpr int kBinChunk = 32;    // visibilities per same-cell accumulation chunk
+constexpr int kWarpBins = 64;    // l2 blocks up to which degridding keeps per-warp FP64 block sums
 
 // Analysis / synthesis kernel modes.
 enum { SARA_DUAL = 0, SARA_APPLY = 1, SARA_REWEIGHT = 2 };
@@ -96,7 +97,7 @@ struct Handle {
   float4 *G = nullptr;        // Wd x Wd packed spectra (I+iQ, U+iV)
   float4 *Acc = nullptr;      // Wd x Wd x 2 gridding accumulators (xI, xQ | xU, xV)
   float4 *T2 = nullptr;       // n x Wd column-transformed adjoint
-  float2 *tw = nullptr;       // K/2 twiddles exp(-2 pi i k / K)
+  float2 *tw = nullptr;       // K per-stage twiddles: stage t at [2^t - 1, 2^(t+1) - 1)
   float *corr = nullptr;      // n de-apodisation factors 1 / phihat(2 pi x / K)
 
   // Launch choices (PS_TUNE_* slots).

@@ -45,51 +45,70 @@ __device__ __forceinline__ float4 cmul2(float4 a, float2 w) {
 }
 __device__ __forceinline__ int bitrev(int i, int logK) { return (int)(__brev((unsigned)i) >> (32 - logK)); }
 
-// In-place decimation-in-time FFT of K float4 (two complex sequences) held in
-// shared memory in bit-reversed order; output in natural order. INV selects
-// exp(+2 pi i jk/K) (no 1/K normalisation). Radix-2 stages s and s+1 are done
-// together by one thread on the four elements a, a+h, a+2h, a+3h (h = 2^s, bits s
-// and s+1 of a clear), so there is one shared-memory pass and one barrier per two
-// stages; an odd stage count ends with a plain radix-2 stage.
+// Bank-group swizzle of float4 indices in the FFT buffers. Bits 0-2 of an index
+// pick one of the eight 16-byte bank groups of a 128-byte row; they are XORed with
+// a linear (GF(2)) function of the higher bits chosen so that the eight lanes of a
+// quarter-warp hit eight different groups in every access pattern of the
+// transforms: the bit-reversed scatter (lanes differ in the top three index bits),
+// the radix-4 passes of stages (0,1) and (2,3) (lanes differ in bits 2-4, resp. 0,
+// 1 and 4), the later passes and the natural-order reads (bits 0-2). Being linear,
+// fsw(a ^ d) = fsw(a) ^ fsw(d).
+__device__ __forceinline__ int fsw(int i) {
+  const int h = i >> 5;
+  const int r = (h ^ (h >> 3) ^ (h >> 6)) & 7;   // bit t: XOR of index bits 5+t, 8+t, 11+t
+  return i ^ ((i >> 3) & 1) ^ (((i >> 4) & 1) * 6) ^ ((r & 1) << 1) ^ ((r & 2) << 1) ^ ((r >> 2) & 1);
+}
+
+// Twiddle p of radix-2 stage t (span 2^(t+1)): tw[2^t - 1 + p] = exp(-2 pi i p / 2^(t+1));
+// each stage's twiddles are contiguous, so the lanes of a pass read consecutive words.
 template <bool INV>
-__device__ __forceinline__ float2 twiddle(const float2* tw, int idx) {
-  float2 w = tw[idx];
+__device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int idx) {
+  float2 w = __ldg(tw + idx);
   if (INV) w.y = -w.y;
   return w;
 }
 
+// In-place decimation-in-time FFT of K = 2^logK float4 (two complex sequences) held
+// in shared memory (swizzled by fsw) in bit-reversed order; output in natural
+// order. INV selects exp(+2 pi i jk/K) (no 1/K normalisation). Radix-2 stages s
+// and s+1 are done together by one thread on the four elements a, a+h, a+2h, a+3h
+// (h = 2^s, bits s and s+1 of a clear), so there is one shared-memory pass and one
+// barrier per two stages; an odd stage count ends with a plain radix-2 stage.
 template <bool INV>
-__device__ void fft_smem(float4* buf, const float2* tw, int K, int logK) {
+__device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK) {
+  const int K = 1 << logK;
   int s = 0;
   for (; s + 1 < logK; s += 2) {
     const int hs = 1 << s;
+    const int c1 = fsw(hs), c2 = fsw(2 * hs);
     for (int g = threadIdx.x; g < (K >> 2); g += blockDim.x) {
       const int pos = g & (hs - 1);
-      const int a = ((g >> s) << (s + 2)) + pos;
-      const float2 w0 = twiddle<INV>(tw, pos * (K >> (s + 1)));          // stage s
-      const float2 w1 = twiddle<INV>(tw, pos * (K >> (s + 2)));          // stage s+1, pair (a, a+2h)
-      const float2 w2 = twiddle<INV>(tw, (pos + hs) * (K >> (s + 2)));   // stage s+1, pair (a+h, a+3h)
-      const float4 x0 = buf[a], x1 = buf[a + hs], x2 = buf[a + 2 * hs], x3 = buf[a + 3 * hs];
+      const int a = fsw(((g >> s) << (s + 2)) + pos);
+      const float2 w0 = twid<INV>(tw, hs - 1 + pos);          // stage s
+      const float2 w1 = twid<INV>(tw, 2 * hs - 1 + pos);      // stage s+1, pair (a, a+2h)
+      const float2 w2 = twid<INV>(tw, 3 * hs - 1 + pos);      // stage s+1, pair (a+h, a+3h)
+      const float4 x0 = buf[a], x1 = buf[a ^ c1], x2 = buf[a ^ c2], x3 = buf[a ^ c1 ^ c2];
       const float4 t1 = cmul2(x1, w0), t3 = cmul2(x3, w0);
       const float4 y0 = f4add(x0, t1), y1 = f4sub(x0, t1), y2 = f4add(x2, t3), y3 = f4sub(x2, t3);
       const float4 u2 = cmul2(y2, w1), u3 = cmul2(y3, w2);
       buf[a] = f4add(y0, u2);
-      buf[a + 2 * hs] = f4sub(y0, u2);
-      buf[a + hs] = f4add(y1, u3);
-      buf[a + 3 * hs] = f4sub(y1, u3);
+      buf[a ^ c2] = f4sub(y0, u2);
+      buf[a ^ c1] = f4add(y1, u3);
+      buf[a ^ c1 ^ c2] = f4sub(y1, u3);
     }
     __syncthreads();
   }
   if (s < logK) {
     const int hs = 1 << s;
+    const int c1 = fsw(hs);
     for (int b = threadIdx.x; b < (K >> 1); b += blockDim.x) {
       const int pos = b & (hs - 1);
-      const int i0 = ((b >> s) << (s + 1)) + pos;
-      const float2 w = twiddle<INV>(tw, pos * (K >> (s + 1)));
+      const int i0 = fsw(((b >> s) << (s + 1)) + pos);
+      const float2 w = twid<INV>(tw, hs - 1 + pos);
       const float4 u = buf[i0];
-      const float4 v = cmul2(buf[i0 + hs], w);
+      const float4 v = cmul2(buf[i0 ^ c1], w);
       buf[i0] = f4add(u, v);
-      buf[i0 + hs] = f4sub(u, v);
+      buf[i0 ^ c1] = f4sub(u, v);
     }
     __syncthreads();
   }
@@ -105,9 +124,7 @@ __global__ void k_fwd_rows(const float* __restrict__ X, int n, int N, const floa
                            int Wd, int off, int full) {
   extern __shared__ float4 sm[];
   float4* buf = sm;
-  float2* stw = reinterpret_cast<float2*>(sm + K);
   const int p = blockIdx.x;
-  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   const float cy = corr[p];
@@ -116,14 +133,14 @@ __global__ void k_fwd_rows(const float* __restrict__ X, int n, int N, const floa
     const int idx = (q - n / 2 + K) & (K - 1);
     const float c = cy * corr[q];
     const size_t o = row + q;
-    buf[bitrev(idx, logK)] = make_float4(X[o] * c, X[N + o] * c, X[2 * (size_t)N + o] * c,
-                                         X[3 * (size_t)N + o] * c);
+    buf[fsw(bitrev(idx, logK))] = make_float4(X[o] * c, X[N + o] * c, X[2 * (size_t)N + o] * c,
+                                              X[3 * (size_t)N + o] * c);
   }
   __syncthreads();
-  fft_smem<false>(buf, stw, K, logK);
+  fft_smem<false>(buf, tw, logK);
   for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
     const int k = full ? gx : gx - off;
-    T1[(size_t)p * Wd + gx] = buf[(k + K) & (K - 1)];
+    T1[(size_t)p * Wd + gx] = buf[fsw((k + K) & (K - 1))];
   }
 }
 
@@ -131,20 +148,18 @@ __global__ void k_fwd_cols(const float4* __restrict__ T1, int n, const float2* _
                            int logK, float4* __restrict__ G, int Wd, int off, int full) {
   extern __shared__ float4 sm[];
   float4* buf = sm;
-  float2* stw = reinterpret_cast<float2*>(sm + K);
   const int gx = blockIdx.x;
-  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int idx = (p - n / 2 + K) & (K - 1);
-    buf[bitrev(idx, logK)] = T1[(size_t)p * Wd + gx];
+    buf[fsw(bitrev(idx, logK))] = T1[(size_t)p * Wd + gx];
   }
   __syncthreads();
-  fft_smem<false>(buf, stw, K, logK);
+  fft_smem<false>(buf, tw, logK);
   for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
     const int k = full ? gy : gy - off;
-    G[(size_t)gy * Wd + gx] = buf[(k + K) & (K - 1)];
+    G[(size_t)gy * Wd + gx] = buf[fsw((k + K) & (K - 1))];
   }
 }
 
@@ -194,14 +209,15 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
                                            const float4* Gp, const float4* Gn, int off, int full, int K, float beta,
                                            int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
                                            const float* __restrict__ cb, float inv_rho2,
-                                           const uint16_t* __restrict__ vblk, bool reduce, double* bsum,
+                                           const uint16_t* __restrict__ vblk, bool reduce, bool private_bins,
+                                           double* bsum,
                                            float2* __restrict__ out) {
   constexpr int TS = kGridTile;
   constexpr int SS = TS + W - 1;
   float4* R4 = reinterpret_cast<float4*>(R);
   const float4* Y4 = reinterpret_cast<const float4*>(Yv);
   int blk = -1;
-  double e2 = 0.0;
+  float e2 = 0.f;
   if (active) {
     float fx, fy, w;
     int cx, cy;
@@ -267,16 +283,23 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
           o4[2 * (size_t)m + 1] = v23;
         }
       }
-      e2 = (double)(v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
-           (double)(v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
+      e2 = (v01.x * v01.x + v01.y * v01.y + v01.z * v01.z + v01.w * v01.w) +
+           (v23.x * v23.x + v23.y * v23.y + v23.z * v23.z + v23.w * v23.w);
     }
   }
   if (reduce) {
-    // Lanes holding the same block add their terms; the lowest such lane updates shared memory.
+    // Lanes holding the same block add their terms (FP32, at most 32 of them); the
+    // lowest such lane adds the group's sum in FP64 to this warp's bin of the block
+    // (private bins: no other lane or warp writes it) or, with many blocks, to the
+    // CTA's shared bin by an atomic.
     const unsigned peers = __match_any_sync(0xffffffffu, blk);
-    double sum = 0.0;
+    float sum = 0.f;
     for (unsigned p = peers; p; p &= p - 1) sum += __shfl_sync(peers, e2, __ffs(p) - 1);
-    if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&bsum[blk], sum);
+    if (blk >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+      if (private_bins) bsum[(threadIdx.x >> 5) * kWarpBins + blk] += (double)sum;
+      else atomicAdd(&bsum[blk], (double)sum);
+    }
+    __syncwarp();   // the next row's leader of this block may be another lane
   }
 }
 
@@ -286,9 +309,10 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
 // cells every tap of the item can touch at +u, and the mirrored cells at -u, are
 // staged in shared memory once; each thread then interpolates one row with taps at
 // fixed offsets from its centre. Per-block sums of ||B~/rho2 - Y||^2 (DUAL) or
-// ||Y - phi X||^2 (RESID) are combined per warp over lanes of the same block, then
-// through shared-memory FP64 accumulators into global FP64 atomics (block_sum,
-// cleared by the caller).
+// ||Y - phi X||^2 (RESID): per row and per warp group of same-block lanes in FP32,
+// then in FP64 through per-warp shared bins (up to kWarpBins blocks; shared FP64
+// atomics beyond) and one global FP64 atomic per block and CTA (block_sum, cleared
+// by the caller).
 template <int W, bool CHUNK>
 __global__ void __launch_bounds__(256) k_degrid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const float4* __restrict__ rec, const float4* __restrict__ G, int Wd,
@@ -304,8 +328,10 @@ __global__ void __launch_bounds__(256) k_degrid(
   double* bsum = reinterpret_cast<double*>(smd + 2 * SS * SS);
   const GridItem it = items[blockIdx.x];
   const bool reduce = (mode != DEG_APPLY);
+  const bool private_bins = nblocks <= kWarpBins;   // per-warp bins: kWarpBins x 8 warps doubles
+  const int nbins = private_bins ? kWarpBins * (blockDim.x >> 5) : nblocks;
   if (reduce)
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) bsum[b] = 0.0;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) bsum[b] = 0.0;
   // Grid frequency (k) of local row 0: +u region starts at tile origin - hw; the -u region
   // holds frequencies -(centre) - hw + j for every centre of the tile.
   const int ky0 = it.ty * TS - hw - (full ? 0 : off), kx0 = it.tx * TS - hw - (full ? 0 : off);
@@ -334,19 +360,25 @@ __global__ void __launch_bounds__(256) k_degrid(
       const int pk = chunks[it.cstart + c];
       const int v0 = pk & 1023, cnt = (pk >> 10) & 63;
       degrid_row<W>(it.vstart + v0 + lane, lane < cnt, it, rec, Gp, Gn, off, full, K, beta, mode, R, Yv, cb, inv_rho2,
-                    vblk, reduce, bsum, out);
+                    vblk, reduce, private_bins, bsum, out);
     }
   } else {
     for (int base = it.vstart; base < it.vend; base += blockDim.x) {
       const int m = base + threadIdx.x;
-      degrid_row<W>(m, m < it.vend, it, rec, Gp, Gn, off, full, K, beta, mode, R, Yv, cb, inv_rho2, vblk, reduce, bsum,
-                    out);
+      degrid_row<W>(m, m < it.vend, it, rec, Gp, Gn, off, full, K, beta, mode, R, Yv, cb, inv_rho2, vblk, reduce,
+                    private_bins, bsum, out);
     }
   }
   if (reduce) {
     __syncthreads();
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-      if (bsum[b] != 0.0) atomicAdd(&block_sum[b], bsum[b]);
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      double t = 0.0;
+      if (private_bins)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += bsum[w * kWarpBins + b];
+      else
+        t = bsum[b];
+      if (t != 0.0) atomicAdd(&block_sum[b], t);
+    }
   }
 }
 
@@ -515,11 +547,9 @@ __global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* 
   extern __shared__ float4 sm[];
   float4* bp = sm;
   float4* bm = sm + K;
-  float2* stw = reinterpret_cast<float2*>(sm + 2 * K);
   const int kx = blockIdx.x;
   const int self = (kx == 0) || (full && kx == K / 2);
   const int gxp = gidx(kx, off, full, K), gxm = gidx(-kx, off, full, K);
-  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) sm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
@@ -530,17 +560,17 @@ __global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* 
     const float P1r = a0.x + b0.x, P1i = a0.y - b0.y, Q1r = a0.z + b0.z, Q1i = a0.w - b0.w;
     const float P2r = a1.x + b1.x, P2i = a1.y - b1.y, Q2r = a1.z + b1.z, Q2i = a1.w - b1.w;
     const float4 hp = make_float4(P1r - Q1i, P1i + Q1r, P2r - Q2i, P2i + Q2r);
-    bp[bitrev((ky + K) & (K - 1), logK)] = hp;
+    bp[fsw(bitrev((ky + K) & (K - 1), logK))] = hp;
     if (!self) {
       const float4 hm = make_float4(P1r + Q1i, -P1i + Q1r, P2r + Q2i, -P2i + Q2r);
-      bm[bitrev((-ky + K) & (K - 1), logK)] = hm;
+      bm[fsw(bitrev((-ky + K) & (K - 1), logK))] = hm;
     }
   }
   __syncthreads();
-  fft_smem<true>(bp, stw, K, logK);
-  if (!self) fft_smem<true>(bm, stw, K, logK);
+  fft_smem<true>(bp, tw, logK);
+  if (!self) fft_smem<true>(bm, tw, logK);
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int idx = (p - n / 2 + K) & (K - 1);
+    const int idx = fsw((p - n / 2 + K) & (K - 1));
     T2[(size_t)p * Wd + gxp] = bp[idx];
     if (!self) T2[(size_t)p * Wd + gxm] = bm[idx];
   }
@@ -551,20 +581,18 @@ __global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const fl
                            float* __restrict__ out) {
   extern __shared__ float4 sm[];
   float4* buf = sm;
-  float2* stw = reinterpret_cast<float2*>(sm + K);
   const int p = blockIdx.x;
-  for (int i = threadIdx.x; i < (K >> 1); i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
     const int k = full ? gx : gx - off;
-    buf[bitrev((k + K) & (K - 1), logK)] = T2[(size_t)p * Wd + gx];
+    buf[fsw(bitrev((k + K) & (K - 1), logK))] = T2[(size_t)p * Wd + gx];
   }
   __syncthreads();
-  fft_smem<true>(buf, stw, K, logK);
+  fft_smem<true>(buf, tw, logK);
   const float cy = 0.5f * corr[p];
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const float4 v = buf[(q - n / 2 + K) & (K - 1)];
+    const float4 v = buf[fsw((q - n / 2 + K) & (K - 1))];
     const float c = cy * corr[q];
     const size_t o = (size_t)p * n + q;
     out[o] = v.x * c;
@@ -574,7 +602,7 @@ __global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const fl
   }
 }
 
-static size_t fft_smem_bytes(int K, int nbuf) { return (size_t)nbuf * K * sizeof(float4) + (K / 2) * sizeof(float2); }
+static size_t fft_smem_bytes(int K, int nbuf) { return (size_t)nbuf * K * sizeof(float4); }
 
 static cudaError_t set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -611,7 +639,8 @@ cudaError_t nufft_forward_grid(Handle* h, const float* X) {
 template <int W>
 static void launch_degrid(Handle* h, int mode, float2* out) {
   const GridGeom& g = h->g;
-  const size_t sm = degrid_smem_tiles<W>() + (size_t)h->nblocks * sizeof(double);
+  const int nbins = h->nblocks <= kWarpBins ? kWarpBins * 8 : h->nblocks;   // 8 warps of 256 threads
+  const size_t sm = degrid_smem_tiles<W>() + (size_t)nbins * sizeof(double);
   auto kern = h->tune[PS_TUNE_DEGRID] ? k_degrid<W, true> : k_degrid<W, false>;
   kern<<<h->nitems, 256, sm, h->stream>>>(h->items, h->gchunks, h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode,
                                           h->R, h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->nblocks,
