@@ -20,6 +20,13 @@ Readings (the paper leaves these open or prints them inconsistently):
   * Modes: POLARIZED is Algorithm 1 in full. NO_CONSTRAINT (Section 5.2) updates
     S, A, B only with P_U' (Stokes I >= 0). NNLS (Section 4.3.4, initialisation)
     updates S and B only, with P_U' and g = 0; every other variable stays zero.
+    SOC is not in the paper: the same problem as POLARIZED, with the polarization
+    constraint iota_P(S) (Eq. pol_const) given its own dual C under the identity
+    operator instead of the epigraphical split of Section 4.3.1. Step 3 is
+    unchanged, step 4 and Z, D drop out, and steps 9-12 become
+    C = C~ - rho3 P_P(C~ / rho3), C~ = C + rho3 (2 S^(k+1) - S^(k)), with the
+    closed-form cone projection P_P (prox.proj_P). tau uses the same sum
+    rho1 + rho2 ||phi||^2 + rho3 (||Id|| = 1).
   * N_p (Section 5.2) uses all of S_{n,2:4}; the threshold zeta is
     ``zeta_sigma`` times the rms of the Stokes I residual image phi^dagger(Y - phi S)
     in units of its PSF peak 2 sum w_m^2.
@@ -38,7 +45,7 @@ from . import measurement as meas
 from . import prox
 from . import wavelets as wav
 
-POLARIZED, NO_CONSTRAINT, NNLS = 0, 1, 2
+POLARIZED, NO_CONSTRAINT, NNLS, SOC = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -67,9 +74,9 @@ def step_sizes(opnorm_sq: float, mode: int, rho1: float = 1.0, rho3: float = 1.0
     if rho2 is None:
         rho2 = 1.0 / opnorm_sq
     denom = rho2 * opnorm_sq
-    if mode in (POLARIZED, NO_CONSTRAINT):
+    if mode in (POLARIZED, NO_CONSTRAINT, SOC):
         denom += rho1
-    if mode == POLARIZED:
+    if mode in (POLARIZED, SOC):
         denom += rho3
     return Params(tau=safety / denom, rho1=rho1, rho2=rho2, rho3=rho3)
 
@@ -98,10 +105,10 @@ def pd_iteration(st: dict, prob: Problem, T: np.ndarray, p: Params, mode: int = 
     grad = meas.phi_adjoint(B, prob.uv, prob.w, n)
     if mode != NNLS:
         grad = grad + wav.psi(A, L)
-    if mode == POLARIZED:
+    if mode in (POLARIZED, SOC):
         grad = grad + C
     X = S - p.tau * grad
-    S1 = prox.proj_U(X) if mode == POLARIZED else prox.proj_U_pos(X)
+    S1 = prox.proj_U(X) if mode in (POLARIZED, SOC) else prox.proj_U_pos(X)
     Sb = 2.0 * S1 - S
     out = dict(st)
     out["S"] = S1
@@ -130,6 +137,9 @@ def pd_iteration(st: dict, prob: Problem, T: np.ndarray, p: Params, mode: int = 
         C1[1:4] = Ct[1:4] - p.rho3 * R2
         D1[1] = Dt[1] - p.rho3 * d2
         out["C"], out["D"] = C1, D1
+    if mode == SOC:
+        Ct = C + p.rho3 * Sb
+        out["C"] = Ct - p.rho3 * prox.proj_P(Ct / p.rho3)
     return out
 
 
@@ -170,7 +180,7 @@ def zeta_threshold(S: np.ndarray, prob: Problem, zeta_sigma: float = 3.0) -> flo
 def metric_sq(dS, dZ, dA, dB, dC, dD, prob: Problem, p: Params, mode: int) -> float:
     """||dz||_M^2 for the primal-dual metric M = [[I/tau, -K^T], [-K, diag(1/rho)]].
 
-    K maps (S, Z) to (Psi^dagger S, phi(S), S, Z). Algorithm 1 is a proximal point
+    K maps (S, Z) to (Psi^dagger S, phi(S), S, Z) (SOC: (Psi^dagger S, phi(S), S)). Algorithm 1 is a proximal point
     step in this metric, so ||z^(k+1) - z^k||_M is non-increasing when the step-size
     condition of Section 4.3.3 holds.
     """
@@ -183,6 +193,9 @@ def metric_sq(dS, dZ, dA, dB, dC, dD, prob: Problem, p: Params, mode: int) -> fl
     if mode == POLARIZED:
         val += (np.sum(dC ** 2) + np.sum(dD ** 2)) / p.rho3
         cross += float(np.sum(dS * dC) + np.sum(dZ * dD))
+    if mode == SOC:
+        val += np.sum(dC ** 2) / p.rho3
+        cross += float(np.sum(dS * dC))
     return float(val - 2.0 * cross)
 
 

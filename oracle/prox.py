@@ -57,6 +57,18 @@ def proj_E2(R: np.ndarray, d: np.ndarray):
     return Rp, dp
 
 
+def proj_P(S: np.ndarray) -> np.ndarray:
+    """Projection onto the polarization set P = {sqrt(Q^2 + U^2 + V^2) <= I} per pixel (Eq. pol_const).
+
+    P is the second-order cone in which Stokes I plays the role of the epigraph
+    variable of h2(r) = ||r||_2 over r = (Q, U, V), i.e. E2 with d = I, so its
+    projection is the closed form of Eq. proj_e2_def applied to (r, d) = (S_2:4, S_1).
+    S: (4, ...); returns the projected (I, Q, U, V).
+    """
+    R, d = proj_E2(S[1:4], S[0])
+    return np.concatenate([d[None], R])
+
+
 def soft_threshold(A: np.ndarray, T: np.ndarray) -> np.ndarray:
     """Component-wise prox of the weighted l1 norm with thresholds T >= 0 (Eq. soft_thresh, sign typo fixed)."""
     return np.where(A < -T, A + T, np.where(A > T, A - T, 0.0))

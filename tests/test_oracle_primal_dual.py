@@ -32,7 +32,7 @@ def _metric_sequence(prob, p, mode, T, iters, st=None, iteration=pd.pd_iteration
     return np.array(out), st
 
 
-@pytest.mark.parametrize("mode", [pd.POLARIZED, pd.NO_CONSTRAINT, pd.NNLS])
+@pytest.mark.parametrize("mode", [pd.POLARIZED, pd.NO_CONSTRAINT, pd.NNLS, pd.SOC])
 def test_fixed_point_residual_non_increasing(mode):
     """Algorithm 1 is a proximal-point step in the metric M, so ||z_{k+1} - z_k||_M never grows."""
     prob, _ = _problem()
@@ -62,6 +62,43 @@ def test_planted_sign_error_breaks_monotonicity():
     st0["C"] = rng.normal(size=st0["C"].shape)
     ds, _ = _metric_sequence(prob, p, pd.POLARIZED, T, 30, st=st0, iteration=wrong)
     assert np.any(np.diff(ds) > 1e-6 * ds[:-1])
+
+
+def test_planted_cone_sign_error_breaks_monotonicity_in_soc_mode():
+    """A wrong sign on C in step 3 of the direct cone variant is caught by the same metric pin."""
+    prob, _ = _problem()
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    p = pd.step_sizes(on, pd.SOC)
+    T = 2e-3 * np.ones((4, 9, prob.n, prob.n))
+
+    def wrong(st, prob, T, p, mode):
+        st = dict(st)
+        st["C"] = -st["C"]
+        return pd.pd_iteration(st, prob, T, p, mode)
+    rng = np.random.default_rng(1)
+    st0 = pd.zero_state(prob.n, prob.Y.shape[0])
+    st0["C"] = rng.normal(size=st0["C"].shape)
+    ds, _ = _metric_sequence(prob, p, pd.SOC, T, 30, st=st0, iteration=wrong)
+    assert np.any(np.diff(ds) > 1e-6 * ds[:-1])
+
+
+def test_soc_and_epigraph_split_solve_the_same_problem():
+    """Both variants minimise sum T |Psi^dagger S| over P and the data balls: at convergence they
+    are feasible, reach the same objective and (the minimiser being unique here) the same maps."""
+    prob, _ = _problem(n=16, M=300, levels=2, nblocks=1, seed=3)
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    T = 1e-2 * np.ones((4, 9, prob.n, prob.n))
+    out = {}
+    for mode in (pd.POLARIZED, pd.SOC):
+        st = pd.run(pd.zero_state(prob.n, 300), prob, T, pd.step_sizes(on, mode), 1200, mode)
+        S = st["S"]
+        assert np.all(pd.residual_norms(S, prob) <= 1.005 * prob.eps)
+        pv = -S[0] + np.sqrt(np.sum(S[1:] ** 2, axis=0))
+        assert pv.max() <= 1e-4 * S[0].max()
+        out[mode] = (S, float(np.sum(T * np.abs(wav.psi_adjoint(S, prob.levels)))))
+    (Sa, fa), (Sb, fb) = out[pd.POLARIZED], out[pd.SOC]
+    assert abs(fa - fb) <= 1e-3 * fa
+    assert np.linalg.norm(Sa - Sb) <= 1e-2 * np.linalg.norm(Sa)
 
 
 def test_polarized_solution_is_feasible_and_fits_data():

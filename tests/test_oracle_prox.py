@@ -61,6 +61,26 @@ def test_proj_E2_brute_force_and_moreau():
         assert np.allclose(np.concatenate([pR2[:, 0], pd2]), got, atol=1e-14)
 
 
+def test_proj_P_brute_force_and_moreau():
+    """The polarization set P (Eq. pol_const) is the second-order cone {I >= ||(Q, U, V)||}."""
+    rng = np.random.default_rng(5)
+    cases = [rng.normal(size=4) * 2 for _ in range(60)]
+    cases += [np.array([-1.0, 0.0, 0.0, 0.0]), np.array([2.0, 0.0, 0.0, 0.0]),
+              np.array([-3.0, 3.0, 0.0, 0.0]), np.array([np.sqrt(3.0), 1.0, 1.0, 1.0]),
+              np.array([1.0, 0.3, -0.2, 0.1])]
+    for v in cases:
+        got = prox.proj_P(v.reshape(4, 1))[:, 0]
+        ref = _brute_projection(v, lambda u: u[0] - np.sqrt(u[1] ** 2 + u[2] ** 2 + u[3] ** 2 + 1e-300))
+        assert np.allclose(got, ref, atol=2e-5), (v, got, ref)
+        assert np.linalg.norm(got[1:]) <= got[0] + 1e-12
+        if np.linalg.norm(v[1:]) <= v[0]:
+            assert np.array_equal(got, v)                       # points of P are kept
+        r = v - got
+        assert abs(r @ got) < 1e-10                             # Moreau: orthogonal parts
+        assert np.linalg.norm(r[1:]) <= -r[0] + 1e-10           # r in the polar cone -P
+        assert np.allclose(prox.proj_P(got.reshape(4, 1))[:, 0], got, atol=1e-14)
+
+
 def test_soft_threshold_is_prox_and_clamp_identity():
     """T is the prox of t|.| (1D brute force), and A - rho T_{T/rho}(A/rho) = clamp(A, -T, T)."""
     rng = np.random.default_rng(3)
