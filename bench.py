@@ -413,6 +413,22 @@ def run_own(args) -> None:
                "d2h_bytes_per_step": int(out_p.numel() * 4),
                "note": "host->device measurements (sort, power iteration) once, then per step one iteration + Stokes read-back"}
 
+    # The direct cone-dual variant (PS_SOC: no Z, D) on the same problem and launch path.
+    soc = None
+    if rank == 0:
+        s.set_mode(B.PS_SOC)
+        s.pd_iterate(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.pd_iterate(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_soc = ev0.elapsed_time(ev1) / args.steps
+        soc = {"iters_per_s": 1000.0 / ms_soc, "ms_per_step": ms_soc,
+               "algorithmic_bytes": total_bytes - 32 * n * n,
+               "note": "PS_SOC: polarization cone as one dual (no Z, D), same problem as the epigraph split"}
+        s.set_mode(B.PS_POLARIZED)
+
     batched = served = None
     if rank == 0 and world == 1 and not args.no_serve:
         s.close()
@@ -450,6 +466,7 @@ def run_own(args) -> None:
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": e2e,
+            "soc_variant": soc,
             "cpu_baseline": cpu,
             "batched": batched,
             "served": served,

@@ -57,13 +57,18 @@ typedef enum {
 enum {
   PS_POLARIZED = 0,      /* Algorithm 1 in full: S, Z, A, B, C, D */
   PS_NO_CONSTRAINT = 1,  /* S, A, B only, with P_U' (Stokes I >= 0) */
-  PS_NNLS = 2            /* S, B only, with P_U' and g = 0: the initialisation of Alg. 2 */
+  PS_NNLS = 2,           /* S, B only, with P_U' and g = 0: the initialisation of Alg. 2 */
+  PS_SOC = 3             /* not in the paper: the problem of PS_POLARIZED with the polarization
+                            constraint (Eq. pol_const, a second-order cone per pixel) given one
+                            dual C under the identity, C = C~ - rho3 P_P(C~/rho3) with the
+                            closed-form cone projection, instead of the epigraph split of
+                            Section 4.3.1: S, A, B, C only (no Z, D; 32 bytes/pixel less) */
 };
 
 typedef struct {
   int32_t n;             /* image side: power of two, 16 <= n <= 2048 */
   int32_t levels;        /* wavelet levels, 1 <= levels, n divisible by 2^levels */
-  int32_t mode;          /* PS_POLARIZED | PS_NO_CONSTRAINT | PS_NNLS */
+  int32_t mode;          /* PS_POLARIZED | PS_NO_CONSTRAINT | PS_NNLS | PS_SOC */
   int32_t literal_ball;  /* 0: l2-ball radius eps (Moreau reading of Alg. 1 step 8);
                             1: the printed radius eps / rho2 */
   int32_t kernel_width;  /* NUFFT interpolation width W: 5, 7 or 9; 0 => 7 */
@@ -140,7 +145,7 @@ ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter);
  * dual state is kept (warm start). delta > 0. */
 ps_status ps_reweight(ps_handle* h, double delta);
 
-/* Switch the problem variant (PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS) keeping the
+/* Switch the problem variant (PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS, PS_SOC) keeping the
  * state; step sizes that were defaulted are recomputed for the new mode. */
 ps_status ps_set_mode(ps_handle* h, int32_t mode);
 

@@ -206,8 +206,9 @@ def run(st: dict, prob: Problem, T: np.ndarray, p: Params, iters: int, mode: int
 
 
 def solve(prob: Problem, iterations: int, reweights: int, gamma: float, opnorm_sq: float,
-          delta_factor: float = 0.1, delta_decay: float = 0.5) -> dict:
-    """Algorithm 2 with the NNLS start (Section 4.3.4): fixed iteration budget."""
+          delta_factor: float = 0.1, delta_decay: float = 0.5, mode: int = POLARIZED) -> dict:
+    """Algorithm 2 with the NNLS start (Section 4.3.4): fixed iteration budget; the reweighted
+    cycles run in `mode` (POLARIZED, or SOC for the direct cone dual)."""
     n, M = prob.n, prob.Y.shape[0]
     cycles = reweights + 1
     per = iterations // cycles
@@ -215,9 +216,9 @@ def solve(prob: Problem, iterations: int, reweights: int, gamma: float, opnorm_s
     T = np.zeros((4, 9, n, n))
     st = run(st, prob, T, step_sizes(opnorm_sq, NNLS), per, NNLS)
     delta = delta_factor * float(np.max(np.abs(wav.psi_adjoint(st["S"], prob.levels))))
-    p = step_sizes(opnorm_sq, POLARIZED)
+    p = step_sizes(opnorm_sq, mode)
     for _ in range(reweights):
         T = gamma * reweight(st["S"], prob.levels, delta)
-        st = run(st, prob, T, p, per, POLARIZED)
+        st = run(st, prob, T, p, per, mode)
         delta *= delta_decay
     return st

@@ -17,7 +17,7 @@ import numpy as np
 from . import _build
 
 PS_OK, PS_EINVAL, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINITE, PS_ESTATE = range(7)
-PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS = 0, 1, 2
+PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS, PS_SOC = 0, 1, 2, 3
 STATUS_NAMES = {0: "PS_OK", 1: "PS_EINVAL", 2: "PS_ENOMEM", 3: "PS_ECUDA", 4: "PS_ETIMEOUT",
                 5: "PS_ENONFINITE", 6: "PS_ESTATE"}
 

@@ -118,7 +118,7 @@ static void set_default_steps(Handle* h) {
   h->rho2 = c.rho2 > 0 ? c.rho2 : (on > 0 ? 1.0 / on : 1.0);
   double denom = h->rho2 * on;
   if (h->mode != PS_NNLS) denom += h->rho1;
-  if (h->mode == PS_POLARIZED) denom += h->rho3;
+  if (h->mode == PS_POLARIZED || h->mode == PS_SOC) denom += h->rho3;
   h->tau = c.tau > 0 ? c.tau : (denom > 0 ? 0.99 / denom : 0.99);
 }
 
@@ -254,7 +254,7 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
     return fail(nullptr, PS_EINVAL, "ps_create: n must be a power of two in [16, 2048]");
   if (L < 1 || (n % (1 << L)) != 0 || (n >> L) < 1)
     return fail(nullptr, PS_EINVAL, "ps_create: levels must satisfy 1 <= levels and n divisible by 2^levels");
-  if (cfg->mode < PS_POLARIZED || cfg->mode > PS_NNLS) return fail(nullptr, PS_EINVAL, "ps_create: bad mode");
+  if (cfg->mode < PS_POLARIZED || cfg->mode > PS_SOC) return fail(nullptr, PS_EINVAL, "ps_create: bad mode");
   const int W = cfg->kernel_width == 0 ? 7 : cfg->kernel_width;
   if (W != 5 && W != 7 && W != 9) return fail(nullptr, PS_EINVAL, "ps_create: kernel_width must be 5, 7 or 9");
   if (cfg->tau < 0 || cfg->rho1 < 0 || cfg->rho2 < 0 || cfg->rho3 < 0)
@@ -639,7 +639,7 @@ ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_
 
 ps_status ps_set_mode(ps_handle* h, int32_t mode) {
   if (!h) return PS_EINVAL;
-  if (mode < PS_POLARIZED || mode > PS_NNLS) return fail(h, PS_EINVAL, "set_mode: bad mode");
+  if (mode < PS_POLARIZED || mode > PS_SOC) return fail(h, PS_EINVAL, "set_mode: bad mode");
   h->mode = mode;
   h->cfg.mode = mode;
   set_default_steps(h);

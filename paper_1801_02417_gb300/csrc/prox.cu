@@ -4,7 +4,8 @@
 // P_U' and P_V), the extrapolations 2 S^(k+1) - S^(k), 2 Z^(k+1) - Z^(k), steps
 // 9-12 (epigraph duals C, D through P_E1 and P_E2, Eqs. proj_e1 and
 // proj_e2_def) and the Dirac part of steps 5-6 (A_dirac = clamp(A + rho1 Xb/3,
-// +-gamma W)). It also writes per-CTA FP64 partials of ||S^(k+1) - S^(k)||^2 and
+// +-gamma W)). In PS_SOC mode the epigraph steps are replaced by the direct
+// cone dual C = C~ - rho3 P_P(C~ / rho3) (Z and D are not touched). It also writes per-CTA FP64 partials of ||S^(k+1) - S^(k)||^2 and
 // ||S^(k)||^2 per map for the relative-change rule (Eq. stop_crit).
 #include <cuda_runtime.h>
 
@@ -84,13 +85,13 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
         const float4 p = ld4(PsiA + o);
         g = make_float4(g.x + p.x, g.y + p.y, g.z + p.z, g.w + p.w);
       }
-      if (mode == PS_POLARIZED) {
+      if (mode == PS_POLARIZED || mode == PS_SOC) {
         const float4 q = ld4(C + o);
         g = make_float4(g.x + q.x, g.y + q.y, g.z + q.z, g.w + q.w);
       }
       const float4 so = ld4(S + o);
       float4 sn = make_float4(so.x - tau * g.x, so.y - tau * g.y, so.z - tau * g.z, so.w - tau * g.w);   // step 3
-      if (mode != PS_POLARIZED && c == 0)                                                              // P_U'
+      if ((mode == PS_NO_CONSTRAINT || mode == PS_NNLS) && c == 0)                                    // P_U'
         sn = make_float4(fmaxf(sn.x, 0.f), fmaxf(sn.y, 0.f), fmaxf(sn.z, 0.f), fmaxf(sn.w, 0.f));
       xb[c] = make_float4(2.f * sn.x - so.x, 2.f * sn.y - so.y, 2.f * sn.z - so.z, 2.f * sn.w - so.w);
       dss[c] += (sn.x - so.x) * (sn.x - so.x) + (sn.y - so.y) * (sn.y - so.y) + (sn.z - so.z) * (sn.z - so.z) +
@@ -145,6 +146,25 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
       st4(Z + (size_t)N + i, z2n);
       st4(D + i, d1n);
       st4(D + (size_t)N + i, d2n);
+      st4(C + i, c0);
+      st4(C + (size_t)N + i, c1);
+      st4(C + 2 * (size_t)N + i, c2);
+      st4(C + 3 * (size_t)N + i, c3);
+    } else if (mode == PS_SOC) {
+      // Direct cone dual: C = C~ - rho3 P_P(C~ / rho3), P_P = P_E2 with (r, d) = ((Q, U, V), I).
+      float4 c0 = ld4(C + i), c1 = ld4(C + (size_t)N + i), c2 = ld4(C + 2 * (size_t)N + i),
+             c3 = ld4(C + 3 * (size_t)N + i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float ct0 = comp(c0, k) + rho3 * comp(xb[0], k), ct1 = comp(c1, k) + rho3 * comp(xb[1], k);
+        const float ct2 = comp(c2, k) + rho3 * comp(xb[2], k), ct3 = comp(c3, k) + rho3 * comp(xb[3], k);
+        float p1, p2, p3, p0;
+        proj_e2(ct1 * inv_r3, ct2 * inv_r3, ct3 * inv_r3, ct0 * inv_r3, p1, p2, p3, p0);
+        setc(c0, k, ct0 - rho3 * p0);
+        setc(c1, k, ct1 - rho3 * p1);
+        setc(c2, k, ct2 - rho3 * p2);
+        setc(c3, k, ct3 - rho3 * p3);
+      }
       st4(C + i, c0);
       st4(C + (size_t)N + i, c1);
       st4(C + 2 * (size_t)N + i, c2);

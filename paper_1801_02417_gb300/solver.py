@@ -112,14 +112,15 @@ class PolarizedSARA:
         return out
 
     # Algorithm 2.
-    def solve(self, sch: Schedule, W0=None) -> np.ndarray:
-        """NNLS start, then `reweights` cycles of Algorithm 1 each preceded by a reweight."""
+    def solve(self, sch: Schedule, W0=None, mode: int = B.PS_POLARIZED) -> np.ndarray:
+        """NNLS start, then `reweights` cycles of Algorithm 1 each preceded by a reweight.
+        mode: PS_POLARIZED (epigraph split) or PS_SOC (direct cone dual) for the cycles."""
         per = sch.iterations // (sch.reweights + 1)
         self.set_mode(B.PS_NNLS)
         self.pd_iterate(per)
         delta = sch.delta_factor * B.ps_max_abs_analysis(self.h)
         self.set_sara_weights(W0, sch.gamma)
-        self.set_mode(B.PS_POLARIZED)
+        self.set_mode(mode)
         for _ in range(sch.reweights):
             self.reweight(delta)
             self.pd_iterate(per)

@@ -88,7 +88,7 @@ def _random_state(n, M, seed, scale=1.0):
     return {k: (v.astype(np.complex64) if k == "B" else v.astype(np.float32)) for k, v in st.items()}
 
 
-@pytest.mark.parametrize("mode", [B.PS_POLARIZED, B.PS_NO_CONSTRAINT, B.PS_NNLS])
+@pytest.mark.parametrize("mode", [B.PS_POLARIZED, B.PS_NO_CONSTRAINT, B.PS_NNLS, B.PS_SOC])
 @pytest.mark.parametrize("n,M,levels,nblocks,coverage", [(32, 1500, 3, 4, "tracks"), (16, 333, 2, 1, "random")])
 def test_iterations_from_random_state_match_oracle(mode, n, M, levels, nblocks, coverage):
     pb = make_problem(n, M, levels, nblocks, seed=11, coverage=coverage)
@@ -102,7 +102,7 @@ def test_iterations_from_random_state_match_oracle(mode, n, M, levels, nblocks, 
     T = gamma * W.astype(np.float64)
     ref = {k: v.astype(np.complex128 if k == "B" else np.float64) for k, v in st32.items()}
     if mode != B.PS_POLARIZED:
-        for k in ("Z", "C", "D"):
+        for k in ("Z", "D") if mode == B.PS_SOC else ("Z", "C", "D"):
             st32[k][:] = 0
             ref[k][:] = 0
     if mode == B.PS_NNLS:
@@ -119,7 +119,8 @@ def test_iterations_from_random_state_match_oracle(mode, n, M, levels, nblocks, 
                 ref = opd.pd_iteration(ref, prob, T, p, mode)
             done += k_iter
             got = s.get_state()
-            for k in ("S", "A", "B") + (("Z", "C", "D") if mode == B.PS_POLARIZED else ()):
+            extra = {B.PS_POLARIZED: ("Z", "C", "D"), B.PS_SOC: ("C",)}.get(mode, ())
+            for k in ("S", "A", "B") + extra:
                 err = rel_err(got[k], ref[k])
                 assert err <= 2e-5 * done, (done, k, err)
 
@@ -206,3 +207,28 @@ def test_full_solve_img64_matches_oracle():
     for i in range(4):
         assert rel_err(S[i], ref["S"][i]) <= 1e-3, (i, rel_err(S[i], ref["S"][i]))
     assert st["violations"] == opd.violation_count(ref["S"], st["zeta"])
+
+
+def test_full_solve_img64_direct_cone_variant():
+    """The direct cone dual (PS_SOC) on the same schedule: within 1e-3 of the FP64 oracle's SOC
+    solve per map with the same violation count, and close to the epigraph-split solve (both
+    approach the same minimiser; after 300 iterations they still differ by the iterates' paths)."""
+    wl = inputs.WORKLOADS["img64_m2k"]
+    pb = make_problem(wl.n, wl.M, wl.levels, wl.nblocks, seed=wl.seed, stations=wl.stations,
+                      weight_spread=0.0)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, wl.n)
+    gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, wl.n),
+                                                          wl.levels))))
+    ref = opd.solve(prob, wl.iterations, wl.reweights, gamma, on, mode=opd.SOC)
+    p = opd.step_sizes(on, opd.SOC)
+    out = {}
+    for mode in (B.PS_SOC, B.PS_POLARIZED):
+        with _solver(pb, wl.n, wl.levels, steps=dict(rho2=p.rho2)) as s:
+            out[mode] = (s.solve(Schedule(wl.iterations, wl.reweights, gamma), mode=mode), s.stats())
+    S, st = out[B.PS_SOC]
+    for i in range(4):
+        assert rel_err(S[i], ref["S"][i]) <= 1e-3, (i, rel_err(S[i], ref["S"][i]))
+    assert st["violations"] == opd.violation_count(ref["S"], st["zeta"])
+    Sp = out[B.PS_POLARIZED][0]
+    assert rel_err(S[0], Sp[0]) <= 5e-2
