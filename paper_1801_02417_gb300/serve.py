@@ -108,19 +108,46 @@ class _Active:
         return False
 
 
+def tuning_key(n: int, M: int) -> tuple:
+    """Problems of one image size and the same power-of-two bracket of visibility count share launch choices."""
+    return (int(n), int(max(M, 1)).bit_length())
+
+
+def apply_tuning(s: PolarizedSARA, n: int, M: int, cache: dict, lock: threading.Lock | None = None) -> None:
+    """Set the handle's launch choices from the cache, autotuning (ps_autotune) the first of its class."""
+    key = tuning_key(n, M)
+    if lock is not None:
+        lock.acquire()
+    try:
+        choices = cache.get(key)
+        if choices is None:
+            B.ps_autotune(s.h, reps=2)
+            cache[key] = B.ps_get_tuning(s.h)
+        else:
+            B.ps_set_tuning(s.h, choices)
+    finally:
+        if lock is not None:
+            lock.release()
+
+
 class Server:
     """Admission by device footprint, resident state, and overlapping per-problem streams."""
 
-    def __init__(self, hbm_budget: int, max_active: int = 64, policy: Policy | None = None, prep_workers: int = 2):
+    def __init__(self, hbm_budget: int, max_active: int = 64, policy: Policy | None = None, prep_workers: int = 2,
+                 autotune: bool = True):
         self.budget = int(hbm_budget)
         self.max_active = int(max_active)
         self.policy = policy or Policy()
         self.prep_workers = prep_workers
+        self.autotune = autotune
+        self._tuning: dict = {}
+        self._tuning_lock = threading.Lock()
 
-    @staticmethod
-    def _prepare(prob: Problem) -> PolarizedSARA:
+    def _prepare(self, prob: Problem) -> PolarizedSARA:
         s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS)
         s.set_measurements(prob.uv, prob.vis, prob.weights, prob.offsets, prob.eps)
+        if self.autotune:
+            apply_tuning(s, prob.n, prob.uv.shape[0], self._tuning, self._tuning_lock)
         return s
 
     def run(self, requests: list[tuple[float, Problem]]) -> list[Result]:

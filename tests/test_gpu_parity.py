@@ -232,3 +232,31 @@ def test_full_solve_img64_direct_cone_variant():
     assert st["violations"] == opd.violation_count(ref["S"], st["zeta"])
     Sp = out[B.PS_POLARIZED][0]
     assert rel_err(S[0], Sp[0]) <= 5e-2
+
+
+def test_unconstrained_solve_and_violation_counts():
+    """Section 5.2 comparison on the 64x64 workload: the solve without the polarization
+    constraint (positivity of I only, P_U') matches the oracle's per map within 1e-3 with the
+    same N_p at the same zeta, and the constrained solve has no more violations than it."""
+    wl = inputs.WORKLOADS["img64_m2k"]
+    pb = make_problem(wl.n, wl.M, wl.levels, wl.nblocks, seed=wl.seed, stations=wl.stations,
+                      weight_spread=0.0)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, wl.n)
+    gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, wl.n),
+                                                          wl.levels))))
+    ref = opd.solve(prob, wl.iterations, wl.reweights, gamma, on, mode=opd.NO_CONSTRAINT)
+    p = opd.step_sizes(on, opd.NO_CONSTRAINT)
+    counts = {}
+    for mode in (B.PS_NO_CONSTRAINT, B.PS_POLARIZED):
+        with _solver(pb, wl.n, wl.levels, steps=dict(rho2=p.rho2)) as s:
+            S = s.solve(Schedule(wl.iterations, wl.reweights, gamma), mode=mode)
+            st = s.stats()
+        counts[mode] = st
+        if mode == B.PS_NO_CONSTRAINT:
+            for i in range(4):
+                assert rel_err(S[i], ref["S"][i]) <= 1e-3, (i, rel_err(S[i], ref["S"][i]))
+            assert S[0].min() >= 0.0                                   # P_U': Stokes I >= 0
+            assert st["violations"] == opd.violation_count(ref["S"], st["zeta"])
+            assert st["violations_raw"] >= st["violations"]
+    assert counts[B.PS_POLARIZED]["violations"] <= counts[B.PS_NO_CONSTRAINT]["violations"]
