@@ -102,19 +102,58 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline model
 def stage_bytes(n: int, L: int, M: int, Wd: int) -> dict:
-    """Algorithmic DRAM bytes of each stage of one iteration (each array read/written once)."""
+    """Algorithmic DRAM bytes of each stage of one iteration (each array read/written once).
+
+    Per map and basis the level-l details are 3 N / 4^l coefficients and the level-l
+    approximation N / 4^l; the 8 bases x 4 maps give 24 N detail coefficients at level 1
+    and 8 N below it. The analysis epilogue reads A and gamma W and writes A (12 B per
+    coefficient); the synthesis reads A (4 B)."""
     N = n * n
     approx = sum(32 * 4 * (N >> (2 * l)) for l in range(1, L))       # 32 (map, basis) approximations
+    a1 = 32 * 4 * (N >> 2) if L > 1 else 0                            # level-1 approximations
     return {
         "primal": 192 * N,                          # S,C (16+16), Z,D (8+8), PsiA, Adj, A0, T0 read; S,Xb,Z,C,D,A0 written
-        "analysis": 16 * N + 12 * 32 * N + 2 * approx,   # Xb read; A r/w + T read; approximations w/r
-        "synthesis": 4 * 32 * N + 16 * N + 16 * N + 2 * approx,   # A read, A0 read, PsiA written
+        "analysis": 16 * N + 12 * 24 * N + a1,      # Xb read; level-1 details A r/w + T read; approximations written
+        "analysis_coarse": 12 * 8 * N + 2 * approx - a1,   # coarser coefficients; approximations read and written
+        "synthesis_coarse": 4 * 8 * N + 2 * approx - a1,   # coarser coefficients; approximations written and read
+        "synthesis": 4 * 24 * N + a1 + 16 * N + 16 * N,    # level-1 details, approximations, A0 read; PsiA written
         "fwd_fft": 16 * N + 2 * 16 * n * Wd + 16 * Wd * Wd,
         "degrid": M * (16 + 32 + 32 + 32) + 16 * Wd * Wd,   # rec, R r/w, Y; spectrum window once
         "ball": 0,
         "grid": M * (16 + 32) + 2 * 32 * Wd * Wd,      # rec, R; accumulator clear + write
         "adj_fft": 32 * Wd * Wd + 2 * 16 * n * Wd + 16 * N,
     }
+
+
+# Stages that are a single kernel launch per iteration, and that kernel's name in ncu.
+SINGLE_KERNEL_STAGES = {"primal": "k_primal", "analysis": "k_ana_l1", "synthesis": "k_syn2_fine",
+                        "degrid": "k_degrid", "grid": "k_grid"}
+
+
+def kernel_sources_digest() -> str:
+    """SHA-256 of the CUDA sources: DRAM counters taken from another build are not reported."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1801_02417_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def dram_traffic(kernel: str, workload: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one launch of `kernel`, from the committed
+    ncu summary of this workload, or None when absent or taken from other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None, None
+    if rec.get("sources_sha256") != kernel_sources_digest():
+        return None, os.path.relpath(path, ROOT) + " (stale: kernels changed)"
+    k = rec.get("kernels", {}).get(kernel)
+    return (None if k is None else k["bytes_per_launch"]), os.path.relpath(path, ROOT)
 
 
 def window_side(uv: np.ndarray, n: int, W: int = 7) -> int:
@@ -411,7 +450,8 @@ def run_own(args) -> None:
     stages = B.ps_profile_stages(s.h, prof_iters)
     Wd = window_side(uv, n)
     sbytes = stage_bytes(n, L, M, Wd)
-    dom = max(stages, key=stages.get)
+    # Dominant kernel: the slowest stage that is one kernel launch per iteration.
+    dom = max(SINGLE_KERNEL_STAGES, key=lambda k: stages[k])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -420,13 +460,7 @@ def run_own(args) -> None:
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = sbytes[dom] / (stages[dom] * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get(dom)
-        except Exception:
-            traffic = None
+    traffic, traffic_src = dram_traffic(SINGLE_KERNEL_STAGES[dom], wl.name)
     total_bytes = sum(sbytes.values())
 
     # End to end through the C ABI with host buffers (pinned): upload of the
@@ -496,9 +530,13 @@ def run_own(args) -> None:
                        "parallelism": "replicas" if world > 1 else "single", "tuning": tuning,
                        "l2": "no flush: per-iteration working set ~%.0f MB > 126 MB L2" % (total_bytes / 1e6),
                        "vis_iters_per_s": value * M},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_src, "algorithmic_bytes": sbytes[dom], "stage_ms": stages[dom]},
+            "roofline": {"bound": "hbm", "kernel": SINGLE_KERNEL_STAGES[dom], "stage": dom, "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": traffic_src, "peak_source": peak_src + " hbm_gbs (copy)",
+                         "algorithmic_bytes": sbytes[dom], "launch_ms": stages[dom]},
+            "stage_roofline": {k: {"ms": stages[k], "algorithmic_bytes": sbytes[k],
+                                   "frac": sbytes[k] / (stages[k] * 1e-3) / 1e9 / peak if stages[k] > 0 else None}
+                               for k in stages},
             "iteration_roofline": {"algorithmic_bytes": total_bytes,
                                    "achieved_gbs": total_bytes / (ms_per_step * 1e-3) / 1e9,
                                    "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak},

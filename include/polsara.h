@@ -184,15 +184,17 @@ ps_status ps_wavelet_filters(double* out);
 
 /* Stages of one iteration, in launch order (index into ps_profile_stages' output). */
 enum {
-  PS_STAGE_PRIMAL = 0,     /* k_primal: steps 3-4, 9-12, Dirac part of 5-6 */
-  PS_STAGE_ANALYSIS = 1,   /* k_analysis x levels: steps 5-6 */
-  PS_STAGE_SYNTHESIS = 2,  /* k_synthesis x levels: Psi A for the next step 3 */
-  PS_STAGE_FWD_FFT = 3,    /* k_fwd_rows + k_fwd_cols: F Z of step 7 */
-  PS_STAGE_DEGRID = 4,     /* k_degrid: G, mixing, B~ and block-norm partials (step 7) */
-  PS_STAGE_BALL = 5,       /* k_block_scale: step 8 */
-  PS_STAGE_GRID = 6,       /* accumulator clear + k_grid: G^T of phi^dagger */
-  PS_STAGE_ADJ_FFT = 7,    /* k_adj_cols + k_adj_rows: Z^T F^H of phi^dagger */
-  PS_NSTAGES = 8
+  PS_STAGE_PRIMAL = 0,            /* k_primal: steps 3-4, 9-12, Dirac part of 5-6 */
+  PS_STAGE_ANALYSIS = 1,          /* level-1 analysis (k_ana_l1): steps 5-6 on the finest details */
+  PS_STAGE_ANALYSIS_COARSE = 2,   /* analysis levels 2..L: steps 5-6 on the coarser coefficients */
+  PS_STAGE_SYNTHESIS_COARSE = 3,  /* synthesis levels L..2 (to the level-1 approximations) */
+  PS_STAGE_SYNTHESIS = 4,         /* finest synthesis level (k_syn2_fine): Psi A for the next step 3 */
+  PS_STAGE_FWD_FFT = 5,           /* k_fwd_rows + k_fwd_cols: F Z of step 7 */
+  PS_STAGE_DEGRID = 6,            /* k_degrid: G, mixing, B~ and block-norm partials (step 7) */
+  PS_STAGE_BALL = 7,              /* k_block_scale: step 8 */
+  PS_STAGE_GRID = 8,              /* accumulator clear + k_grid: G^T of phi^dagger */
+  PS_STAGE_ADJ_FFT = 9,           /* k_adj_cols + k_adj_rows: Z^T F^H of phi^dagger */
+  PS_NSTAGES = 10
 };
 
 /* Run n_iter iterations launched one kernel at a time (no graph) with CUDA events

@@ -324,7 +324,8 @@ def ps_batch_destroy(b) -> None:
     lib().ps_batch_destroy(b)
 
 
-STAGES = ("primal", "analysis", "synthesis", "fwd_fft", "degrid", "ball", "grid", "adj_fft")
+STAGES = ("primal", "analysis", "analysis_coarse", "synthesis_coarse", "synthesis", "fwd_fft", "degrid", "ball",
+          "grid", "adj_fft")
 
 
 def ps_profile_stages(h, n_iter: int) -> dict:

@@ -193,11 +193,14 @@ static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
   const bool sara = (h->mode != PS_NNLS);
   if (ev || !sara || h->M == 0 || !h->aux) {
     if ((e = mark(PS_STAGE_ANALYSIS)) != cudaSuccess) return e;
-    if (sara && (e = ps::sara_analysis(h, h->Xb, h->A, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f)) !=
-                    cudaSuccess)
+    if (sara && (e = ps::sara_analysis(h, h->Xb, h->A, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f,
+                                       ev ? ev[PS_STAGE_ANALYSIS_COARSE] : nullptr)) != cudaSuccess)
       return e;
-    if ((e = mark(PS_STAGE_SYNTHESIS)) != cudaSuccess) return e;
-    if (sara && (e = ps::sara_synthesis(h, h->A, h->PsiA)) != cudaSuccess) return e;
+    if (!sara && (e = mark(PS_STAGE_ANALYSIS_COARSE)) != cudaSuccess) return e;
+    if ((e = mark(PS_STAGE_SYNTHESIS_COARSE)) != cudaSuccess) return e;
+    if (sara && (e = ps::sara_synthesis(h, h->A, h->PsiA, ev ? ev[PS_STAGE_SYNTHESIS] : nullptr)) != cudaSuccess)
+      return e;
+    if (!sara && (e = mark(PS_STAGE_SYNTHESIS)) != cudaSuccess) return e;
     return nufft_chain(h, ev);
   }
   if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;

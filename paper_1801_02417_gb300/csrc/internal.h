@@ -129,9 +129,11 @@ cudaError_t nufft_adjoint_image(Handle* h, float* out);                    // Ac
 cudaError_t block_scales(Handle* h);                                        // chunk partials -> c_b
 
 // SARA pieces (sara.cu).
+// `fine_done` (may be null) is recorded on h->stream after the level-1 analysis launch;
+// `fine_start` (may be null) before the finest synthesis level (stage profiling).
 cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, int mode,
-                          float scale, float gamma, float delta);
-cudaError_t sara_synthesis(Handle* h, const float* coef, float* out);
+                          float scale, float gamma, float delta, cudaEvent_t fine_done = nullptr);
+cudaError_t sara_synthesis(Handle* h, const float* coef, float* out, cudaEvent_t fine_start = nullptr);
 
 // Elementwise / reductions (prox.cu).
 cudaError_t primal_sweep(Handle* h);

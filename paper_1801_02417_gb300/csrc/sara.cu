@@ -1012,7 +1012,7 @@ cudaError_t configure_kernels() {
 }
 
 cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, int mode, float scale, float gamma,
-                          float delta) {
+                          float delta, cudaEvent_t fine_done) {
   const int n = h->n, L = h->L;
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
   float* buf[2] = {h->approx, h->approx + quarter};
@@ -1043,6 +1043,10 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
       k_analysis<<<grid, 256, analysis_smem(TO), h->stream>>>(in, in_map, in_basis, m, TO, n, l == L, coef, thr,
                                                               buf[(l - 1) & 1], mode, scale, gamma, delta);
     }
+    if (l == 1 && fine_done) {
+      const cudaError_t e = cudaEventRecord(fine_done, h->stream);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaGetLastError();
 }
@@ -1051,7 +1055,7 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
 // (2 x 32 x (n/2)^2 floats); `err` (may be null) receives the bounded-wait flag;
 // `variant` is the PS_TUNE_SYNTHESIS choice of the finest level.
 static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx,
-                                    int* err, int variant) {
+                                    int* err, int variant, cudaEvent_t fine_start = nullptr) {
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
   float* buf[2] = {approx, approx + quarter};
   for (int l = L; l >= 1; --l) {
@@ -1060,6 +1064,10 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
     const int tiles = (m / TI) * (m / TI);
     const float* ain = (l == L) ? nullptr : buf[l & 1];
     float* aout = (l == 1) ? nullptr : buf[(l - 1) & 1];
+    if (l == 1 && fine_start) {
+      const cudaError_t e = cudaEventRecord(fine_start, stream);
+      if (e != cudaSuccess) return e;
+    }
     if (m >= kT2 && l == 1) {
       const dim3 grid((m / kT2) * (m / kT2), 1, 4);
       if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err);
@@ -1079,8 +1087,9 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
   return cudaGetLastError();
 }
 
-cudaError_t sara_synthesis(Handle* h, const float* coef, float* out) {
-  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->dev_flags, h->tune[PS_TUNE_SYNTHESIS]);
+cudaError_t sara_synthesis(Handle* h, const float* coef, float* out, cudaEvent_t fine_start) {
+  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->dev_flags, h->tune[PS_TUNE_SYNTHESIS],
+                          fine_start);
 }
 
 // ---------------------------------------------------------------------------
