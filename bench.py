@@ -294,14 +294,25 @@ def batched_measure(problems, iters: int) -> dict:
             "solve_iters_per_s_batched": k * iters / bat, "solve_iters_per_s_sequential": k * iters / seq}
 
 
-def np_comparison(wl_name: str = "img64_m2k", iterations: int = 8000, reweights: int = 3) -> dict:
-    """Section 5.2 protocol on synthetic data: the same schedule (NNLS start, reweighted cycles)
-    with and without the polarization constraint; N_p = pixels with -I + ||(Q,U,V)|| > zeta.
-    The budget is larger than the workload's own so that the data fit (reported beside N_p)
-    approaches the l2 balls; zeta grows with the misfit otherwise."""
+def default_gamma(s, dirty: np.ndarray, factor: float = 1e-3) -> float:
+    """gamma = factor * max |Psi^dagger phi^dagger Y| / ||phi||^2: the dirty image's analysis
+    coefficients brought back to image units (phi^dagger phi has peak ||phi||^2). gamma leaves
+    the minimiser unchanged and sets how fast the duals balance; in back-projected units it
+    would exceed the data dual's scale by ~||phi||^2 and stall the data fit."""
+    from paper_1801_02417_gb300 import binding as B
+    on = B.ps_get_params(s.h)["opnorm_sq"]
+    return factor * float(np.max(np.abs(s.psi_adjoint(dirty)))) / on
+
+
+def np_comparison(wl_name: str = "img256_m50k", iterations: int = 0, reweights: int = -1) -> dict:
+    """Section 5.2 protocol on synthetic data: the same schedule (NNLS start, reweighted cycles;
+    the workload's own budget unless given) with and without the polarization constraint;
+    N_p = pixels with -I + ||(Q,U,V)|| > zeta, reported beside the data fit reached."""
     from paper_1801_02417_gb300 import binding as B
     from paper_1801_02417_gb300.solver import PolarizedSARA, Schedule
     wl = inputs.WORKLOADS[wl_name]
+    iterations = iterations or wl.iterations
+    reweights = wl.reweights if reweights < 0 else reweights
     uv, w, truth, off = make_inputs(wl)
     out = {"workload": wl.name, "iterations": iterations, "reweights": reweights}
     with PolarizedSARA(wl.n, wl.levels) as s:
@@ -314,7 +325,7 @@ def np_comparison(wl_name: str = "img64_m2k", iterations: int = 8000, reweights:
         s.set_measurements(uv, Y, w, off, eps)
         dirty = np.empty((4, wl.n, wl.n), np.float32)
         B.ps_apply_phi_adjoint(s.h, Y, dirty)
-        gamma = 1e-3 * float(np.max(np.abs(s.psi_adjoint(dirty))))
+        gamma = default_gamma(s, dirty)
         for name, mode in (("polarized", B.PS_POLARIZED), ("soc", B.PS_SOC), ("no_constraint", B.PS_NO_CONSTRAINT)):
             s.set_measurements(uv, Y, w, off, eps)      # fresh state
             t = time.perf_counter()
@@ -410,7 +421,7 @@ def run_own(args) -> None:
     s.set_measurements(uv, Y, w, off, eps)
     dirty = np.empty((4, n, n), np.float32)
     B.ps_apply_phi_adjoint(s.h, Y, dirty)
-    gamma = 1e-3 * float(np.max(np.abs(s.psi_adjoint(dirty))))
+    gamma = default_gamma(s, dirty)
     s.set_sara_weights(None, gamma)
     s.set_mode(B.PS_POLARIZED)
     # Launch choices measured on this problem before the warm-up.

@@ -224,7 +224,8 @@ def synthesize_problem(n: int, levels: int, M: int, seed: int, nblocks: int = 1,
     """A seeded request whose clean visibilities come from the library's own phi.
 
     uv tracks and the source come from `inputs`; the noise matches `snr_db`; the
-    l2 radii are the chi^2 bounds; gamma = gamma_factor * max |Psi^dagger phi^dagger Y|.
+    l2 radii are the chi^2 bounds; gamma = gamma_factor * max |Psi^dagger phi^dagger Y| / ||phi||^2
+    (image units: phi^dagger phi peaks at ||phi||^2; gamma does not change the minimiser).
     """
     from . import inputs
     stations = 8
@@ -247,7 +248,7 @@ def synthesize_problem(n: int, levels: int, M: int, seed: int, nblocks: int = 1,
         dirty = np.empty((4, n, n), np.float32)
         B.ps_apply_phi_adjoint(s.h, Y, dirty)
         s.set_state({"S": dirty})
-        gamma = gamma_factor * B.ps_max_abs_analysis(s.h)
+        gamma = gamma_factor * B.ps_max_abs_analysis(s.h) / B.ps_get_params(s.h)["opnorm_sq"]
     eps = np.array([chi2_epsilon(int(off[b + 1] - off[b]), sigma) for b in range(nblocks)])
     return Problem(n, levels, uv, Y, w, off, eps, gamma)
 

@@ -198,7 +198,7 @@ def test_full_solve_img64_matches_oracle():
     prob = pb["prob"]
     on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, wl.n)
     gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, wl.n),
-                                                          wl.levels))))
+                                                          wl.levels)))) / on
     ref = opd.solve(prob, wl.iterations, wl.reweights, gamma, on)
     p = opd.step_sizes(on, opd.POLARIZED)
     with _solver(pb, wl.n, wl.levels, steps=dict(rho2=p.rho2)) as s:
@@ -219,7 +219,7 @@ def test_full_solve_img64_direct_cone_variant():
     prob = pb["prob"]
     on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, wl.n)
     gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, wl.n),
-                                                          wl.levels))))
+                                                          wl.levels)))) / on
     ref = opd.solve(prob, wl.iterations, wl.reweights, gamma, on, mode=opd.SOC)
     p = opd.step_sizes(on, opd.SOC)
     out = {}
@@ -244,7 +244,7 @@ def test_unconstrained_solve_and_violation_counts():
     prob = pb["prob"]
     on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, wl.n)
     gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, wl.n),
-                                                          wl.levels))))
+                                                          wl.levels)))) / on
     ref = opd.solve(prob, wl.iterations, wl.reweights, gamma, on, mode=opd.NO_CONSTRAINT)
     p = opd.step_sizes(on, opd.NO_CONSTRAINT)
     counts = {}
@@ -260,3 +260,5 @@ def test_unconstrained_solve_and_violation_counts():
             assert st["violations"] == opd.violation_count(ref["S"], st["zeta"])
             assert st["violations_raw"] >= st["violations"]
     assert counts[B.PS_POLARIZED]["violations"] <= counts[B.PS_NO_CONSTRAINT]["violations"]
+    # Pixels outside P at all (zeta = 0): the constraint removes most of them (oracle: 188 vs 2266).
+    assert 2 * counts[B.PS_POLARIZED]["violations_raw"] < counts[B.PS_NO_CONSTRAINT]["violations_raw"]
