@@ -263,7 +263,9 @@ enum {
                              1 single-buffered, refilled during the x-pass (4 CTAs/SM) */
   PS_TUNE_DEGRID = 1,     /* 0 one row per thread over a work item,
                              1 one same-cell chunk per warp (broadcast stencil reads) */
-  PS_TUNE_COUNT = 4       /* slots 2, 3 reserved (0) */
+  PS_TUNE_GRID = 2,       /* 0 one warp per same-cell chunk (2 kernel cells per lane),
+                             1 half-warps on alternate rows of a chunk (4 cells per lane) */
+  PS_TUNE_COUNT = 4       /* slot 3 reserved (0) */
 };
 
 /* Autotuner: after ps_set_measurements, time every candidate of every PS_TUNE_*

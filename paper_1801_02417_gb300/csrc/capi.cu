@@ -938,7 +938,7 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms) {
 
 // ---------------------------------------------------------------------------
 // Autotuner: candidates per PS_TUNE_* slot, each timed on the handle's own data.
-static const int kTuneCandidates[PS_TUNE_COUNT] = {2, 2, 1, 1};
+static const int kTuneCandidates[PS_TUNE_COUNT] = {2, 2, 2, 1};
 
 // Mean milliseconds of `reps` launches of f after one untimed launch.
 extern "C++" {
@@ -994,6 +994,9 @@ ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms) 
   if (h->M > 0) {
     CK(h, ps::nufft_forward_grid(h, h->S));
     st = pick(PS_TUNE_DEGRID, [&] { return ps::nufft_degrid(h, ps::DEG_APPLY, h->vtmp); });
+    if (st != PS_OK) return st;
+    // Gridding: the current dual into the accumulator (an intermediate; phi^dagger B is kept).
+    st = pick(PS_TUNE_GRID, [&] { return ps::nufft_grid(h, h->R, 1); });
     if (st != PS_OK) return st;
   }
   drop_graph(h);

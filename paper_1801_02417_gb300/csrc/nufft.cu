@@ -414,9 +414,17 @@ __global__ void k_block_scale(const double* __restrict__ block_sum, const double
 //  3. The tile (with halo) is added to the global accumulator.
 // Channels are gridded at +u only; k_adj_cols forms the -u half by Hermitian
 // symmetrisation.
-constexpr int kGridV = kGridItem + 1;   // odd stride of the staged per-row fields (conflict-free)
+// Stride of the staged per-row weight planes: tap j of row v sits in bank (2 j + v) mod 32, so
+// the lanes of a warp (one row, or two rows v, v+1 in the half-warp form) reading their
+// cells' taps never share a bank.
+constexpr int kGridV = kGridItem + 2;
 
-template <int W>
+// HALF = false: one warp per same-cell chunk, lane l owns kernel cells l, l + 32.
+// HALF = true: the two half-warps take alternate rows of the chunk, lane l owns cells
+// (l & 15) + 16 q; each 16-byte broadcast read of a row's channels then serves 16 lanes
+// (two rows per instruction), and the halves' sums are combined by shuffles before the
+// shared-memory flush.
+template <int W, bool HALF>
 __global__ void __launch_bounds__(256) k_grid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
     const float4* __restrict__ rec, const float2* __restrict__ vin, const float* __restrict__ cb, int use_scale,
@@ -425,7 +433,8 @@ __global__ void __launch_bounds__(256) k_grid(
   constexpr int SS = TS + W - 1;
   constexpr int NC = SS * SS;                    // cells of the tile with halo
   constexpr int hw = W / 2;
-  constexpr int CPL = (W * W + 31) / 32;         // kernel cells per lane
+  constexpr int LPR = HALF ? 16 : 32;            // lanes per row in flight
+  constexpr int CPL = (W * W + LPR - 1) / LPR;   // kernel cells per lane
   extern __shared__ float4 smg[];
   float4* x4 = smg;                              // kGridItem x 2: mixed, scaled channels of each row
   float* acc = reinterpret_cast<float*>(smg + 2 * kGridItem);   // 8 planes of NC cells
@@ -456,18 +465,18 @@ __global__ void __launch_bounds__(256) k_grid(
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int sub = HALF ? (lane >> 4) : 0, sl = HALF ? (lane & 15) : lane;
   const int nc = it.cend - it.cstart;
-  const float* wxl[CPL];
-  const float* wyl[CPL];
-  int coff[CPL];
+  int wxo[CPL], wyo[CPL], coff[CPL];
 #pragma unroll
   for (int q = 0; q < CPL; ++q) {
-    const int cell = lane + 32 * q;
+    const int cell = sl + LPR * q;
     const int jy = cell < W * W ? cell / W : 0, jx = cell < W * W ? cell - (cell / W) * W : 0;
-    wxl[q] = wxs + jx * kGridV;
-    wyl[q] = wys + jy * kGridV;
+    wxo[q] = jx * kGridV;
+    wyo[q] = jy * kGridV;
     coff[q] = jy * SS + jx;
   }
+  const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x4);
   for (int c = warp; c < nc; c += nwarps) {
     const int pk = chunks[it.cstart + c];
     const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
@@ -477,41 +486,65 @@ __global__ void __launch_bounds__(256) k_grid(
     for (int q = 0; q < CPL; ++q)
 #pragma unroll
       for (int p = 0; p < 4; ++p) a2[q][p] = 0ull;
-    const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x4);
-    int v = v0;
-    for (; v + 1 < v0 + cnt; v += 2) {
-      const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1], y0 = xv[2 * v + 2], y1 = xv[2 * v + 3];
+    if (HALF) {
+      for (int v = v0 + sub; v < v0 + cnt; v += 2) {
+        const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
 #pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const u64 k0 = fdup(wxl[q][v] * wyl[q][v]), k1 = fdup(wxl[q][v + 1] * wyl[q][v + 1]);
-        a2[q][0] = ffma2(k1, y0.x, ffma2(k0, x0.x, a2[q][0]));
-        a2[q][1] = ffma2(k1, y0.y, ffma2(k0, x0.y, a2[q][1]));
-        a2[q][2] = ffma2(k1, y1.x, ffma2(k0, x1.x, a2[q][2]));
-        a2[q][3] = ffma2(k1, y1.y, ffma2(k0, x1.y, a2[q][3]));
+        for (int q = 0; q < CPL; ++q) {
+          const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
+          a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
+          a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
+          a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
+          a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          float lo, hi;
+          f2unpack(a2[q][p], lo, hi);
+          lo += __shfl_xor_sync(0xffffffffu, lo, 16);
+          hi += __shfl_xor_sync(0xffffffffu, hi, 16);
+          a2[q][p] = f2pack(lo, hi);
+        }
+    } else {
+      int v = v0;
+      for (; v + 1 < v0 + cnt; v += 2) {
+        const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1], y0 = xv[2 * v + 2], y1 = xv[2 * v + 3];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
+          const u64 k1 = fdup(wxs[wxo[q] + v + 1] * wys[wyo[q] + v + 1]);
+          a2[q][0] = ffma2(k1, y0.x, ffma2(k0, x0.x, a2[q][0]));
+          a2[q][1] = ffma2(k1, y0.y, ffma2(k0, x0.y, a2[q][1]));
+          a2[q][2] = ffma2(k1, y1.x, ffma2(k0, x1.x, a2[q][2]));
+          a2[q][3] = ffma2(k1, y1.y, ffma2(k0, x1.y, a2[q][3]));
+        }
+      }
+      if (v < v0 + cnt) {
+        const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
+          a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
+          a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
+          a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
+          a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
+        }
       }
     }
-    if (v < v0 + cnt) {
-      const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const u64 k0 = fdup(wxl[q][v] * wyl[q][v]);
-        a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
-        a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
-        a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
-        a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
-      }
-    }
-    float a[CPL][8];
-#pragma unroll
-    for (int q = 0; q < CPL; ++q)
-#pragma unroll
-      for (int p = 0; p < 4; ++p) f2unpack(a2[q][p], a[q][2 * p], a[q][2 * p + 1]);
     const int cbase = ly * SS + lx;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
-      if (lane + 32 * q < W * W) {
+      if (sub == 0 && sl + LPR * q < W * W) {
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) atomicAdd(acc + ch * NC + cbase + coff[q], a[q][ch]);
+        for (int p = 0; p < 4; ++p) {
+          float lo, hi;
+          f2unpack(a2[q][p], lo, hi);
+          atomicAdd(acc + (2 * p) * NC + cbase + coff[q], lo);
+          atomicAdd(acc + (2 * p + 1) * NC + cbase + coff[q], hi);
+        }
       }
     }
   }
@@ -615,9 +648,12 @@ cudaError_t configure_nufft_kernels() {
   if ((e = set_smem((const void*)k_fwd_rows, sm1)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_fwd_cols, sm1)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_adj_rows, sm1)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<5>, grid_smem<5>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<7>, grid_smem<7>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<9>, grid_smem<9>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<5, false>, grid_smem<5>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<7, false>, grid_smem<7>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<9, false>, grid_smem<9>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<5, true>, grid_smem<5>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<7, true>, grid_smem<7>())) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_grid<9, true>, grid_smem<9>())) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
   const void* degrids[] = {(const void*)k_degrid<5, false>, (const void*)k_degrid<7, false>,
                            (const void*)k_degrid<9, false>, (const void*)k_degrid<5, true>,
@@ -671,7 +707,8 @@ cudaError_t block_scales(Handle* h) {
 template <int W>
 static void launch_grid(Handle* h, const float2* in, int use_scale) {
   const GridGeom& g = h->g;
-  k_grid<W><<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->vblk, h->rec, in, h->cb,
+  auto kern = h->tune[PS_TUNE_GRID] ? k_grid<W, true> : k_grid<W, false>;
+  kern<<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->vblk, h->rec, in, h->cb,
                                                             use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
 }
 

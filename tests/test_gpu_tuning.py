@@ -38,22 +38,27 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
     A = rng.normal(size=(4, 9, n, n)).astype(np.float32)
     ref_psi = wav.psi(A.astype(np.float64), levels)
     ref_phi = meas.phi(S.astype(np.float64), pb["uv"], pb["w"].astype(np.float64))
+    Yr = (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))).astype(np.complex64)
+    ref_adj = meas.phi_adjoint(Yr.astype(np.complex128), pb["uv"], pb["w"].astype(np.float64), n)
     with _solver(pb, n, levels) as s:
-        for syn, deg in itertools.product(range(2), range(2)):
-            B.ps_set_tuning(s.h, [syn, deg, 0, 0])
-            assert B.ps_get_tuning(s.h) == [syn, deg, 0, 0]
+        for syn, deg, grd in itertools.product(range(2), range(2), range(2)):
+            B.ps_set_tuning(s.h, [syn, deg, grd, 0])
+            assert B.ps_get_tuning(s.h) == [syn, deg, grd, 0]
             Sg = np.empty((4, n, n), np.float32)
             B.ps_apply_psi(s.h, A, Sg)
             Yg = np.empty((M, 4), np.complex64)
             B.ps_apply_phi(s.h, S, Yg)
-            assert rel_err(Sg, ref_psi) <= 1e-6, (syn, deg)
-            assert rel_err(Yg, ref_phi) <= OP_TOL, (syn, deg)
+            Ag = np.empty((4, n, n), np.float32)
+            B.ps_apply_phi_adjoint(s.h, Yr, Ag)
+            assert rel_err(Sg, ref_psi) <= 1e-6, (syn, deg, grd)
+            assert rel_err(Yg, ref_phi) <= OP_TOL, (syn, deg, grd)
+            assert rel_err(Ag, ref_adj) <= OP_TOL, (syn, deg, grd)
 
 
 def test_set_tuning_rejects_unknown_choices():
     pb = make_problem(32, 500, 2, 1, seed=13)
     with _solver(pb, 32, 2) as s:
-        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 1, 0]):
+        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 2, 0], [0, 0, 0, 1]):
             with pytest.raises(B.PolsaraError) as e:
                 B.ps_set_tuning(s.h, bad)
             assert e.value.status == B.PS_EINVAL
@@ -62,8 +67,10 @@ def test_set_tuning_rejects_unknown_choices():
 
 def test_autotune_keeps_the_state_and_the_iteration():
     """Two solvers from the same start: one autotuned, one on the default choices.
-    The autotuner changes nothing in the state, and the next iterations agree to
-    FP32 rounding (the candidates differ only in the order of FP64 block sums)."""
+    The autotuner changes nothing in the state, and the next iterations agree within
+    the iteration bound of the parity tests (2e-5 per iteration): the candidates
+    differ only in the grouping of FP32 partial sums, which the ball factor
+    c_b = rho2 (1 - eps/r) amplifies when the block residual r is near eps."""
     n, M, levels = 128, 6000, 4
     pb = make_problem(n, M, levels, 4, seed=14)
     with _solver(pb, n, levels) as a, _solver(pb, n, levels) as b:
@@ -74,7 +81,7 @@ def test_autotune_keeps_the_state_and_the_iteration():
         picks = B.ps_autotune(a.h, reps=2)
         for slot, (choice, ms) in picks.items():
             assert choice >= 0
-            if slot in ("synthesis", "degrid"):
+            if slot in ("synthesis", "degrid", "grid"):
                 assert ms > 0
         after = np.empty((4, n, n), np.float32)
         B.ps_get_stokes(a.h, after)
@@ -85,4 +92,4 @@ def test_autotune_keeps_the_state_and_the_iteration():
         sb = np.empty((4, n, n), np.float32)
         B.ps_get_stokes(a.h, sa)
         B.ps_get_stokes(b.h, sb)
-        assert rel_err(sa, sb) <= 1e-5
+        assert rel_err(sa, sb) <= 2e-5 * 5
