@@ -300,7 +300,7 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
   }
   double filt[ps::kDb][ps::kMaxTaps];
   ps::daubechies_filters(filt);
-  if ((e = ps::upload_filters(filt)) != cudaSuccess) {
+  if ((e = ps::upload_filters(filt, h->stream)) != cudaSuccess) {
     h->err = std::string("upload filters: ") + cudaGetErrorString(e);
     return bail(PS_ECUDA);
   }
@@ -365,9 +365,10 @@ void ps_destroy(ps_handle* h) {
 // that gave up is reported as PS_ETIMEOUT (the flag is then cleared).
 static ps_status check_flags(Handle* h) {
   int f[4] = {0, 0, 0, 0};
-  CK(h, cudaMemcpy(f, h->dev_flags, sizeof(f), cudaMemcpyDeviceToHost));
+  CK(h, cudaMemcpyAsync(f, h->dev_flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
   if (f[0]) {
-    CK(h, cudaMemset(h->dev_flags, 0, sizeof(f)));
+    CK(h, cudaMemsetAsync(h->dev_flags, 0, sizeof(f), h->stream));
     return fail(h, PS_ETIMEOUT, "a bounded device wait (bulk-copy barrier) gave up; results of that launch are invalid");
   }
   return PS_OK;
@@ -423,11 +424,13 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   std::vector<double> uvh(2 * (size_t)M);
   std::vector<float> wh(M, 1.0f);
   if (M > 0) {
-    CK(h, cudaMemcpy(uvh.data(), uv, uvh.size() * sizeof(double),
-                     device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    // Caller device pointers are read on the handle's stream (its order, not the legacy stream's).
+    CK(h, cudaMemcpyAsync(uvh.data(), uv, uvh.size() * sizeof(double),
+                          device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, h->stream));
     if (weights)
-      CK(h, cudaMemcpy(wh.data(), weights, wh.size() * sizeof(float),
-                       device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      CK(h, cudaMemcpyAsync(wh.data(), weights, wh.size() * sizeof(float),
+                            device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
   }
   for (int m = 0; m < M; ++m) {
     if (!std::isfinite(uvh[2 * m]) || !std::isfinite(uvh[2 * m + 1]) || std::fabs(uvh[2 * m]) >= M_PI ||
@@ -562,15 +565,15 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   std::vector<float> corrh(h->n);
   for (int q = 0; q < h->n; ++q)
     corrh[q] = (float)(1.0 / ps::es_fourier(2.0 * M_PI * (q - h->n / 2) / g.K, g.W, g.beta));
-  CK(h, cudaMemcpy(h->tw, twh.data(), twh.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(h->corr, corrh.data(), corrh.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpyAsync(h->tw, twh.data(), twh.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(h->corr, corrh.data(), corrh.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   if (M > 0) {
-    CK(h, cudaMemcpy(h->rec, rech.data(), rech.size() * sizeof(float4), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->eps, eps, h->nblocks * sizeof(double), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->items, items.data(), items.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->gchunks, gchunks.data(), gchunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->vblk, vblk.data(), vblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpyAsync(h->rec, rech.data(), rech.size() * sizeof(float4), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->eps, eps, h->nblocks * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->items, items.data(), items.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->gchunks, gchunks.data(), gchunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->vblk, vblk.data(), vblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
     // Measurements into sorted order.
     ps_status st = stage_in(h, vis, 4 * (size_t)M * sizeof(float2), device_ptrs, h->vtmp);
     if (st != PS_OK) return st;
@@ -598,7 +601,8 @@ static ps_status power_iteration(Handle* h) {
   }
   const float inv = (float)(1.0 / std::sqrt(nrm));
   for (auto& v : x) v *= inv;
-  CK(h, cudaMemcpy(h->tmp4, x.data(), N4 * sizeof(float), cudaMemcpyHostToDevice));
+  // On the handle's (non-blocking) stream, so the iterations below are ordered after the copy.
+  CK(h, cudaMemcpyAsync(h->tmp4, x.data(), N4 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   double* dres = h->red + (size_t)h->red_cap - 600;
   double lam = 0.0;
   for (int it = 0; it < 1000; ++it) {

@@ -115,18 +115,18 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 }
 
 double es_fourier(double xi, int W, double beta) {
-  // phihat(xi) = int_{-W/2}^{W/2} phi(t) cos(xi t) dt; phi is even.
-  static std::vector<double> gx, gw;
-  static int cached = 0;
-  const int nodes = 400;
-  if (cached != nodes) {
-    gauss_legendre(nodes, gx, gw);
-    cached = nodes;
-  }
-  double half = 0.5 * W, s = 0.0;
-  for (int i = 0; i < nodes; ++i) {
-    double t = half * gx[i];
-    s += gw[i] * es_kernel(t, W, beta) * std::cos(xi * t);
+  // phihat(xi) = int_{-W/2}^{W/2} phi(t) cos(xi t) dt; phi is even. The quadrature rule is
+  // built once (thread-safe static initialisation: handles may be prepared concurrently).
+  struct Rule {
+    std::vector<double> x, w;
+    Rule() { gauss_legendre(400, x, w); }
+  };
+  static const Rule rule;
+  const double half = 0.5 * W;
+  double s = 0.0;
+  for (size_t i = 0; i < rule.x.size(); ++i) {
+    const double t = half * rule.x[i];
+    s += rule.w[i] * es_kernel(t, W, beta) * std::cos(xi * t);
   }
   return s * half;
 }

@@ -119,7 +119,7 @@ double es_kernel(double t, int W, double beta);            // ES kernel value at
 double es_fourier(double xi, int W, double beta);          // its Fourier transform at xi
 
 // Kernel launchers (return cudaGetLastError()).
-cudaError_t upload_filters(const double h[kDb][kMaxTaps]);
+cudaError_t upload_filters(const double h[kDb][kMaxTaps], cudaStream_t stream);
 
 // NUFFT pieces (nufft.cu).
 cudaError_t nufft_forward_grid(Handle* h, const float* X);                 // X (4 planes) -> G

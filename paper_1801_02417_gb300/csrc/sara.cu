@@ -30,7 +30,7 @@ __constant__ __align__(16) float c_g[kDb][kMaxTaps];
 __constant__ __align__(16) float2 c_hd[kDb][kMaxTaps];
 __constant__ __align__(16) float2 c_gd[kDb][kMaxTaps];
 
-cudaError_t upload_filters(const double h[kDb][kMaxTaps]) {
+cudaError_t upload_filters(const double h[kDb][kMaxTaps], cudaStream_t stream) {
   float hf[kDb][kMaxTaps], gf[kDb][kMaxTaps];
   for (int b = 0; b < kDb; ++b) {
     const int Lf = 2 * (b + 1);
@@ -45,10 +45,13 @@ cudaError_t upload_filters(const double h[kDb][kMaxTaps]) {
       hd[b][j] = make_float2(hf[b][j], hf[b][j]);
       gd[b][j] = make_float2(gf[b][j], gf[b][j]);
     }
-  cudaError_t e = cudaMemcpyToSymbol(c_h, hf, sizeof(hf));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_g, gf, sizeof(gf));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hd, hd, sizeof(hd));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gd, gd, sizeof(gd));
+  // On the caller's stream and waited for: kernels launched on non-blocking streams are
+  // not ordered after the legacy stream's copies.
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_h, hf, sizeof(hf), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_g, gf, sizeof(gf), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_hd, hd, sizeof(hd), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_gd, gd, sizeof(gd), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   return e;
 }
 
@@ -79,68 +82,6 @@ __device__ __forceinline__ void sara_epilogue(int mode, float val, size_t idx, f
     coef[idx] = scale * val;
   } else {
     thr[idx] = gamma * delta / (delta + fabsf(scale * val));
-  }
-}
-
-// One analysis level. Input arrays: in + map*in_map + basis*in_basis, m x m.
-__global__ void __launch_bounds__(256) k_analysis(const float* __restrict__ in, size_t in_map, size_t in_basis, int m,
-                                                  int TO, int n, int last, float* __restrict__ coef,
-                                                  float* __restrict__ thr, float* __restrict__ approx_out,
-                                                  int mode, float scale, float gamma, float delta) {
-  extern __shared__ float sm[];
-  const int bi = blockIdx.y;  // 0..7 -> db1..db8
-  const int map = blockIdx.z;
-  const int Lf = 2 * (bi + 1);
-  const int hm = m >> 1;
-  const int tilesx = hm / TO;
-  const int oy0 = (blockIdx.x / tilesx) * TO, ox0 = (blockIdx.x % tilesx) * TO;
-  const int RS = 2 * TO + Lf - 2;               // input tile side
-  float* in_s = sm;                              // RS x RS
-  float* lo_s = sm + RS * RS;                    // RS x TO
-  float* hi_s = lo_s + RS * TO;                  // RS x TO
-  const float* src = in + (size_t)map * in_map + (size_t)bi * in_basis;
-  for (int i = threadIdx.x; i < RS * RS; i += blockDim.x) {
-    const int r = i / RS, c = i - r * RS;
-    const int y = (2 * oy0 + r) % m, x = (2 * ox0 + c) % m;
-    in_s[i] = src[(size_t)y * m + x];
-  }
-  __syncthreads();
-  const float* h = c_h[bi];
-  const float* g = c_g[bi];
-  for (int i = threadIdx.x; i < RS * TO; i += blockDim.x) {
-    const int r = i / TO, k = i - r * TO;
-    const float* row = in_s + r * RS + 2 * k;
-    float lo = 0.f, hi = 0.f;
-    for (int j = 0; j < Lf; ++j) {
-      const float v = row[j];
-      lo = fmaf(h[j], v, lo);
-      hi = fmaf(g[j], v, hi);
-    }
-    lo_s[i] = lo;
-    hi_s[i] = hi;
-  }
-  __syncthreads();
-  const size_t base = ((size_t)map * kBases + (bi + 1)) * (size_t)n * n;
-  for (int i = threadIdx.x; i < TO * TO; i += blockDim.x) {
-    const int ky = i / TO, kx = i - ky * TO;
-    float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
-    for (int j = 0; j < Lf; ++j) {
-      const float a = lo_s[(2 * ky + j) * TO + kx];
-      const float b = hi_s[(2 * ky + j) * TO + kx];
-      ll = fmaf(h[j], a, ll);
-      lh = fmaf(g[j], a, lh);
-      hl = fmaf(h[j], b, hl);
-      hh = fmaf(g[j], b, hh);
-    }
-    const int Y = oy0 + ky, X = ox0 + kx;
-    sara_epilogue(mode, hl, base + (size_t)Y * n + (hm + X), coef, thr, scale, gamma, delta);        // x-high, y-low
-    sara_epilogue(mode, lh, base + (size_t)(hm + Y) * n + X, coef, thr, scale, gamma, delta);        // x-low, y-high
-    sara_epilogue(mode, hh, base + (size_t)(hm + Y) * n + (hm + X), coef, thr, scale, gamma, delta);
-    if (last) {
-      sara_epilogue(mode, ll, base + (size_t)Y * n + X, coef, thr, scale, gamma, delta);
-    } else {
-      approx_out[((size_t)map * kDb + bi) * (size_t)hm * hm + (size_t)Y * hm + X] = ll;
-    }
   }
 }
 
@@ -692,29 +633,6 @@ __global__ void __launch_bounds__(256, 3) k_syn_fine(const float* __restrict__ c
       make_float4((d.x + acc[0]) * k, (d.y + acc[1]) * k, (d.z + acc[2]) * k, (d.w + acc[3]) * k);
 }
 
-// Coarser levels with output side m >= 32: one basis per CTA (grid.y), output to approximation scratch.
-__global__ void __launch_bounds__(256, 4) k_syn_lv(const float* __restrict__ coef, const float* __restrict__ approx_in,
-                                                   int coarsest, int m, int n, float* __restrict__ approx_out) {
-  __shared__ __align__(16) float sm_s[kS4 + 2 * kTI * kPs];
-  float* s4 = sm_s;
-  float* s_lo = sm_s + kS4;
-  float* s_hi = s_lo + kTI * kPs;
-  const int bi = blockIdx.y, map = blockIdx.z;
-  const int tilesx = m / kTI;
-  const int oy0 = (blockIdx.x / tilesx) * kTI, ox0 = (blockIdx.x % tilesx) * kTI;
-  const int hm = m >> 1;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
-  const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
-  syn_load_dispatch(bi, cb, apx, n, m, oy0, ox0, s4);
-  cp_async_commit();
-  cp_async_wait<0>();
-  __syncthreads();
-  syn_compute_dispatch(bi, s4, s_lo, s_hi, acc);
-  const int r = threadIdx.x & 31, c0 = (threadIdx.x >> 5) * 4;
-  *reinterpret_cast<float4*>(approx_out + ((size_t)map * kDb + bi) * (size_t)m * m + (size_t)(oy0 + r) * m + ox0 + c0) =
-      make_float4(acc[0], acc[1], acc[2], acc[3]);
-}
 
 // ---------------------------------------------------------------------------
 // Synthesis for levels with output side m >= 64: 64 x 64 output tiles.
@@ -972,22 +890,179 @@ __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ co
 
 static size_t fast_analysis_smem() { return (size_t)kAnaFloats * sizeof(float) + 16; }
 
-static size_t analysis_smem(int TO) {
-  const int RS = 2 * TO + kMaxTaps - 2;
-  return (size_t)(RS * RS + 2 * RS * TO) * sizeof(float);
-}
 static size_t synthesis_smem(int TI) {
   const int CI = TI / 2 + kMaxTaps / 2 - 1;
   return (size_t)(4 * CI * CI + 2 * TI * CI) * sizeof(float);
 }
 
+// ---------------------------------------------------------------------------
+// Coarse levels in one launch. The analysis levels whose input side is at most
+// kTail (all levels for images of at most kTail), and the synthesis levels whose
+// output side is at most kTailSyn (from the coarsest up to level 2), each take a few
+// microseconds of work but cost one dependent launch each when tiled. Here one CTA
+// per (basis, map) keeps a whole level in shared memory and runs the levels back to
+// back; periodic boundaries are indices modulo the level side (a power of two).
+constexpr int kTail = 64;      // analysis: fused levels have input side <= kTail
+constexpr int kTailSyn = 32;   // synthesis: fused levels have output side <= kTailSyn (tiled is faster above)
+constexpr int kTailThreads = 512;
+
+// One analysis level of side m held in img (m x m, row-major): rows then columns,
+// epilogue on the three detail subbands (and on LL at the last level, else LL
+// replaces img as the next level's input, side m/2).
+template <int LF>
+__device__ __forceinline__ void tail_ana_level(float* img, float* lo, float* hi, int m, int bi, int map, int n,
+                                               int last, float* coef, float* thr, int mode, float scale, float gamma,
+                                               float delta) {
+  constexpr int b = LF / 2 - 1;
+  const int hm = m >> 1, mask = m - 1;
+  for (int u = threadIdx.x; u < m * hm; u += blockDim.x) {      // lo/hi[r][k] = sum_j h/g[j] img[r][2k + j]
+    const int r = u / hm, k = u - r * hm;
+    const float* row = img + r * m;
+    float a = 0.f, c = 0.f;
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+      const float v = row[(2 * k + j) & mask];
+      a = fmaf(c_h[b][j], v, a);
+      c = fmaf(c_g[b][j], v, c);
+    }
+    lo[u] = a;
+    hi[u] = c;
+  }
+  __syncthreads();
+  const size_t base = ((size_t)map * kBases + (bi + 1)) * (size_t)n * n;
+  for (int u = threadIdx.x; u < hm * hm; u += blockDim.x) {     // columns: rows 2 ky + j of lo/hi
+    const int ky = u / hm, kx = u - ky * hm;
+    float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+      const int y = (2 * ky + j) & mask;
+      const float a = lo[y * hm + kx], c = hi[y * hm + kx];
+      ll = fmaf(c_h[b][j], a, ll);
+      lh = fmaf(c_g[b][j], a, lh);
+      hl = fmaf(c_h[b][j], c, hl);
+      hh = fmaf(c_g[b][j], c, hh);
+    }
+    sara_epilogue(mode, hl, base + (size_t)ky * n + (hm + kx), coef, thr, scale, gamma, delta);         // x-high, y-low
+    sara_epilogue(mode, lh, base + (size_t)(hm + ky) * n + kx, coef, thr, scale, gamma, delta);         // x-low, y-high
+    sara_epilogue(mode, hh, base + (size_t)(hm + ky) * n + (hm + kx), coef, thr, scale, gamma, delta);
+    if (last) sara_epilogue(mode, ll, base + (size_t)ky * n + kx, coef, thr, scale, gamma, delta);
+    else img[u] = ll;   // img was fully consumed by the row pass before the barrier above
+  }
+  __syncthreads();
+}
+
+// Analysis levels l0..L in one CTA per (basis, map) = (blockIdx.x, blockIdx.y). The
+// input of level l0 (side m0 <= kTail) is X (l0 = 1) or that level's approximation
+// scratch (layout [map][basis][m0][m0]).
+__global__ void __launch_bounds__(kTailThreads) k_ana_tail(const float* __restrict__ in, int l0, int L, int n,
+                                                           float* __restrict__ coef, float* __restrict__ thr, int mode,
+                                                           float scale, float gamma, float delta) {
+  extern __shared__ float4 smt[];
+  float* img = reinterpret_cast<float*>(smt);
+  const int bi = blockIdx.x, map = blockIdx.y;
+  const int m0 = n >> (l0 - 1);
+  float* lo = img + m0 * m0;
+  float* hi = lo + m0 * (m0 >> 1);
+  const float* src = l0 == 1 ? in + (size_t)map * n * n : in + ((size_t)map * kDb + bi) * (size_t)m0 * m0;
+  for (int i = threadIdx.x; i < m0 * m0 / 4; i += blockDim.x)
+    reinterpret_cast<float4*>(img)[i] = reinterpret_cast<const float4*>(src)[i];
+  __syncthreads();
+  for (int l = l0, m = m0; l <= L; ++l, m >>= 1) {
+#define PS_TA(LFv) tail_ana_level<LFv>(img, lo, hi, m, bi, map, n, l == L, coef, thr, mode, scale, gamma, delta)
+    PS_SWITCH_LF(bi, PS_TA)
+#undef PS_TA
+  }
+}
+
+// One synthesis level to output side m: LL (hm x hm) in shared memory; the level's
+// detail subbands are first copied from the coefficient plane cb into det
+// (LH, HL, HH, each hm x hm); output into out (m x m).
+template <int LF>
+__device__ __forceinline__ void tail_syn_level(const float* LLs, const float* __restrict__ cb, int n, int m,
+                                               float* det, float* lo, float* hi, float* out) {
+  constexpr int b = LF / 2 - 1;
+  const int hm = m >> 1, hmask = hm - 1, hh2 = hm * hm;
+  for (int i = threadIdx.x; i < 3 * hh2; i += blockDim.x) {
+    const int sb = i / hh2, k = i - sb * hh2, r = k / hm, c = k - r * hm;
+    det[i] = sb == 0 ? cb[(size_t)(hm + r) * n + c] : (sb == 1 ? cb[(size_t)r * n + hm + c]
+                                                             : cb[(size_t)(hm + r) * n + hm + c]);
+  }
+  __syncthreads();
+  // Along y: output row R takes coefficient rows (R - j)/2 (mod hm) through taps j = R mod 2.
+  for (int u = threadIdx.x; u < m * hm; u += blockDim.x) {
+    const int R = u / hm, c = u - R * hm;
+    float a = 0.f, d = 0.f;
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+      if ((j & 1) != (R & 1)) continue;
+      const int kr = ((R - j) >> 1) & hmask;
+      const float vll = LLs[kr * hm + c];
+      const float vlh = det[kr * hm + c];
+      const float vhl = det[hh2 + kr * hm + c];
+      const float vhh = det[2 * hh2 + kr * hm + c];
+      a = fmaf(c_h[b][j], vll, fmaf(c_g[b][j], vlh, a));
+      d = fmaf(c_h[b][j], vhl, fmaf(c_g[b][j], vhh, d));
+    }
+    lo[u] = a;
+    hi[u] = d;
+  }
+  __syncthreads();
+  // Along x.
+  for (int u = threadIdx.x; u < m * m; u += blockDim.x) {
+    const int R = u / m, X = u - R * m;
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+      if ((j & 1) != (X & 1)) continue;
+      const int kc = ((X - j) >> 1) & hmask;
+      v = fmaf(c_h[b][j], lo[R * hm + kc], fmaf(c_g[b][j], hi[R * hm + kc], v));
+    }
+    out[u] = v;
+  }
+  __syncthreads();
+}
+
+// Synthesis levels L..l1 (l1 >= 2, output side of level l1 <= kTail) in one CTA per
+// (basis, map); the level-l1 output goes to approx_out ([map][basis][m][m]).
+__global__ void __launch_bounds__(kTailThreads) k_syn_tail(const float* __restrict__ coef, int L, int l1, int n,
+                                                           float* __restrict__ approx_out) {
+  extern __shared__ float4 smt[];
+  const int bi = blockIdx.x, map = blockIdx.y;
+  const int mmax = n >> (l1 - 1);
+  float* bufA = reinterpret_cast<float*>(smt);          // mmax^2
+  float* bufB = bufA + mmax * mmax;                     // mmax^2 / 4
+  float* lo = bufB + mmax * mmax / 4;                   // mmax x mmax/2
+  float* hi = lo + mmax * (mmax >> 1);
+  float* det = hi + mmax * (mmax >> 1);                 // 3 x (mmax/2)^2
+  const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
+  const int s0 = n >> L;                                // coarsest approximation side
+  // Level l writes bufA when l - l1 is even (the last level, the largest output, lands in
+  // bufA), so the coarsest approximation starts in the other buffer.
+  float* cur = (((L - l1) & 1) == 0) ? bufB : bufA;
+  for (int i = threadIdx.x; i < s0 * s0; i += blockDim.x) cur[i] = cb[(size_t)(i / s0) * n + (i % s0)];
+  __syncthreads();
+  for (int l = L; l >= l1; --l) {
+    const int m = n >> (l - 1);
+    float* nxt = (cur == bufA) ? bufB : bufA;
+#define PS_TS(LFv) tail_syn_level<LFv>(cur, cb, n, m, det, lo, hi, nxt)
+    PS_SWITCH_LF(bi, PS_TS)
+#undef PS_TS
+    cur = nxt;
+  }
+  float* dst = approx_out + ((size_t)map * kDb + bi) * (size_t)mmax * mmax;
+  for (int i = threadIdx.x; i < mmax * mmax / 4; i += blockDim.x)
+    reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(cur)[i];
+}
+
+static size_t ana_tail_smem(int m0) { return (size_t)2 * m0 * m0 * sizeof(float); }
+static size_t syn_tail_smem(int mmax) {
+  return (size_t)(mmax * mmax + mmax * mmax / 4 + mmax * mmax + 3 * (mmax / 2) * (mmax / 2)) * sizeof(float);
+}
+
 cudaError_t configure_nufft_kernels();
 
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)analysis_smem(32));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute((const void*)k_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)synthesis_smem(32));
   if (e != cudaSuccess) return e;
   for (const void* f : {(const void*)k_ana_l1, (const void*)k_ana_lv}) {
@@ -1008,6 +1083,12 @@ cudaError_t configure_kernels() {
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
+  e = cudaFuncSetAttribute((const void*)k_ana_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ana_tail_smem(kTail));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)k_syn_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syn_tail_smem(kTailSyn));
+  if (e != cudaSuccess) return e;
   return configure_nufft_kernels();
 }
 
@@ -1016,34 +1097,34 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
   const int n = h->n, L = h->L;
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
   float* buf[2] = {h->approx, h->approx + quarter};
-  for (int l = 1; l <= L; ++l) {
-    const int m = n >> (l - 1), hm = m / 2;
-    const int TO = hm < 32 ? hm : 32;
-    const float* in;
-    size_t in_map, in_basis;
-    if (l == 1) {
-      in = X;
-      in_map = (size_t)n * n;
-      in_basis = 0;
-    } else {
-      in = buf[(l - 2) & 1];
-      in_map = (size_t)kDb * m * m;
-      in_basis = (size_t)m * m;
+  int lt = L + 1;                                   // first level of the fused tail
+  for (int l = 1; l <= L; ++l)
+    if ((n >> (l - 1)) <= kTail) {
+      lt = l;
+      break;
     }
-    if (hm >= kTO && l == 1) {
-      dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
+  // Levels with input side > kTail: tiled, one launch per level (half side >= 128).
+  for (int l = 1; l < lt; ++l) {
+    const int m = n >> (l - 1), hm = m / 2;
+    const dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
+    if (l == 1) {
       k_ana_l1<<<grid, 256, fast_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[(l - 1) & 1], mode, scale,
                                                               gamma, delta, h->dev_flags);
-    } else if (hm >= kTO) {
-      dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
-      k_ana_lv<<<grid, 256, fast_analysis_smem(), h->stream>>>(in, m, n, l == L, coef, thr, buf[(l - 1) & 1], mode,
-                                                              scale, gamma, delta, h->dev_flags);
+      if (fine_done) {
+        const cudaError_t e = cudaEventRecord(fine_done, h->stream);
+        if (e != cudaSuccess) return e;
+      }
     } else {
-      dim3 grid((hm / TO) * (hm / TO), kDb, 4);
-      k_analysis<<<grid, 256, analysis_smem(TO), h->stream>>>(in, in_map, in_basis, m, TO, n, l == L, coef, thr,
-                                                              buf[(l - 1) & 1], mode, scale, gamma, delta);
+      k_ana_lv<<<grid, 256, fast_analysis_smem(), h->stream>>>(buf[(l - 2) & 1], m, n, l == L, coef, thr,
+                                                              buf[(l - 1) & 1], mode, scale, gamma, delta,
+                                                              h->dev_flags);
     }
-    if (l == 1 && fine_done) {
+  }
+  if (lt <= L) {
+    const float* in = lt == 1 ? X : buf[(lt - 2) & 1];
+    k_ana_tail<<<dim3(kDb, 4), kTailThreads, ana_tail_smem(n >> (lt - 1)), h->stream>>>(in, lt, L, n, coef, thr,
+                                                                                         mode, scale, gamma, delta);
+    if (lt == 1 && fine_done) {
       const cudaError_t e = cudaEventRecord(fine_done, h->stream);
       if (e != cudaSuccess) return e;
     }
@@ -1058,7 +1139,16 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
                                     int* err, int variant, cudaEvent_t fine_start = nullptr) {
   const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
   float* buf[2] = {approx, approx + quarter};
-  for (int l = L; l >= 1; --l) {
+  int lt = 0;                                       // lowest level of the fused tail (>= 2), 0: none
+  for (int l = 2; l <= L; ++l)
+    if ((n >> (l - 1)) <= kTailSyn) {
+      lt = l;
+      break;
+    }
+  if (lt)
+    k_syn_tail<<<dim3(kDb, 4), kTailThreads, syn_tail_smem(n >> (lt - 1)), stream>>>(coef, L, lt, n,
+                                                                                      buf[(lt - 1) & 1]);
+  for (int l = lt ? lt - 1 : L; l >= 1; --l) {
     const int m = n >> (l - 1);
     const int TI = m < 32 ? m : 32;
     const int tiles = (m / TI) * (m / TI);
@@ -1077,8 +1167,6 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
                                                                                      err);
     } else if (m >= kTI && l == 1) {
       k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, stream>>>(coef, ain, l == L, n, out);
-    } else if (m >= kTI) {
-      k_syn_lv<<<dim3(tiles, kDb, 4), 256, 0, stream>>>(coef, ain, l == L, m, n, aout);
     } else {
       dim3 grid(tiles, l == 1 ? 1 : kDb, 4);
       k_synthesis<<<grid, 256, synthesis_smem(TI), stream>>>(coef, ain, l == L, m, TI, n, l == 1, aout, out);
@@ -1137,7 +1225,7 @@ extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, in
       }
       double filt[kDb][kMaxTaps];
       daubechies_filters(filt);
-      e = upload_filters(filt);
+      e = upload_filters(filt, (cudaStream_t)cuda_stream);
       if (e != cudaSuccess) {
         set_global_error(std::string("apply_psi_static: filter upload: ") + cudaGetErrorString(e));
         return PS_ECUDA;

@@ -76,3 +76,36 @@ def test_each_request_same_alone_and_in_the_mix(problems):
         assert r.iterations == 300
         for k in range(4):
             assert _rel(r.S[k], alone[r.rid][k]) <= TOL_FINAL, (r.rid, k)
+
+
+def test_concurrent_preparation_matches_sequential(problems):
+    """The server prepares admitted problems on worker threads: handles created and given
+    their measurements concurrently must get the same operator norm and the same phi as
+    when prepared one at a time (host-side set-up shares no unsynchronised state)."""
+    import concurrent.futures
+
+    def prep(p):
+        s = PolarizedSARA(p.n, p.levels)
+        s.set_measurements(p.uv, p.vis, p.weights, p.offsets, p.eps)
+        return s
+
+    ref = []
+    for p in problems:
+        with prep(p) as s:
+            Y = np.empty((p.uv.shape[0], 4), np.complex64)
+            B.ps_apply_phi(s.h, np.ones((4, p.n, p.n), np.float32), Y)
+            ref.append((B.ps_get_params(s.h)["opnorm_sq"], Y))
+    for _ in range(3):
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(problems)) as ex:
+            handles = list(ex.map(prep, problems))
+        try:
+            for p, s, (on, Yr) in zip(problems, handles, ref):
+                Y = np.empty((p.uv.shape[0], 4), np.complex64)
+                B.ps_apply_phi(s.h, np.ones((4, p.n, p.n), np.float32), Y)
+                # phi (interpolation, no atomics) is deterministic; ||phi||^2 comes from power
+                # iterations whose gridding adds with float atomics.
+                assert np.array_equal(Y, Yr)
+                assert abs(B.ps_get_params(s.h)["opnorm_sq"] - on) <= 1e-5 * on   # stop rule 1e-7, atomics
+        finally:
+            for s in handles:
+                s.close()
