@@ -349,6 +349,19 @@ def served_measure(pool, rate: float, duration: float, seed: int) -> dict:
 
 
 # ------------------------------------------------------------------ arms
+def aggregate_replicas(ms: float, steps: int, world: int, device: str = "cuda"):
+    """Replicas (one independent solve per rank, no collective on the data path): the job's
+    time is the slowest rank's timed region, and the job processed world x steps iterations.
+    Returns (max ms over ranks, whole-job iterations/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1000.0)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -448,12 +461,8 @@ def run_own(args) -> None:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate_replicas(ms, args.steps, world, "cuda")
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
     launches = B.ps_kernels_per_iteration(s.h) * args.steps
 
     # Stage timing (CUDA events between stages, same launch configuration, eager).
