@@ -264,7 +264,8 @@ enum {
   PS_TUNE_DEGRID = 1,     /* 0 one row per thread over a work item,
                              1 one same-cell chunk per warp (broadcast stencil reads) */
   PS_TUNE_GRID = 2,       /* 0 one warp per same-cell chunk (2 kernel cells per lane),
-                             1 half-warps on alternate rows of a chunk (4 cells per lane) */
+                             1 half-warps on alternate rows of a chunk (4 cells per lane),
+                             2 lanes own (stencil row, channel pair) (W <= 8; W = 9 runs 0) */
   PS_TUNE_COUNT = 4       /* slot 3 reserved (0) */
 };
 

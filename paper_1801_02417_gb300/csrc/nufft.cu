@@ -419,12 +419,16 @@ __global__ void k_block_scale(const double* __restrict__ block_sum, const double
 // cells' taps never share a bank.
 constexpr int kGridV = kGridItem + 2;
 
-// HALF = false: one warp per same-cell chunk, lane l owns kernel cells l, l + 32.
-// HALF = true: the two half-warps take alternate rows of the chunk, lane l owns cells
-// (l & 15) + 16 q; each 16-byte broadcast read of a row's channels then serves 16 lanes
-// (two rows per instruction), and the halves' sums are combined by shuffles before the
-// shared-memory flush.
-template <int W, bool HALF>
+// Work split of a same-cell chunk (one warp per chunk in every form):
+// FORM 0: lane l owns kernel cells l, l + 32, all 8 channels.
+// FORM 1: the two half-warps take alternate rows of the chunk, lane l owns cells
+//   (l & 15) + 16 q; each 16-byte broadcast read of a row's channels then serves 16 lanes
+//   (two rows per instruction), and the halves' sums are combined by shuffles before the
+//   shared-memory flush.
+// FORM 2 (W <= 8): lane l < 4 W owns stencil row jy = l / 4 and channel pair cp = l % 4,
+//   i.e. the W cells (jy, 0..W-1) of two channels: per row it reads w_y[jy], its channel
+//   pair and the W x-weights (broadcasts), forms t = w_y x once and applies W packed FMAs.
+template <int W, int FORM>
 __global__ void __launch_bounds__(256) k_grid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
     const float4* __restrict__ rec, const float2* __restrict__ vin, const float* __restrict__ cb, int use_scale,
@@ -433,6 +437,7 @@ __global__ void __launch_bounds__(256) k_grid(
   constexpr int SS = TS + W - 1;
   constexpr int NC = SS * SS;                    // cells of the tile with halo
   constexpr int hw = W / 2;
+  constexpr bool HALF = FORM == 1;
   constexpr int LPR = HALF ? 16 : 32;            // lanes per row in flight
   constexpr int CPL = (W * W + LPR - 1) / LPR;   // kernel cells per lane
   extern __shared__ float4 smg[];
@@ -480,6 +485,31 @@ __global__ void __launch_bounds__(256) k_grid(
   for (int c = warp; c < nc; c += nwarps) {
     const int pk = chunks[it.cstart + c];
     const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
+    if (FORM == 2) {
+      static_assert(FORM != 2 || 4 * W <= 32, "row-channel lanes need 4 W <= 32");
+      const int jy = lane >> 2, cp = lane & 3;
+      if (lane < 4 * W) {
+        const u64* xp = reinterpret_cast<const u64*>(x4);   // row v, channel pair cp at 4 v + cp
+        const float* wyr = wys + jy * kGridV;
+        u64 acc2[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc2[k] = 0ull;
+        for (int v = v0; v < v0 + cnt; ++v) {
+          const u64 t = ffma2(fdup(wyr[v]), xp[4 * v + cp], 0ull);
+#pragma unroll
+          for (int k = 0; k < W; ++k) acc2[k] = ffma2(fdup(wxs[k * kGridV + v]), t, acc2[k]);
+        }
+        const int cell0 = (ly + jy) * SS + lx;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          float lo, hi;
+          f2unpack(acc2[k], lo, hi);
+          atomicAdd(acc + (2 * cp) * NC + cell0 + k, lo);
+          atomicAdd(acc + (2 * cp + 1) * NC + cell0 + k, hi);
+        }
+      }
+      continue;
+    }
     // a2[q][p] holds channels (2p, 2p+1) of kernel cell q: packed FP32x2 accumulation.
     u64 a2[CPL][4];
 #pragma unroll
@@ -648,12 +678,12 @@ cudaError_t configure_nufft_kernels() {
   if ((e = set_smem((const void*)k_fwd_rows, sm1)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_fwd_cols, sm1)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_adj_rows, sm1)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<5, false>, grid_smem<5>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<7, false>, grid_smem<7>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<9, false>, grid_smem<9>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<5, true>, grid_smem<5>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<7, true>, grid_smem<7>())) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_grid<9, true>, grid_smem<9>())) != cudaSuccess) return e;
+  const void* grids[] = {(const void*)k_grid<5, 0>, (const void*)k_grid<7, 0>, (const void*)k_grid<9, 0>,
+                         (const void*)k_grid<5, 1>, (const void*)k_grid<7, 1>, (const void*)k_grid<9, 1>,
+                         (const void*)k_grid<5, 2>, (const void*)k_grid<7, 2>};
+  const size_t grid_bytes[] = {grid_smem<5>(), grid_smem<7>(), grid_smem<9>()};
+  for (int i = 0; i < 8; ++i)
+    if ((e = set_smem(grids[i], grid_bytes[i < 6 ? i % 3 : i - 6])) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
   const void* degrids[] = {(const void*)k_degrid<5, false>, (const void*)k_degrid<7, false>,
                            (const void*)k_degrid<9, false>, (const void*)k_degrid<5, true>,
@@ -707,7 +737,8 @@ cudaError_t block_scales(Handle* h) {
 template <int W>
 static void launch_grid(Handle* h, const float2* in, int use_scale) {
   const GridGeom& g = h->g;
-  auto kern = h->tune[PS_TUNE_GRID] ? k_grid<W, true> : k_grid<W, false>;
+  const int form = (h->tune[PS_TUNE_GRID] == 2 && 4 * W > 32) ? 0 : h->tune[PS_TUNE_GRID];   // W = 9: no FORM 2
+  auto kern = form == 1 ? k_grid<W, 1> : (form == 2 ? k_grid<W, (4 * W <= 32 ? 2 : 0)> : k_grid<W, 0>);
   kern<<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->vblk, h->rec, in, h->cb,
                                                             use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
 }
