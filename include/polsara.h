@@ -266,7 +266,9 @@ enum {
   PS_TUNE_GRID = 2,       /* 0 one warp per same-cell chunk (2 kernel cells per lane),
                              1 half-warps on alternate rows of a chunk (4 cells per lane),
                              2 lanes own (stencil row, channel pair) (W <= 8; W = 9 runs 0) */
-  PS_TUNE_COUNT = 4       /* slot 3 reserved (0) */
+  PS_TUNE_ANALYSIS = 3,   /* tiled analysis levels: 0 one (tile, basis, map) unit per CTA,
+                             1 persistent (2 CTAs/SM looping over units, next unit's copies in flight) */
+  PS_TUNE_COUNT = 4
 };
 
 /* Autotuner: after ps_set_measurements, time every candidate of every PS_TUNE_*

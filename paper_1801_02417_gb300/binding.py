@@ -350,7 +350,7 @@ def ps_estimate_bytes(n: int, levels: int, M: int) -> int:
     return int(lib().ps_estimate_bytes(int(n), int(levels), int(M)))
 
 
-TUNE_SLOTS = ("synthesis", "degrid", "grid", "reserved3")
+TUNE_SLOTS = ("synthesis", "degrid", "grid", "analysis")
 
 
 def ps_autotune(h, reps: int = 5) -> dict:

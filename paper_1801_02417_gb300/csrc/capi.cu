@@ -298,6 +298,12 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
     h->err = std::string("configure kernels: ") + cudaGetErrorString(e);
     return bail(PS_ECUDA);
   }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    h->err = "ps_create: device attributes";
+    return bail(PS_ECUDA);
+  }
   double filt[ps::kDb][ps::kMaxTaps];
   ps::daubechies_filters(filt);
   if ((e = ps::upload_filters(filt, h->stream)) != cudaSuccess) {
@@ -942,7 +948,7 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms) {
 
 // ---------------------------------------------------------------------------
 // Autotuner: candidates per PS_TUNE_* slot, each timed on the handle's own data.
-static const int kTuneCandidates[PS_TUNE_COUNT] = {2, 2, 3, 1};
+static const int kTuneCandidates[PS_TUNE_COUNT] = {2, 2, 3, 2};
 
 // Mean milliseconds of `reps` launches of f after one untimed launch.
 extern "C++" {
@@ -991,6 +997,17 @@ ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms) 
     best_ms[slot] = best_t;
     return PS_OK;
   };
+  // Analysis: the dual update of steps 5-6 as the iteration runs it (staged A and gamma W
+  // reads), on scratch coefficients so the state's A is untouched.
+  {
+    ps_status st0 = ensure_tmp36(h);
+    if (st0 != PS_OK) return st0;
+    CK(h, cudaMemsetAsync(h->tmp36, 0, 36 * (size_t)h->N * sizeof(float), h->stream));
+  }
+  ps_status sta = pick(PS_TUNE_ANALYSIS, [&] {
+    return ps::sara_analysis(h, h->S, h->tmp36, h->T, ps::SARA_DUAL, (float)(h->rho1 / 3.0), 0.f, 0.f);
+  });
+  if (sta != PS_OK) return sta;
   // Synthesis: Psi A of the current coefficients, written where it already is.
   ps_status st = pick(PS_TUNE_SYNTHESIS, [&] { return ps::sara_synthesis(h, h->A, h->PsiA); });
   if (st != PS_OK) return st;

@@ -100,8 +100,9 @@ struct Handle {
   float2 *tw = nullptr;       // K per-stage twiddles: stage t at [2^t - 1, 2^(t+1) - 1)
   float *corr = nullptr;      // n de-apodisation factors 1 / phihat(2 pi x / K)
 
-  // Launch choices (PS_TUNE_* slots).
+  // Launch choices (PS_TUNE_* slots) and the device's SM count (persistent grids).
   int32_t tune[PS_TUNE_COUNT] = {};
+  int num_sms = 0;
 
   // CUDA graph of one iteration.
   cudaGraphExec_t graph = nullptr;

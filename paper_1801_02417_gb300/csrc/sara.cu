@@ -15,6 +15,7 @@
 // sums the eight bases and the Dirac part in registers and writes Psi A once.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -394,6 +395,7 @@ __device__ __forceinline__ void stage_epilogue(const float* coef, const float* t
     const size_t off = sb == 0 ? base + (size_t)Y * n + hm + ox0
                                : (sb == 1 ? base + (size_t)(hm + Y) * n + ox0 : base + (size_t)(hm + Y) * n + hm + ox0);
     float* dst = (arr ? st_t : st_a) + sb * kTO * kTO + r * kTO;
+    fence_proxy_async();   // the persistent form refills buffers its threads have read
     bulk_g2s(dst, (arr ? thr : coef) + off, kTO * sizeof(float), bar);
   }
 }
@@ -493,6 +495,92 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
   __syncthreads();
   ana_dispatch(bi, approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, S, map, n, hm, oy0, ox0, last, coef, thr,
                approx_out, mode, scale, gamma, delta, err);
+}
+
+// Persistent form of the tiled analysis levels: 2 CTAs per SM loop over the units
+// (tile, basis, map) of a level, tile fastest. A unit's input rows are copied while
+// the previous unit's columns are filtered, and its staged A and gamma W rows
+// (double-buffered) while the whole previous unit runs, so the copy latency that the
+// one-unit-per-CTA form exposes once per CTA is hidden behind compute.
+constexpr int kAnaPFloats = kA2In + 2 * kRSmax * kPlo + 4 * kStage;
+static size_t pers_analysis_smem() { return (size_t)kAnaPFloats * sizeof(float) + 32; }
+
+__global__ void __launch_bounds__(256, 2) k_ana_pers(const float* __restrict__ in, size_t in_map, size_t in_basis, int m,
+                                                     int n, int last, float* __restrict__ coef,
+                                                     float* __restrict__ thr, float* __restrict__ approx_out,
+                                                     int mode, float scale, float gamma, float delta, int* err) {
+  extern __shared__ float4 smp[];
+  float* in_s = reinterpret_cast<float*>(smp);
+  float* lo_s = in_s + kA2In;
+  float* hi_s = lo_s + kRSmax * kPlo;
+  float* st = hi_s + kRSmax * kPlo;                                  // set s: A at st + 2 s kStage, gamma W after it
+  uint64_t* bar = reinterpret_cast<uint64_t*>(st + 4 * kStage);     // [0] input rows, [1 + s] stage set s
+  const int hm = m >> 1, tilesx = hm / kTO, tiles = tilesx * tilesx;
+  const int units = tiles * kDb * 4;
+  const bool staged = mode == SARA_DUAL;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) mbar_init(&bar[q], 1);
+  __syncthreads();
+  int issued_in = 0, issued_st[2] = {0, 0};
+  auto decode = [&](int u, int& bi, int& map, int& oy0, int& ox0) {
+    const int t = u % tiles, r = u / tiles;
+    bi = r % kDb;
+    map = r / kDb;
+    oy0 = (t / tilesx) * kTO;
+    ox0 = (t % tilesx) * kTO;
+  };
+  auto issue = [&](int u, int s) {
+    int bi, map, oy0, ox0;
+    decode(u, bi, map, oy0, ox0);
+    ana_issue_input(in + (size_t)map * in_map + (size_t)bi * in_basis, m, oy0, ox0, 2 * kTO + 2 * (bi + 1) - 2, in_s,
+                    &bar[0]);
+    ++issued_in;
+    if (staged) {
+      stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, st + 2 * s * kStage,
+                     st + (2 * s + 1) * kStage, &bar[1 + s]);
+      ++issued_st[s];
+    }
+  };
+  auto abort_all = [&]() {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      if (issued_in) (void)mbar_wait(&bar[0], (issued_in - 1) & 1);
+      for (int q = 0; q < 2; ++q)
+        if (issued_st[q]) (void)mbar_wait(&bar[1 + q], (issued_st[q] - 1) & 1);
+    }
+  };
+  int u = blockIdx.x;
+  if (u < units) issue(u, 0);
+  for (int i = 0; u < units; ++i, u += gridDim.x) {
+    const int s = i & 1;
+    int bi, map, oy0, ox0;
+    decode(u, bi, map, oy0, ox0);
+    const bool ok = mbar_wait(&bar[0], i & 1);
+    if (__syncthreads_or(!ok)) {
+      abort_all();
+      return;
+    }
+#define PS_PR(LFv) ana_rows<LFv>(in_s, lo_s, hi_s)
+    PS_SWITCH_LF(bi, PS_PR)
+#undef PS_PR
+    // The input tile is consumed and every thread is past the previous unit's columns,
+    // so the input buffer and stage set s ^ 1 can be refilled for the next unit.
+    __syncthreads();
+    if (u + (int)gridDim.x < units) issue(u + gridDim.x, s ^ 1);
+    if (staged) {
+      const bool ok2 = mbar_wait(&bar[1 + s], (i >> 1) & 1);
+      if (__syncthreads_or(!ok2)) {
+        abort_all();
+        return;
+      }
+    }
+#define PS_PC(LFv)                                                                                                 \
+  ana_cols<LFv>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta,      \
+                st + 2 * s * kStage, st + (2 * s + 1) * kStage)
+    PS_SWITCH_LF(bi, PS_PC)
+#undef PS_PC
+    __syncthreads();   // lo/hi consumed before the next unit's rows
+  }
 }
 
 // Synthesis of one basis on a TI x TI output tile, split in two steps so the
@@ -1083,6 +1171,12 @@ cudaError_t configure_kernels() {
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
+  e = cudaFuncSetAttribute((const void*)k_ana_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pers_analysis_smem());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)k_ana_pers, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute((const void*)k_ana_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ana_tail_smem(kTail));
   if (e != cudaSuccess) return e;
@@ -1107,7 +1201,19 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
   for (int l = 1; l < lt; ++l) {
     const int m = n >> (l - 1), hm = m / 2;
     const dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
-    if (l == 1) {
+    if (h->tune[PS_TUNE_ANALYSIS] == 1) {
+      const int units = (int)(grid.x * grid.y * grid.z);
+      const int ctas = std::min(units, 2 * std::max(1, h->num_sms));
+      const float* in = l == 1 ? X : buf[(l - 2) & 1];
+      const size_t in_map = l == 1 ? (size_t)n * n : (size_t)kDb * m * m, in_basis = l == 1 ? 0 : (size_t)m * m;
+      k_ana_pers<<<ctas, 256, pers_analysis_smem(), h->stream>>>(in, in_map, in_basis, m, n, l == L, coef, thr,
+                                                                 buf[(l - 1) & 1], mode, scale, gamma, delta,
+                                                                 h->dev_flags);
+      if (l == 1 && fine_done) {
+        const cudaError_t e = cudaEventRecord(fine_done, h->stream);
+        if (e != cudaSuccess) return e;
+      }
+    } else if (l == 1) {
       k_ana_l1<<<grid, 256, fast_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[(l - 1) & 1], mode, scale,
                                                               gamma, delta, h->dev_flags);
       if (fine_done) {

@@ -37,28 +37,33 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
     S = rng.normal(size=(4, n, n)).astype(np.float32)
     A = rng.normal(size=(4, 9, n, n)).astype(np.float32)
     ref_psi = wav.psi(A.astype(np.float64), levels)
+    ref_psia = wav.psi_adjoint(S.astype(np.float64), levels)
     ref_phi = meas.phi(S.astype(np.float64), pb["uv"], pb["w"].astype(np.float64))
     Yr = (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))).astype(np.complex64)
     ref_adj = meas.phi_adjoint(Yr.astype(np.complex128), pb["uv"], pb["w"].astype(np.float64), n)
     with _solver(pb, n, levels) as s:
-        for syn, deg, grd in itertools.product(range(2), range(2), range(3)):
-            B.ps_set_tuning(s.h, [syn, deg, grd, 0])
-            assert B.ps_get_tuning(s.h) == [syn, deg, grd, 0]
+        for syn, deg, grd, ana in itertools.product(range(2), range(2), range(3), range(2)):
+            B.ps_set_tuning(s.h, [syn, deg, grd, ana])
+            assert B.ps_get_tuning(s.h) == [syn, deg, grd, ana]
             Sg = np.empty((4, n, n), np.float32)
             B.ps_apply_psi(s.h, A, Sg)
             Yg = np.empty((M, 4), np.complex64)
             B.ps_apply_phi(s.h, S, Yg)
             Ag = np.empty((4, n, n), np.float32)
             B.ps_apply_phi_adjoint(s.h, Yr, Ag)
-            assert rel_err(Sg, ref_psi) <= 1e-6, (syn, deg, grd)
-            assert rel_err(Yg, ref_phi) <= OP_TOL, (syn, deg, grd)
-            assert rel_err(Ag, ref_adj) <= OP_TOL, (syn, deg, grd)
+            Cg = np.empty((4, 9, n, n), np.float32)
+            B.ps_apply_psi_adjoint(s.h, S, Cg)
+            key = (syn, deg, grd, ana)
+            assert rel_err(Sg, ref_psi) <= 1e-6, key
+            assert rel_err(Cg, ref_psia) <= 1e-6, key
+            assert rel_err(Yg, ref_phi) <= OP_TOL, key
+            assert rel_err(Ag, ref_adj) <= OP_TOL, key
 
 
 def test_set_tuning_rejects_unknown_choices():
     pb = make_problem(32, 500, 2, 1, seed=13)
     with _solver(pb, 32, 2) as s:
-        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 3, 0], [0, 0, 0, 1]):
+        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 3, 0], [0, 0, 0, 2]):
             with pytest.raises(B.PolsaraError) as e:
                 B.ps_set_tuning(s.h, bad)
             assert e.value.status == B.PS_EINVAL
@@ -81,7 +86,7 @@ def test_autotune_keeps_the_state_and_the_iteration():
         picks = B.ps_autotune(a.h, reps=2)
         for slot, (choice, ms) in picks.items():
             assert choice >= 0
-            if slot in ("synthesis", "degrid", "grid"):
+            if slot in ("synthesis", "degrid", "grid", "analysis"):
                 assert ms > 0
         after = np.empty((4, n, n), np.float32)
         B.ps_get_stokes(a.h, after)
@@ -93,3 +98,34 @@ def test_autotune_keeps_the_state_and_the_iteration():
         B.ps_get_stokes(a.h, sa)
         B.ps_get_stokes(b.h, sb)
         assert rel_err(sa, sb) <= 2e-5 * 5
+
+
+def test_persistent_analysis_iterations_match_oracle():
+    """The persistent analysis form inside the iteration (dual update with staged A and
+    gamma W, refilled buffers), forced on, against Algorithm 1 of the FP64 oracle from a
+    random state, at a size whose level 1 is tiled (the form's only use)."""
+    from oracle import primal_dual as opd
+    from paper_1801_02417_gb300 import inputs
+    n, M, levels = 128, 1500, 3
+    pb = make_problem(n, M, levels, 2, seed=16)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, n)
+    p = opd.step_sizes(on, opd.POLARIZED)
+    st = inputs.random_state(n, M, 23, 0.05)
+    st32 = {k: (v.astype(np.complex64) if k == "B" else v.astype(np.float32)) for k, v in st.items()}
+    ref = {k: v.astype(np.complex128 if k == "B" else np.float64) for k, v in st32.items()}
+    W = np.random.default_rng(7).uniform(0.2, 1.0, size=(4, 9, n, n)).astype(np.float32)
+    gamma = 0.02
+    T = gamma * W.astype(np.float64)
+    s = PolarizedSARA(n, levels, tau=p.tau, rho1=p.rho1, rho2=p.rho2, rho3=p.rho3)
+    with s:
+        s.set_measurements(pb["uv"], pb["Y"], pb["w"], pb["off"], pb["eps"])
+        s.set_sara_weights(W, gamma)
+        B.ps_set_tuning(s.h, [0, 0, 0, 1])
+        s.set_state(st32)
+        s.pd_iterate(3)
+        for _ in range(3):
+            ref = opd.pd_iteration(ref, prob, T, p, opd.POLARIZED)
+        got = s.get_state()
+    for k in ("S", "Z", "A", "B", "C", "D"):
+        assert rel_err(got[k], ref[k]) <= 2e-5 * 3, k
