@@ -58,7 +58,10 @@ def test_phi_and_adjoint_match_direct_dft(coverage, n, M):
     assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(Yg) ** 2) * np.sum(np.abs(Yr) ** 2))
 
 
-@pytest.mark.parametrize("n,levels", [(64, 4), (32, 3), (16, 4), (128, 2), (256, 6)])
+# Covers every split between the tiled levels and the fused coarse levels: all levels fused
+# (n <= 64 analysis), level 1 tiled + the rest fused (128), fused synthesis tails of one to
+# three levels, and 512 at 4 levels (the largest size of the batched and served mixes).
+@pytest.mark.parametrize("n,levels", [(64, 4), (32, 3), (16, 4), (128, 2), (128, 4), (256, 4), (256, 6), (512, 4)])
 def test_psi_and_adjoint_match_oracle(n, levels):
     pb = make_problem(n, 64, levels, 1, seed=2)
     rng = np.random.default_rng(4)
