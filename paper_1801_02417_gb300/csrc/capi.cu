@@ -401,6 +401,13 @@ static __global__ void k_fill(float* p, int n, float v) {
   if (i < n) p[i] = v;
 }
 
+// p[0 .. len) = v, grid-stride, float4 stores (p 16-byte aligned, len a multiple of 4).
+static __global__ void k_fill4(float4* p, size_t len4, float v) {
+  const float4 q = make_float4(v, v, v, v);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len4; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = q;
+}
+
 extern "C" {
 
 ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const float* vis, const float* weights,
@@ -478,22 +485,30 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   g.tilesX = (g.Wd + ps::kGridTile - 1) / ps::kGridTile;
   auto gi = [&](int k) { return g.full ? (k & (g.K - 1)) : k + g.off; };
 
-  // Sort key of each row: gridding tile, then tap-centre cell.
+  // Sort key of each row: gridding tile, then tap-centre cell (row-major in the tile).
+  // The keys take at most tilesX^2 kGridTile^2 values, so a stable counting sort orders
+  // the rows in O(M) (rows of one cell keep the caller's order).
   std::vector<int32_t> perm(M);
-  std::iota(perm.begin(), perm.end(), 0);
   std::vector<int64_t> key(M);
+  std::vector<int32_t> bucket(M);
+  const int64_t nbuckets = (int64_t)g.tilesX * g.tilesX * ps::kGridTile * ps::kGridTile;
+  std::vector<int32_t> count(nbuckets + 1, 0);
   for (int m = 0; m < M; ++m) {
     const int gy = gi(cy[m]), gx = gi(cx[m]);
     const int64_t tile = (int64_t)(gy / ps::kGridTile) * g.tilesX + gx / ps::kGridTile;
     key[m] = (tile << 26) | ((int64_t)gy << 13) | gx;
+    bucket[m] = (int32_t)(tile * ps::kGridTile * ps::kGridTile + (gy % ps::kGridTile) * ps::kGridTile +
+                          gx % ps::kGridTile);
+    ++count[bucket[m] + 1];
   }
+  for (int64_t b = 0; b < nbuckets; ++b) count[b + 1] += count[b];
+  for (int m = 0; m < M; ++m) perm[count[bucket[m]]++] = m;
   if (M > 0) h->offsets_host.assign(block_offsets, block_offsets + nblocks + 1);
   else h->offsets_host.assign(1, 0);
   // Storage order: every row sorted by tap-centre cell (tile-major), blocks interleaved.
   std::vector<uint16_t> blk_user(M);
   for (int b = 0; b < (M > 0 ? nblocks : 0); ++b)
     for (int64_t i = block_offsets[b]; i < block_offsets[b + 1]; ++i) blk_user[i] = (uint16_t)b;
-  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t c) { return key[a] < key[c]; });
   std::vector<uint16_t> vblk(M);
   for (int i = 0; i < M; ++i) vblk[i] = blk_user[perm[i]];
   std::vector<ps::GridItem> items;
@@ -640,10 +655,9 @@ ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_
     ps_status st = stage_in(h, W, len * sizeof(float), device_ptrs, h->T);
     if (st != PS_OK) return st;
     CK(h, ps::scale_copy(h, h->T, h->T, len, gamma));
-  } else {
-    std::vector<float> v(len, (float)gamma);
-    CK(h, cudaMemcpyAsync(h->T, v.data(), len * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+  } else {   // W = 1: gamma W filled on the device
+    k_fill4<<<1024, 256, 0, h->stream>>>(reinterpret_cast<float4*>(h->T), len / 4, (float)gamma);
+    CK(h, cudaGetLastError());
   }
   h->gamma = gamma;
   if (!device_ptrs) CK(h, cudaStreamSynchronize(h->stream));
