@@ -584,8 +584,11 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
       twh[(1 << t) - 1 + p] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
   std::vector<float> corrh(h->n);
-  for (int q = 0; q < h->n; ++q)
+  // phihat is even: q and n - q (offsets -d and +d from the centre) share a value.
+  for (int q = 0; q <= h->n / 2; ++q) {
     corrh[q] = (float)(1.0 / ps::es_fourier(2.0 * M_PI * (q - h->n / 2) / g.K, g.W, g.beta));
+    if (q > 0 && q < h->n / 2) corrh[h->n - q] = corrh[q];
+  }
   CK(h, cudaMemcpyAsync(h->tw, twh.data(), twh.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaMemcpyAsync(h->corr, corrh.data(), corrh.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   if (M > 0) {
