@@ -274,8 +274,11 @@ enum {
 /* Autotuner: after ps_set_measurements, time every candidate of every PS_TUNE_*
  * slot on the handle's data (reps launches each, CUDA events on the handle's
  * stream, after one untimed launch) and keep the fastest. The state of the
- * iteration is unchanged (the timed launches recompute Psi A of the current A and
- * interpolate the current spectrum into scratch). choices (nullable) receives the
+ * iteration is unchanged (the timed launches run the analysis dual update on scratch
+ * coefficients, recompute Psi A of the current A in place, interpolate the current
+ * spectrum into scratch and grid the current dual into the gridding accumulator, an
+ * intermediate; phi^dagger B is kept). Uses (and on first use allocates) the handle's
+ * 36N operator scratch. choices (nullable) receives the
  * PS_TUNE_COUNT picks; ms (nullable) receives, per slot, the time of the pick in
  * milliseconds. Synchronises the stream. PS_ESTATE before measurements. */
 ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms);
