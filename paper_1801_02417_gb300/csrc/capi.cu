@@ -226,7 +226,7 @@ static ps_status build_graph(Handle* h) {
     if (graph) cudaGraphDestroy(graph);
     return fail(h, PS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(&h->graph, graph, 0);
+  e = cudaGraphInstantiate(&h->graph, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(h, PS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   h->graph_mode = h->mode;
@@ -287,7 +287,12 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
     }
     h->own_stream = true;
   }
-  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+  // The SARA branch of the iteration graph runs at the highest stream priority (graph
+  // nodes keep their capture stream's priority): measured slightly faster at 1024^2 than
+  // equal priorities, and faster than prioritising the NUFFT branch.
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     h->err = "ps_create: auxiliary stream/events";
