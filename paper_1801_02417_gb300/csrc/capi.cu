@@ -1232,7 +1232,7 @@ static ps_status batch_build(ps_batch* b) {
     if (graph) cudaGraphDestroy(graph);
     return batch_fail(err != cudaSuccess ? err : e, "batch: capture");
   }
-  e = cudaGraphInstantiate(&b->graph, graph, 0);
+  e = cudaGraphInstantiate(&b->graph, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return batch_fail(e, "batch: instantiate");
   for (size_t i = 0; i < b->hs.size(); ++i) b->versions[i] = b->hs[i]->version;
