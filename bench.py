@@ -437,9 +437,14 @@ def run_own(args) -> None:
     gamma = default_gamma(s, dirty)
     s.set_sara_weights(None, gamma)
     s.set_mode(B.PS_POLARIZED)
-    # Launch choices measured on this problem before the warm-up.
-    picks = B.ps_autotune(s.h, reps=5)
-    tuning = {k: v[0] for k, v in picks.items() if not k.startswith("reserved")}
+    # Launch choices measured on this problem before the warm-up (or forced by --tuning,
+    # e.g. to profile the configuration the autotuner picks without a profiler attached).
+    if args.tuning:
+        B.ps_set_tuning(s.h, [int(v) for v in args.tuning.split(",")])
+        tuning = dict(zip(B.TUNE_SLOTS, B.ps_get_tuning(s.h)))
+    else:
+        picks = B.ps_autotune(s.h, reps=5)
+        tuning = {k: v[0] for k, v in picks.items() if not k.startswith("reserved")}
 
     # Warm-up, then exactly K timed steps between barriers.
     s.pd_iterate(args.warmup)
@@ -600,6 +605,7 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="", help="force the launch choices (comma-separated PS_TUNE_* values)")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batched measurement")
     ap.add_argument("--serve-rate", type=float, default=20.0)

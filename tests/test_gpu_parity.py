@@ -265,3 +265,34 @@ def test_unconstrained_solve_and_violation_counts():
     assert counts[B.PS_POLARIZED]["violations"] <= counts[B.PS_NO_CONSTRAINT]["violations"]
     # Pixels outside P at all (zeta = 0): the constraint removes most of them (oracle: 188 vs 2266).
     assert 2 * counts[B.PS_POLARIZED]["violations_raw"] < counts[B.PS_NO_CONSTRAINT]["violations_raw"]
+
+
+def test_literal_ball_radius_matches_oracle():
+    """literal_ball = 1 (the printed radius eps / rho2 of step 8) against the oracle's
+    iteration under the same reading, from a random state. With that radius (eps ||phi||^2
+    here) every B~/rho2 lies inside its ball, so the data dual B is zeroed on both sides:
+    the data constraint is inactive, which is why the Moreau reading (radius eps) is the
+    default."""
+    n, M, levels, nblocks = 32, 1500, 3, 4
+    pb = make_problem(n, M, levels, nblocks, seed=17)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, n)
+    p = opd.step_sizes(on, opd.POLARIZED)
+    p.literal_ball = True
+    st32 = _random_state(n, M, 29, scale=0.05)
+    ref = {k: v.astype(np.complex128 if k == "B" else np.float64) for k, v in st32.items()}
+    W = np.random.default_rng(8).uniform(0.2, 1.0, size=(4, 9, n, n)).astype(np.float32)
+    gamma = 0.02
+    T = gamma * W.astype(np.float64)
+    steps = dict(tau=p.tau, rho1=p.rho1, rho2=p.rho2, rho3=p.rho3)
+    with _solver(pb, n, levels, steps=steps, literal_ball=True) as s:
+        s.set_sara_weights(W, gamma)
+        s.set_state(st32)
+        s.pd_iterate(3)
+        for _ in range(3):
+            ref = opd.pd_iteration(ref, prob, T, p, opd.POLARIZED)
+        got = s.get_state()
+    for k in ("S", "Z", "A", "C", "D"):
+        assert rel_err(got[k], ref[k]) <= 2e-5 * 3, k
+    scale = float(np.abs(st32["B"]).max())
+    assert np.abs(got["B"]).max() <= 1e-6 * scale and np.abs(ref["B"]).max() <= 1e-6 * scale
