@@ -142,62 +142,176 @@ class Server:
         self.autotune = autotune
         self._tuning: dict = {}
         self._tuning_lock = threading.Lock()
+        self._thread: threading.Thread | None = None
 
     def _prepare(self, prob: Problem) -> PolarizedSARA:
         s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS)
-        s.set_measurements(prob.uv, prob.vis, prob.weights, prob.offsets, prob.eps)
-        if self.autotune:
-            apply_tuning(s, prob.n, prob.uv.shape[0], self._tuning, self._tuning_lock)
+        try:
+            s.set_measurements(prob.uv, prob.vis, prob.weights, prob.offsets, prob.eps)
+            if self.autotune:
+                apply_tuning(s, prob.n, prob.uv.shape[0], self._tuning, self._tuning_lock)
+        except BaseException:
+            s.close()
+            raise
         return s
 
     def run(self, requests: list[tuple[float, Problem]]) -> list[Result]:
         """Serve requests given as (arrival offset in seconds, problem), in real time."""
         order = sorted(range(len(requests)), key=lambda i: requests[i][0])
-        pending = list(order)
-        t0 = time.perf_counter()
+        results: list[Result] = []
+
+        def poll(now):
+            out = []
+            while order and requests[order[0]][0] <= now:
+                rid = order.pop(0)
+                out.append((rid, requests[rid][0], requests[rid][1]))
+            return out
+
+        def next_arrival():
+            return requests[order[0]][0] if order else None
+
+        def fail(rid, exc):
+            raise exc
+
+        self._schedule(poll, next_arrival, lambda: not order, results.append, fail)
+        return results
+
+    # ---- live serving: submit() from any thread while the scheduler runs.
+    def __enter__(self) -> "Server":
+        self.start()
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.stop()
+
+    def start(self) -> None:
+        """Start the scheduler on a background thread; requests then come from submit()."""
+        import queue
+        self._queue = queue.Queue()
+        self._closing = threading.Event()
+        self._futures: dict = {}
+        self._next_id = 0
+        self._t0 = time.perf_counter()
+        self._thread = threading.Thread(target=self._live_loop, daemon=True)
+        self._thread.start()
+
+    def submit(self, prob: Problem) -> concurrent.futures.Future:
+        """Queue one solve; the future resolves to its Result (or raises its error)."""
+        if self._thread is None or self._closing.is_set():
+            raise RuntimeError("server not running: submit() before start() or after stop()")
+        fut: concurrent.futures.Future = concurrent.futures.Future()
+        with self._tuning_lock:
+            rid = self._next_id
+            self._next_id += 1
+        self._futures[rid] = fut
+        self._queue.put((rid, time.perf_counter() - self._t0, prob))
+        return fut
+
+    def stop(self) -> None:
+        """Finish every submitted request, then end the scheduler thread."""
+        if self._thread is None:
+            return
+        self._closing.set()
+        self._thread.join()
+        self._thread = None
+
+    def _live_loop(self) -> None:
+        import queue
+        waiting: list = []
+
+        def poll(now):
+            while True:
+                try:
+                    waiting.append(self._queue.get_nowait())
+                except queue.Empty:
+                    break
+            out, waiting[:] = list(waiting), []
+            return out
+
+        def deliver(r: Result) -> None:
+            self._futures.pop(r.rid).set_result(r)
+
+        def fail(rid, exc) -> None:
+            self._futures.pop(rid).set_exception(exc)
+
+        def done() -> bool:
+            return self._closing.is_set() and self._queue.empty()
+
+        try:
+            self._schedule(poll, lambda: None, done, deliver, fail, t0=self._t0)
+        except BaseException as e:   # fail every request still waiting
+            for f in list(self._futures.values()):
+                if not f.done():
+                    f.set_exception(e)
+            raise
+
+    def _schedule(self, poll, next_arrival, exhausted, deliver, fail, t0: float | None = None) -> None:
+        """Admission in arrival order by footprint and free slots, preparation on worker
+        threads, ticks of `check_every` iterations of every active problem (each on its own
+        stream), stopping rules, delivery. poll(now) returns newly arrived (rid, arrival,
+        problem); exhausted() tells that no more will arrive; fail(rid, exc) reports a
+        request whose preparation or iterations raised (its memory is released first)."""
+        t0 = time.perf_counter() if t0 is None else t0
+        pending: list = []
         in_use = 0
         preparing: dict = {}
         active: list[_Active] = []
-        results: list[Result] = []
-        lock = threading.Lock()
         with concurrent.futures.ThreadPoolExecutor(self.prep_workers) as pool:
-            while pending or preparing or active:
+            while True:
                 now = time.perf_counter() - t0
+                pending.extend(poll(now))
+                if not (pending or preparing or active) and exhausted():
+                    break
                 # Admission in arrival order: footprint within budget and a free slot.
-                while pending and requests[pending[0]][0] <= now:
-                    rid = pending[0]
-                    fp = requests[rid][1].footprint()
+                while pending:
+                    rid, arrival, prob = pending[0]
+                    fp = prob.footprint()
                     if len(active) + len(preparing) >= self.max_active or (in_use + fp > self.budget and in_use > 0):
                         break
                     pending.pop(0)
                     in_use += fp
-                    preparing[pool.submit(self._prepare, requests[rid][1])] = (rid, fp, now)
+                    preparing[pool.submit(self._prepare, prob)] = (rid, arrival, prob, fp, now)
                 for fut in [f for f in preparing if f.done()]:
-                    rid, fp, adm = preparing.pop(fut)
-                    active.append(_Active(rid, requests[rid][1], fut.result(), requests[rid][0], adm, self.policy))
+                    rid, arrival, prob, fp, adm = preparing.pop(fut)
+                    if fut.exception() is not None:
+                        in_use -= fp
+                        fail(rid, fut.exception())
+                        continue
+                    active.append(_Active(rid, prob, fut.result(), arrival, adm, self.policy))
                 if not active:
                     if preparing:
                         concurrent.futures.wait(list(preparing), timeout=0.05,
                                                 return_when=concurrent.futures.FIRST_COMPLETED)
-                    elif pending:
-                        time.sleep(max(0.0, min(0.05, requests[pending[0]][0] - (time.perf_counter() - t0))))
+                    else:
+                        nxt = next_arrival()
+                        wait = 0.005 if nxt is None else max(0.0, nxt - (time.perf_counter() - t0))
+                        time.sleep(min(0.05, wait))
                     continue
                 # One tick: launch every active problem (each on its own stream), then check them.
+                errors: dict = {}
                 for a in active:
-                    a.launch()
+                    try:
+                        a.launch()
+                    except B.PolsaraError as e:
+                        errors[a.rid] = e
                 still = []
                 for a in active:
-                    if a.advance():
+                    try:
+                        if a.rid in errors:
+                            raise errors[a.rid]
+                        if not a.advance():
+                            still.append(a)
+                            continue
                         S = a.s.get_stokes()
-                        with lock:
-                            results.append(Result(a.rid, a.arrival, a.admitted, time.perf_counter() - t0,
-                                                  a.used, S))
+                    except B.PolsaraError as e:
                         a.s.close()
                         in_use -= a.prob.footprint()
-                    else:
-                        still.append(a)
+                        fail(a.rid, e)
+                        continue
+                    a.s.close()
+                    in_use -= a.prob.footprint()
+                    deliver(Result(a.rid, a.arrival, a.admitted, time.perf_counter() - t0, a.used, S))
                 active = still
-        return results
 
 
 def summarize(results: list[Result]) -> dict:

@@ -109,3 +109,31 @@ def test_concurrent_preparation_matches_sequential(problems):
         finally:
             for s in handles:
                 s.close()
+
+
+def test_live_submissions_resolve_like_solo_runs(problems):
+    """Server.start/submit/stop: requests submitted from several threads while the
+    scheduler runs resolve their futures with the same maps as solo runs; a request whose
+    measurements the library rejects (eps <= 0) fails its own future only."""
+    import concurrent.futures
+    import dataclasses
+
+    pol = Policy(rel_tol=0.0, max_iter=200, reweights=1, check_every=25)
+    alone = [Server(hbm_budget=1 << 40, max_active=1, policy=pol).run([(0.0, p)])[0].S for p in problems]
+    bad = dataclasses.replace(problems[0], eps=-np.abs(problems[0].eps))
+    budget = sum(p.footprint() for p in problems[:3])
+    with Server(hbm_budget=budget, max_active=8, policy=pol) as srv:
+        with concurrent.futures.ThreadPoolExecutor(4) as ex:
+            futs = list(ex.map(srv.submit, problems + [bad] + problems[::-1]))
+        got = [f.result(timeout=300) for f in futs[:len(problems)]]
+        with pytest.raises(B.PolsaraError) as e:
+            futs[len(problems)].result(timeout=300)
+        assert e.value.status == B.PS_EINVAL
+        got_rev = [f.result(timeout=300) for f in futs[len(problems) + 1:]]
+    with pytest.raises(RuntimeError):
+        srv.submit(problems[0])
+    assert len({r.rid for r in got + got_rev}) == 2 * len(problems)
+    for r, ref in zip(got + got_rev, alone + alone[::-1]):
+        assert r.iterations == 200
+        for k in range(4):
+            assert _rel(r.S[k], ref[k]) <= TOL_FINAL, (r.rid, k)
