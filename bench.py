@@ -130,6 +130,13 @@ SINGLE_KERNEL_STAGES = {"primal": "k_primal", "analysis": "k_ana_l1", "synthesis
                         "degrid": "k_degrid", "grid": "k_grid"}
 
 
+def stage_kernel(stage: str, tuning: list) -> str:
+    """Name of the kernel a single-kernel stage launches under the handle's launch choices."""
+    if stage == "analysis" and tuning[3] == 1:
+        return "k_ana_pers"
+    return SINGLE_KERNEL_STAGES[stage]
+
+
 def kernel_sources_digest() -> str:
     """SHA-256 of the CUDA sources: DRAM counters taken from another build are not reported."""
     import hashlib
@@ -485,7 +492,8 @@ def run_own(args) -> None:
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = sbytes[dom] / (stages[dom] * 1e-3) / 1e9
-    traffic, traffic_src = dram_traffic(SINGLE_KERNEL_STAGES[dom], wl.name)
+    dom_kernel = stage_kernel(dom, B.ps_get_tuning(s.h))
+    traffic, traffic_src = dram_traffic(dom_kernel, wl.name)
     total_bytes = sum(sbytes.values())
 
     # End to end through the C ABI with host buffers (pinned), as a user runs a solve:
@@ -570,7 +578,7 @@ def run_own(args) -> None:
                        "parallelism": "replicas" if world > 1 else "single", "tuning": tuning,
                        "l2": "no flush: per-iteration working set ~%.0f MB > 126 MB L2" % (total_bytes / 1e6),
                        "vis_iters_per_s": value * M},
-            "roofline": {"bound": "hbm", "kernel": SINGLE_KERNEL_STAGES[dom], "stage": dom, "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": dom_kernel, "stage": dom, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_source": traffic_src, "peak_source": peak_src + " hbm_gbs (copy)",
                          "algorithmic_bytes": sbytes[dom], "launch_ms": stages[dom]},

@@ -265,7 +265,9 @@ enum {
                              1 one same-cell chunk per warp (broadcast stencil reads) */
   PS_TUNE_GRID = 2,       /* 0 one warp per same-cell chunk (2 kernel cells per lane),
                              1 half-warps on alternate rows of a chunk (4 cells per lane),
-                             2 lanes own (stencil row, channel pair) (W <= 8; W = 9 runs 0) */
+                             2 lanes own (stencil row, channel pair) (W <= 8; W = 9 runs 0),
+                             3 tensor cores: each chunk's block as a small matrix product
+                               (TF32 hi/lo split, FP32 accumulation) (W <= 8; W = 9 runs 0) */
   PS_TUNE_ANALYSIS = 3,   /* tiled analysis levels: 0 one (tile, basis, map) unit per CTA,
                              1 persistent (2 CTAs/SM looping over units, next unit's copies in flight) */
   PS_TUNE_COUNT = 4

@@ -428,50 +428,102 @@ constexpr int kGridV = kGridItem + 2;
 // FORM 2 (W <= 8): lane l < 4 W owns stencil row jy = l / 4 and channel pair cp = l % 4,
 //   i.e. the W cells (jy, 0..W-1) of two channels: per row it reads w_y[jy], its channel
 //   pair and the W x-weights (broadcasts), forms t = w_y x once and applies W packed FMAs.
+// FORM 3 (W <= 8): the chunk's block as a product of two small matrices on the tensor
+//   cores (mma.m16n8k8, TF32 with hi/lo operand splitting for FP32 accuracy); lanes load
+//   distinct words of the rows instead of broadcasts.
+// Stride of the 8 channel planes of a gridding tile: its (kGridTile + W - 1)^2 cells plus
+// one, odd modulo 32, so lanes adding to the same cell of different planes spread over banks.
+template <int W>
+__host__ __device__ constexpr int grid_plane() {
+  return (kGridTile + W - 1) * (kGridTile + W - 1) + 1;
+}
+
+// FP32 -> TF32 hi part (round to nearest, ties away) and the TF32 rounding of the
+// remainder; hi + lo carries the operand to about 2^-21 of its value.
+__device__ __forceinline__ void tf32_split(float a, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(a));
+  const float r = a - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+// The same split with integer rounding of the hi part (round half up on the magnitude) and
+// the remainder left for the tensor core to truncate to TF32: |a - hi - lo_tf32| <= 2^-21 |a|.
+__device__ __forceinline__ void tf32_split_fast(float a, uint32_t& hi, uint32_t& lo) {
+  hi = (__float_as_uint(a) + 0x1000u) & 0xFFFFE000u;
+  lo = __float_as_uint(a - __uint_as_float(hi));
+}
+// d += A B for one m16n8k8 TF32 tile: A (16 x 8) fragment a[4], B (8 x 8) fragment b[2].
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// FORM 3 keeps 8 y-weights and 8 x-weights per row for kGridItem rows plus 8 spare
+// rows (its last k-step of a chunk may read, and then discard, up to 7 rows past it).
+constexpr int kGridRows3 = kGridItem + 8;
+// Floats of staged weights per work item (a multiple of 4: the tile planes after them stay 16-byte aligned).
 template <int W, int FORM>
-__global__ void __launch_bounds__(256) k_grid(
-    const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
-    const float4* __restrict__ rec, const float2* __restrict__ vin, const float* __restrict__ cb, int use_scale,
-    int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
-  constexpr int TS = kGridTile;
-  constexpr int SS = TS + W - 1;
-  constexpr int NC = SS * SS;                    // cells of the tile with halo
-  constexpr int hw = W / 2;
-  constexpr bool HALF = FORM == 1;
-  constexpr int LPR = HALF ? 16 : 32;            // lanes per row in flight
-  constexpr int CPL = (W * W + LPR - 1) / LPR;   // kernel cells per lane
-  extern __shared__ float4 smg[];
-  float4* x4 = smg;                              // kGridItem x 2: mixed, scaled channels of each row
-  float* acc = reinterpret_cast<float*>(smg + 2 * kGridItem);   // 8 planes of NC cells
-  float* wxs = acc + 8 * NC;                     // W planes of kGridV
-  float* wys = wxs + W * kGridV;                 // W planes of kGridV
-  const GridItem it = items[blockIdx.x];
-  for (int i = threadIdx.x; i < 8 * NC; i += blockDim.x) acc[i] = 0.f;
-  const int nv = it.vend - it.vstart;
-  const float4* v4 = reinterpret_cast<const float4*>(vin);
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    const int idx = it.vstart + j;
-    float fx, fy, w;
-    int cx, cy;
-    unpack_rec(rec[idx], fx, fy, w, cx, cy);
-    const float sc = (use_scale ? cb[vblk[idx]] : 1.0f) * w;
-    const float4 b0 = v4[2 * (size_t)idx], b1 = v4[2 * (size_t)idx + 1];   // RR, RL | LR, LL
-    // x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL).
-    x4[2 * j] = make_float4(sc * (b0.x + b1.z), sc * (b0.y + b1.w), sc * (b0.x - b1.z), sc * (b0.y - b1.w));
-    x4[2 * j + 1] = make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
-    float wx[W], wy[W];
-    es_weights<W>(fx, beta, wx);
-    es_weights<W>(fy, beta, wy);
+__host__ __device__ constexpr int grid_wts_floats() {
+  return FORM == 3 ? 16 * kGridRows3 : (2 * W * kGridV + 3) / 4 * 4;
+}
+
+// Step 1 for one visibility j of a work item: row record r (fx, fy, w), its correlations
+// b0 = (RR, RL), b1 = (LR, LL) and its block scale. The weights go to wts: FORM 0-2 as W
+// x-planes then W y-planes of stride kGridV; FORM 3 row-major, 8 y-weights per row
+// (zero past W) for kGridRows3 rows, then 8 x-weights per row likewise.
+template <int W, int FORM>
+__device__ __forceinline__ void grid_stage_row(int j, float4 r, float4 b0, float4 b1, float blk_scale, float beta,
+                                               float4* __restrict__ x4, float* __restrict__ wts) {
+  float fx, fy, w;
+  int cx, cy;
+  unpack_rec(r, fx, fy, w, cx, cy);
+  const float sc = blk_scale * w;
+  // x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL).
+  x4[2 * j] = make_float4(sc * (b0.x + b1.z), sc * (b0.y + b1.w), sc * (b0.x - b1.z), sc * (b0.y - b1.w));
+  x4[2 * j + 1] = make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
+  float wx[W], wy[W];
+  es_weights<W>(fx, beta, wx);
+  es_weights<W>(fy, beta, wy);
+  if (FORM == 3) {
+    static_assert(FORM != 3 || W <= 8, "row-major weights hold 8 taps");
+    float t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = k < W ? wy[k] : 0.f;
+    float4* yb = reinterpret_cast<float4*>(wts) + 2 * j;
+    yb[0] = make_float4(t[0], t[1], t[2], t[3]);
+    yb[1] = make_float4(t[4], t[5], t[6], t[7]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = k < W ? wx[k] : 0.f;
+    float4* xb = reinterpret_cast<float4*>(wts + 8 * kGridRows3) + 2 * j;
+    xb[0] = make_float4(t[0], t[1], t[2], t[3]);
+    xb[1] = make_float4(t[4], t[5], t[6], t[7]);
+  } else {
+    float* wxs = wts;
+    float* wys = wts + W * kGridV;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
       wxs[k * kGridV + j] = wx[k];
       wys[k * kGridV + j] = wy[k];
     }
   }
-  __syncthreads();
+}
+
+// Step 2: every same-cell chunk of the work item, one warp per chunk (FORM as above),
+// added to the channel-planar tile acc (8 planes of grid_plane<W>() floats).
+template <int W, int FORM>
+__device__ __forceinline__ void grid_chunks(const int32_t* __restrict__ chunks, int nc, const float4* __restrict__ x4,
+                                            const float* __restrict__ wts, float* __restrict__ acc) {
+  const float* wxs = wts;
+  const float* wys = wts + W * kGridV;
+  constexpr int TS = kGridTile;
+  constexpr int SS = TS + W - 1;
+  constexpr int NP = grid_plane<W>();
+  constexpr bool HALF = FORM == 1;
+  constexpr int LPR = HALF ? 16 : 32;            // lanes per row in flight
+  constexpr int CPL = (W * W + LPR - 1) / LPR;   // kernel cells per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int sub = HALF ? (lane >> 4) : 0, sl = HALF ? (lane & 15) : lane;
-  const int nc = it.cend - it.cstart;
   int wxo[CPL], wyo[CPL], coff[CPL];
 #pragma unroll
   for (int q = 0; q < CPL; ++q) {
@@ -483,9 +535,67 @@ __global__ void __launch_bounds__(256) k_grid(
   }
   const ulonglong2* xv = reinterpret_cast<const ulonglong2*>(x4);
   for (int c = warp; c < nc; c += nwarps) {
-    const int pk = chunks[it.cstart + c];
+    const int pk = chunks[c];
     const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
-    if (FORM == 2) {
+    if constexpr (FORM == 3) {
+      // Tensor cores: the chunk's W x W x 8 block is the product G = P^T Y over its rows,
+      // P[v][(jx, c)] = w_x[v][jx] x_c[v] (64 rows (jx, c) in MT m-tiles of 16) and
+      // Y[v][jy] = w_y[v][jy] (8 columns), k = 8 rows per mma.m16n8k8 (TF32). Each FP32
+      // operand is split into TF32 hi + lo parts and the three products hi hi, hi lo,
+      // lo hi are accumulated in FP32 (the lo lo term is below FP32 rounding). Rows of
+      // the last k-step past the chunk enter as zeros.
+      constexpr int MT = (W + 1) / 2;
+      const int g = lane >> 2, tig = lane & 3;
+      const float* xs = reinterpret_cast<const float*>(x4);
+      const float* wyb = wts;
+      const float* wxb = wts + 8 * kGridRows3;
+      float d[MT][4];
+#pragma unroll
+      for (int t = 0; t < MT; ++t) d[t][0] = d[t][1] = d[t][2] = d[t][3] = 0.f;
+      const int vend = v0 + cnt;
+      for (int k0 = v0; k0 < vend; k0 += 8) {
+        const int va = k0 + tig, vb = va + 4;
+        // Rows past the chunk (the next chunk's, or the zeroed spare rows after the
+        // item) keep their finite P entries; their Y entries are zeroed.
+        const float xa = xs[8 * va + g], xb = xs[8 * vb + g];
+        uint32_t bh[2], bl[2];
+        tf32_split(va < vend ? wyb[8 * va + g] : 0.f, bh[0], bl[0]);
+        tf32_split(vb < vend ? wyb[8 * vb + g] : 0.f, bh[1], bl[1]);
+        const float4* wa = reinterpret_cast<const float4*>(wxb + 8 * va);
+        const float4* wb = reinterpret_cast<const float4*>(wxb + 8 * vb);
+        const float4 wa0 = wa[0], wa1 = wa[1], wb0 = wb[0], wb1 = wb[1];
+        const float pa[8] = {wa0.x, wa0.y, wa0.z, wa0.w, wa1.x, wa1.y, wa1.z, wa1.w};
+        const float pb[8] = {wb0.x, wb0.y, wb0.z, wb0.w, wb1.x, wb1.y, wb1.z, wb1.w};
+        uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+          tf32_split_fast(pa[2 * t] * xa, ah[t][0], al[t][0]);
+          tf32_split_fast(pb[2 * t] * xb, ah[t][2], al[t][2]);
+          if (2 * t + 1 < W) {
+            tf32_split_fast(pa[2 * t + 1] * xa, ah[t][1], al[t][1]);
+            tf32_split_fast(pb[2 * t + 1] * xb, ah[t][3], al[t][3]);
+          } else {
+            ah[t][1] = al[t][1] = ah[t][3] = al[t][3] = 0u;
+          }
+        }
+        // Small terms first; consecutive products go to different tiles (independent).
+#pragma unroll
+        for (int t = 0; t < MT; ++t) mma_tf32(d[t], al[t], bh);
+#pragma unroll
+        for (int t = 0; t < MT; ++t) mma_tf32(d[t], ah[t], bl);
+#pragma unroll
+        for (int t = 0; t < MT; ++t) mma_tf32(d[t], ah[t], bh);
+      }
+      // d[t][i]: cell (jy = 2 tig + (i & 1), jx = 2 t + (i >> 1)), channel g.
+      const int base = g * NP + ly * SS + lx;
+#pragma unroll
+      for (int t = 0; t < MT; ++t)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int jy = 2 * tig + (i & 1), jx = 2 * t + (i >> 1);
+          if (jy < W && jx < W) atomicAdd(acc + base + jy * SS + jx, d[t][i]);
+        }
+    } else if constexpr (FORM == 2) {
       static_assert(FORM != 2 || 4 * W <= 32, "row-channel lanes need 4 W <= 32");
       const int jy = lane >> 2, cp = lane & 3;
       if (lane < 4 * W) {
@@ -504,102 +614,146 @@ __global__ void __launch_bounds__(256) k_grid(
         for (int k = 0; k < W; ++k) {
           float lo, hi;
           f2unpack(acc2[k], lo, hi);
-          atomicAdd(acc + (2 * cp) * NC + cell0 + k, lo);
-          atomicAdd(acc + (2 * cp + 1) * NC + cell0 + k, hi);
+          atomicAdd(acc + (2 * cp) * NP + cell0 + k, lo);
+          atomicAdd(acc + (2 * cp + 1) * NP + cell0 + k, hi);
         }
       }
-      continue;
-    }
-    // a2[q][p] holds channels (2p, 2p+1) of kernel cell q: packed FP32x2 accumulation.
-    u64 a2[CPL][4];
-#pragma unroll
-    for (int q = 0; q < CPL; ++q)
-#pragma unroll
-      for (int p = 0; p < 4; ++p) a2[q][p] = 0ull;
-    if (HALF) {
-      for (int v = v0 + sub; v < v0 + cnt; v += 2) {
-        const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
-#pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
-          a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
-          a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
-          a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
-          a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
-        }
-      }
+    } else {
+      // a2[q][p] holds channels (2p, 2p+1) of kernel cell q: packed FP32x2 accumulation.
+      u64 a2[CPL][4];
 #pragma unroll
       for (int q = 0; q < CPL; ++q)
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          float lo, hi;
-          f2unpack(a2[q][p], lo, hi);
-          lo += __shfl_xor_sync(0xffffffffu, lo, 16);
-          hi += __shfl_xor_sync(0xffffffffu, hi, 16);
-          a2[q][p] = f2pack(lo, hi);
-        }
-    } else {
-      int v = v0;
-      for (; v + 1 < v0 + cnt; v += 2) {
-        const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1], y0 = xv[2 * v + 2], y1 = xv[2 * v + 3];
+        for (int p = 0; p < 4; ++p) a2[q][p] = 0ull;
+      if (HALF) {
+        for (int v = v0 + sub; v < v0 + cnt; v += 2) {
+          const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
-          const u64 k1 = fdup(wxs[wxo[q] + v + 1] * wys[wyo[q] + v + 1]);
-          a2[q][0] = ffma2(k1, y0.x, ffma2(k0, x0.x, a2[q][0]));
-          a2[q][1] = ffma2(k1, y0.y, ffma2(k0, x0.y, a2[q][1]));
-          a2[q][2] = ffma2(k1, y1.x, ffma2(k0, x1.x, a2[q][2]));
-          a2[q][3] = ffma2(k1, y1.y, ffma2(k0, x1.y, a2[q][3]));
+          for (int q = 0; q < CPL; ++q) {
+            const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
+            a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
+            a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
+            a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
+            a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            float lo, hi;
+            f2unpack(a2[q][p], lo, hi);
+            lo += __shfl_xor_sync(0xffffffffu, lo, 16);
+            hi += __shfl_xor_sync(0xffffffffu, hi, 16);
+            a2[q][p] = f2pack(lo, hi);
+          }
+      } else {
+        int v = v0;
+        for (; v + 1 < v0 + cnt; v += 2) {
+          const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1], y0 = xv[2 * v + 2], y1 = xv[2 * v + 3];
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
+            const u64 k1 = fdup(wxs[wxo[q] + v + 1] * wys[wyo[q] + v + 1]);
+            a2[q][0] = ffma2(k1, y0.x, ffma2(k0, x0.x, a2[q][0]));
+            a2[q][1] = ffma2(k1, y0.y, ffma2(k0, x0.y, a2[q][1]));
+            a2[q][2] = ffma2(k1, y1.x, ffma2(k0, x1.x, a2[q][2]));
+            a2[q][3] = ffma2(k1, y1.y, ffma2(k0, x1.y, a2[q][3]));
+          }
+        }
+        if (v < v0 + cnt) {
+          const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
+            a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
+            a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
+            a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
+            a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
+          }
         }
       }
-      if (v < v0 + cnt) {
-        const ulonglong2 x0 = xv[2 * v], x1 = xv[2 * v + 1];
+      const int cbase = ly * SS + lx;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          const u64 k0 = fdup(wxs[wxo[q] + v] * wys[wyo[q] + v]);
-          a2[q][0] = ffma2(k0, x0.x, a2[q][0]);
-          a2[q][1] = ffma2(k0, x0.y, a2[q][1]);
-          a2[q][2] = ffma2(k0, x1.x, a2[q][2]);
-          a2[q][3] = ffma2(k0, x1.y, a2[q][3]);
-        }
-      }
-    }
-    const int cbase = ly * SS + lx;
+      for (int q = 0; q < CPL; ++q) {
+        if (sub == 0 && sl + LPR * q < W * W) {
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-      if (sub == 0 && sl + LPR * q < W * W) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          float lo, hi;
-          f2unpack(a2[q][p], lo, hi);
-          atomicAdd(acc + (2 * p) * NC + cbase + coff[q], lo);
-          atomicAdd(acc + (2 * p + 1) * NC + cbase + coff[q], hi);
+          for (int p = 0; p < 4; ++p) {
+            float lo, hi;
+            f2unpack(a2[q][p], lo, hi);
+            atomicAdd(acc + (2 * p) * NP + cbase + coff[q], lo);
+            atomicAdd(acc + (2 * p + 1) * NP + cbase + coff[q], hi);
+          }
         }
       }
     }
   }
-  __syncthreads();
+}
+
+// Step 3: the tile with its halo added to the global accumulator.
+template <int W>
+__device__ __forceinline__ void grid_flush(const float* __restrict__ acc, int ty, int tx, int Wd, int full, int K,
+                                           float4* __restrict__ Acc) {
+  constexpr int TS = kGridTile;
+  constexpr int SS = TS + W - 1;
+  constexpr int NC = SS * SS;
+  constexpr int NP = grid_plane<W>();
+  constexpr int hw = W / 2;
   for (int c = threadIdx.x; c < NC; c += blockDim.x) {
     const int ly = c / SS, lx = c - (c / SS) * SS;
-    int gy = it.ty * TS - hw + ly, gx = it.tx * TS - hw + lx;
+    int gy = ty * TS - hw + ly, gx = tx * TS - hw + lx;
     if (full) {
       gy &= (K - 1);
       gx &= (K - 1);
     } else if (gy < 0 || gy >= Wd || gx < 0 || gx >= Wd) {
       continue;
     }
-    const float4 lo = make_float4(acc[0 * NC + c], acc[1 * NC + c], acc[2 * NC + c], acc[3 * NC + c]);
-    const float4 hi = make_float4(acc[4 * NC + c], acc[5 * NC + c], acc[6 * NC + c], acc[7 * NC + c]);
+    const float4 lo = make_float4(acc[0 * NP + c], acc[1 * NP + c], acc[2 * NP + c], acc[3 * NP + c]);
+    const float4 hi = make_float4(acc[4 * NP + c], acc[5 * NP + c], acc[6 * NP + c], acc[7 * NP + c]);
     float4* dst = Acc + 2 * ((size_t)gy * Wd + gx);
     if (lo.x != 0.f || lo.y != 0.f || lo.z != 0.f || lo.w != 0.f) atomicAdd(dst, lo);
     if (hi.x != 0.f || hi.y != 0.f || hi.z != 0.f || hi.w != 0.f) atomicAdd(dst + 1, hi);
   }
 }
 
-template <int W>
+template <int W, int FORM>
+__global__ void __launch_bounds__(256) k_grid(
+    const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
+    const float4* __restrict__ rec, const float2* __restrict__ vin, const float* __restrict__ cb, int use_scale,
+    int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
+  constexpr int NP = grid_plane<W>();
+  extern __shared__ float4 smg[];
+  float4* x4 = smg;                              // kGridItem x 2: mixed, scaled channels of each row
+  float* wts = reinterpret_cast<float*>(smg + 2 * kGridItem);   // weights (layout by FORM)
+  float* acc = wts + grid_wts_floats<W, FORM>(); // 8 planes of NP floats
+  const GridItem it = items[blockIdx.x];
+  for (int i = threadIdx.x; i < 8 * NP; i += blockDim.x) acc[i] = 0.f;
+  const int nv = it.vend - it.vstart;
+  const float4* v4 = reinterpret_cast<const float4*>(vin);
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const int idx = it.vstart + j;
+    grid_stage_row<W, FORM>(j, rec[idx], v4[2 * (size_t)idx], v4[2 * (size_t)idx + 1],
+                            use_scale ? cb[vblk[idx]] : 1.0f, beta, x4, wts);
+  }
+  if (FORM == 3 && threadIdx.x < 8) {
+    // Spare rows after the item: finite (zero) operands for the last k-step of its last chunk.
+    const int j = nv + threadIdx.x;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < kGridItem) x4[2 * j] = x4[2 * j + 1] = z;
+    float4* yb = reinterpret_cast<float4*>(wts) + 2 * j;
+    float4* xb = reinterpret_cast<float4*>(wts + 8 * kGridRows3) + 2 * j;
+    yb[0] = yb[1] = xb[0] = xb[1] = z;
+  }
+  __syncthreads();
+  grid_chunks<W, FORM>(chunks + it.cstart, it.cend - it.cstart, x4, wts, acc);
+  __syncthreads();
+  grid_flush<W>(acc, it.ty, it.tx, Wd, full, K, Acc);
+}
+
+template <int W, int FORM>
 static constexpr size_t grid_smem() {
   return (size_t)2 * kGridItem * sizeof(float4) +
-         (size_t)(8 * (kGridTile + W - 1) * (kGridTile + W - 1) + 2 * W * kGridV) * sizeof(float);
+         (size_t)(grid_wts_floats<W, FORM>() + 8 * grid_plane<W>()) * sizeof(float);
 }
 
 // Hermitian symmetrisation + inverse column FFTs for the column pair (kx, -kx).
@@ -680,10 +834,13 @@ cudaError_t configure_nufft_kernels() {
   if ((e = set_smem((const void*)k_adj_rows, sm1)) != cudaSuccess) return e;
   const void* grids[] = {(const void*)k_grid<5, 0>, (const void*)k_grid<7, 0>, (const void*)k_grid<9, 0>,
                          (const void*)k_grid<5, 1>, (const void*)k_grid<7, 1>, (const void*)k_grid<9, 1>,
-                         (const void*)k_grid<5, 2>, (const void*)k_grid<7, 2>};
-  const size_t grid_bytes[] = {grid_smem<5>(), grid_smem<7>(), grid_smem<9>()};
-  for (int i = 0; i < 8; ++i)
-    if ((e = set_smem(grids[i], grid_bytes[i < 6 ? i % 3 : i - 6])) != cudaSuccess) return e;
+                         (const void*)k_grid<5, 2>, (const void*)k_grid<7, 2>, (const void*)k_grid<5, 3>,
+                         (const void*)k_grid<7, 3>};
+  const size_t grid_bytes[] = {grid_smem<5, 0>(), grid_smem<7, 0>(), grid_smem<9, 0>(), grid_smem<5, 1>(),
+                               grid_smem<7, 1>(), grid_smem<9, 1>(), grid_smem<5, 2>(), grid_smem<7, 2>(),
+                               grid_smem<5, 3>(), grid_smem<7, 3>()};
+  for (int i = 0; i < 10; ++i)
+    if ((e = set_smem(grids[i], grid_bytes[i])) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
   const void* degrids[] = {(const void*)k_degrid<5, false>, (const void*)k_degrid<7, false>,
                            (const void*)k_degrid<9, false>, (const void*)k_degrid<5, true>,
@@ -734,13 +891,23 @@ cudaError_t block_scales(Handle* h) {
   return cudaGetLastError();
 }
 
+template <int W, int FORM>
+static void launch_grid_form(Handle* h, const float2* in, int use_scale) {
+  const GridGeom& g = h->g;
+  k_grid<W, FORM><<<h->nitems, 256, grid_smem<W, FORM>(), h->stream>>>(
+      h->items, h->gchunks, h->vblk, h->rec, in, h->cb, use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
+}
+
 template <int W>
 static void launch_grid(Handle* h, const float2* in, int use_scale) {
-  const GridGeom& g = h->g;
-  const int form = (h->tune[PS_TUNE_GRID] == 2 && 4 * W > 32) ? 0 : h->tune[PS_TUNE_GRID];   // W = 9: no FORM 2
-  auto kern = form == 1 ? k_grid<W, 1> : (form == 2 ? k_grid<W, (4 * W <= 32 ? 2 : 0)> : k_grid<W, 0>);
-  kern<<<h->nitems, 256, grid_smem<W>(), h->stream>>>(h->items, h->gchunks, h->vblk, h->rec, in, h->cb,
-                                                            use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
+  // FORM 2 needs 4 W <= 32 lanes and FORM 3 8 taps per row: W = 9 runs FORM 0 for both.
+  constexpr bool narrow = W <= 8;
+  switch (h->tune[PS_TUNE_GRID]) {
+    case 1: launch_grid_form<W, 1>(h, in, use_scale); break;
+    case 2: launch_grid_form<W, narrow ? 2 : 0>(h, in, use_scale); break;
+    case 3: launch_grid_form<W, narrow ? 3 : 0>(h, in, use_scale); break;
+    default: launch_grid_form<W, 0>(h, in, use_scale); break;
+  }
 }
 
 cudaError_t nufft_grid(Handle* h, const float2* in, int use_scale) {

@@ -63,6 +63,27 @@ def test_phi_adjoint_on_sampled_pixels(big):
     assert _rel(got, ref) <= 1e-5
 
 
+def test_phi_adjoint_every_gridding_choice(big):
+    """Every gridding launch choice at full size on sampled pixels; the whole maps of all
+    choices agree within the FP32 tolerance of the atomics' order."""
+    s, uv, w, Y = big["s"], big["uv"], big["w"], big["Y"]
+    pix = np.stack([big["rng"].integers(0, WL.n, 10), big["rng"].integers(0, WL.n, 10)], axis=1)
+    ref = meas.phi_adjoint_at(Y.astype(np.complex128), uv, w.astype(np.float64), WL.n, pix)
+    saved = B.ps_get_tuning(s.h)
+    maps = []
+    try:
+        for choice in range(4):
+            B.ps_set_tuning(s.h, saved[:2] + [choice] + saved[3:])
+            img = np.empty((4, WL.n, WL.n), np.float32)
+            B.ps_apply_phi_adjoint(s.h, Y, img)
+            assert _rel(img[:, pix[:, 0], pix[:, 1]], ref) <= 1e-5, choice
+            maps.append(img)
+    finally:
+        B.ps_set_tuning(s.h, saved)
+    for choice, img in enumerate(maps[1:], 1):
+        assert _rel(img, maps[0]) <= 1e-6, choice
+
+
 def test_sara_transforms_full_maps(big):
     s = big["s"]
     S = big["truth"]

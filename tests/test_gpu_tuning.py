@@ -42,7 +42,7 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
     Yr = (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))).astype(np.complex64)
     ref_adj = meas.phi_adjoint(Yr.astype(np.complex128), pb["uv"], pb["w"].astype(np.float64), n)
     with _solver(pb, n, levels) as s:
-        for syn, deg, grd, ana in itertools.product(range(2), range(2), range(3), range(2)):
+        for syn, deg, grd, ana in itertools.product(range(2), range(2), range(4), range(2)):
             B.ps_set_tuning(s.h, [syn, deg, grd, ana])
             assert B.ps_get_tuning(s.h) == [syn, deg, grd, ana]
             Sg = np.empty((4, n, n), np.float32)
@@ -63,7 +63,7 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
 def test_set_tuning_rejects_unknown_choices():
     pb = make_problem(32, 500, 2, 1, seed=13)
     with _solver(pb, 32, 2) as s:
-        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 3, 0], [0, 0, 0, 2]):
+        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 4, 0], [0, 0, 0, 2]):
             with pytest.raises(B.PolsaraError) as e:
                 B.ps_set_tuning(s.h, bad)
             assert e.value.status == B.PS_EINVAL
