@@ -93,6 +93,7 @@ static void free_vis(Handle* h) {
   dfree(h, h->items, (size_t)h->nitems);
   dfree(h, h->gchunks, (size_t)h->ngchunks);
   dfree(h, h->vblk, M);
+  dfree(h, h->wrow, 16 * M);
   const size_t Wd = h->g.Wd;
   dfree(h, h->T1, (size_t)h->n * Wd);
   dfree(h, h->G, Wd * Wd);
@@ -242,7 +243,7 @@ int64_t ps_estimate_bytes(int32_t n, int32_t levels, int64_t M) {
   if (n < 16 || n > 2048 || !is_pow2(n) || levels < 1 || (n % (1 << levels)) != 0 || M < 0) return 0;
   const int64_t N = (int64_t)n * n, K = 2 * (int64_t)n;
   const int64_t img = (28 + 72 + 16) * N * 4 + (8 * (int64_t)sweep_blocks_host((int)N) + 1024) * 8;
-  const int64_t vis = M * (3 * 32 + 16 + 4) + (M / ps::kChunk + 64) * 24;
+  const int64_t vis = M * (3 * 32 + 16 + 4 + 64) + (M / ps::kChunk + 64) * 24;
   const int64_t grid = 2 * (int64_t)n * K * 16 + 48 * K * K + K * 12 + (int64_t)n * 4;
   return img + vis + grid;
 }
@@ -575,7 +576,8 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
             dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess && dalloc(h, &h->vblk, (size_t)M) == cudaSuccess &&
             dalloc(h, &h->T1, (size_t)h->n * Wd) == cudaSuccess && dalloc(h, &h->G, Wd * Wd) == cudaSuccess &&
             dalloc(h, &h->Acc, 2 * Wd * Wd) == cudaSuccess && dalloc(h, &h->T2, (size_t)h->n * Wd) == cudaSuccess &&
-            dalloc(h, &h->tw, (size_t)g.K) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess;
+            dalloc(h, &h->tw, (size_t)g.K) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess &&
+            (g.W > 8 || dalloc(h, &h->wrow, 16 * (size_t)M) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
     free_vis(h);
@@ -603,6 +605,7 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
     CK(h, cudaMemcpyAsync(h->items, items.data(), items.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->gchunks, gchunks.data(), gchunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->vblk, vblk.data(), vblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, ps::nufft_row_weights(h));
     // Measurements into sorted order.
     ps_status st = stage_in(h, vis, 4 * (size_t)M * sizeof(float2), device_ptrs, h->vtmp);
     if (st != PS_OK) return st;

@@ -86,6 +86,8 @@ struct Handle {
   GridItem *items = nullptr;       // gridding work items
   int32_t *gchunks = nullptr;      // packed (start, count, ly, lx) of same-cell chunks
   uint16_t *vblk = nullptr;        // l2 block of each stored row
+  float *wrow = nullptr;           // W <= 8: kernel weights of each stored row, 8 y-taps (M x 8)
+                                   // then 8 x-taps (M x 8), zero past W
   std::vector<double> eps_host;
   double psf_peak = 0.0;      // 2 sum w_m^2: peak of the Stokes-I PSF
   float *tmp36 = nullptr;     // 36N scratch for operator calls (allocated on first use)
@@ -126,6 +128,7 @@ cudaError_t upload_filters(const double h[kDb][kMaxTaps], cudaStream_t stream);
 cudaError_t nufft_forward_grid(Handle* h, const float* X);                 // X (4 planes) -> G
 cudaError_t nufft_degrid(Handle* h, int mode, float2* out);                // G -> visibilities
 cudaError_t nufft_grid(Handle* h, const float2* in, int use_block_scale);  // visibilities -> Acc
+cudaError_t nufft_row_weights(Handle* h);                                   // rec -> wrow (W <= 8)
 cudaError_t nufft_adjoint_image(Handle* h, float* out);                    // Acc -> 4 planes
 cudaError_t block_scales(Handle* h);                                        // chunk partials -> c_b
 

@@ -469,9 +469,9 @@ __host__ __device__ constexpr int grid_wts_floats() {
 }
 
 // Step 1 for one visibility j of a work item: row record r (fx, fy, w), its correlations
-// b0 = (RR, RL), b1 = (LR, LL) and its block scale. The weights go to wts: FORM 0-2 as W
-// x-planes then W y-planes of stride kGridV; FORM 3 row-major, 8 y-weights per row
-// (zero past W) for kGridRows3 rows, then 8 x-weights per row likewise.
+// b0 = (RR, RL), b1 = (LR, LL) and its block scale. FORM 0-2 evaluate its weights into
+// wts as W x-planes then W y-planes of stride kGridV; FORM 3 copies them instead (8
+// y-weights per row for kGridRows3 rows, then 8 x-weights per row, zero past W).
 template <int W, int FORM>
 __device__ __forceinline__ void grid_stage_row(int j, float4 r, float4 b0, float4 b1, float blk_scale, float beta,
                                                float4* __restrict__ x4, float* __restrict__ wts) {
@@ -482,23 +482,12 @@ __device__ __forceinline__ void grid_stage_row(int j, float4 r, float4 b0, float
   // x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL).
   x4[2 * j] = make_float4(sc * (b0.x + b1.z), sc * (b0.y + b1.w), sc * (b0.x - b1.z), sc * (b0.y - b1.w));
   x4[2 * j + 1] = make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
-  float wx[W], wy[W];
-  es_weights<W>(fx, beta, wx);
-  es_weights<W>(fy, beta, wy);
   if (FORM == 3) {
-    static_assert(FORM != 3 || W <= 8, "row-major weights hold 8 taps");
-    float t[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) t[k] = k < W ? wy[k] : 0.f;
-    float4* yb = reinterpret_cast<float4*>(wts) + 2 * j;
-    yb[0] = make_float4(t[0], t[1], t[2], t[3]);
-    yb[1] = make_float4(t[4], t[5], t[6], t[7]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) t[k] = k < W ? wx[k] : 0.f;
-    float4* xb = reinterpret_cast<float4*>(wts + 8 * kGridRows3) + 2 * j;
-    xb[0] = make_float4(t[0], t[1], t[2], t[3]);
-    xb[1] = make_float4(t[4], t[5], t[6], t[7]);
+    // Weights arrive by bulk copies from the per-row table (k_row_weights).
   } else {
+    float wx[W], wy[W];
+    es_weights<W>(fx, beta, wx);
+    es_weights<W>(fy, beta, wy);
     float* wxs = wts;
     float* wys = wts + W * kGridV;
 #pragma unroll
@@ -716,12 +705,17 @@ __device__ __forceinline__ void grid_flush(const float* __restrict__ acc, int ty
   }
 }
 
+constexpr int kGridThreads = 256;   // threads of a gridding CTA
+static_assert(kGridItem % kGridThreads == 0, "whole rows per thread");
+
 template <int W, int FORM>
-__global__ void __launch_bounds__(256) k_grid(
+__global__ void __launch_bounds__(kGridThreads) k_grid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const uint16_t* __restrict__ vblk,
     const float4* __restrict__ rec, const float2* __restrict__ vin, const float* __restrict__ cb, int use_scale,
-    int Wd, int full, int K, float beta, float4* __restrict__ Acc) {
+    int Wd, int full, int K, float beta, const float* __restrict__ wrow, int M, float4* __restrict__ Acc,
+    int* __restrict__ err) {
   constexpr int NP = grid_plane<W>();
+  __shared__ uint64_t wbar;                      // FORM 3: completion of the weight copies
   extern __shared__ float4 smg[];
   float4* x4 = smg;                              // kGridItem x 2: mixed, scaled channels of each row
   float* wts = reinterpret_cast<float*>(smg + 2 * kGridItem);   // weights (layout by FORM)
@@ -729,11 +723,30 @@ __global__ void __launch_bounds__(256) k_grid(
   const GridItem it = items[blockIdx.x];
   for (int i = threadIdx.x; i < 8 * NP; i += blockDim.x) acc[i] = 0.f;
   const int nv = it.vend - it.vstart;
+  if (FORM == 3 && threadIdx.x == 0) {
+    mbar_init(&wbar, 1);
+    mbar_expect_tx(&wbar, (uint32_t)nv * 64u);
+    bulk_g2s(wts, wrow + 8 * (size_t)it.vstart, (uint32_t)nv * 32u, &wbar);
+    bulk_g2s(wts + 8 * kGridRows3, wrow + 8 * ((size_t)M + it.vstart), (uint32_t)nv * 32u, &wbar);
+  }
   const float4* v4 = reinterpret_cast<const float4*>(vin);
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    const int idx = it.vstart + j;
-    grid_stage_row<W, FORM>(j, rec[idx], v4[2 * (size_t)idx], v4[2 * (size_t)idx + 1],
-                            use_scale ? cb[vblk[idx]] : 1.0f, beta, x4, wts);
+  // Every global load of this thread's rows is issued before the first is used.
+  constexpr int RPT = kGridItem / kGridThreads;   // rows per thread
+  float4 r[RPT], b0[RPT], b1[RPT];
+  int blk[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int j = threadIdx.x + q * kGridThreads;
+    const size_t idx = (size_t)it.vstart + (j < nv ? j : 0);
+    r[q] = rec[idx];
+    b0[q] = v4[2 * idx];
+    b1[q] = v4[2 * idx + 1];
+    blk[q] = use_scale ? vblk[idx] : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int j = threadIdx.x + q * kGridThreads;
+    if (j < nv) grid_stage_row<W, FORM>(j, r[q], b0[q], b1[q], use_scale ? cb[blk[q]] : 1.0f, beta, x4, wts);
   }
   if (FORM == 3 && threadIdx.x < 8) {
     // Spare rows after the item: finite (zero) operands for the last k-step of its last chunk.
@@ -745,6 +758,16 @@ __global__ void __launch_bounds__(256) k_grid(
     yb[0] = yb[1] = xb[0] = xb[1] = z;
   }
   __syncthreads();
+  if (FORM == 3) {
+    const bool ok = mbar_wait(&wbar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        (void)mbar_wait(&wbar, 0);
+      }
+      return;
+    }
+  }
   grid_chunks<W, FORM>(chunks + it.cstart, it.cend - it.cstart, x4, wts, acc);
   __syncthreads();
   grid_flush<W>(acc, it.ty, it.tx, Wd, full, K, Acc);
@@ -891,11 +914,46 @@ cudaError_t block_scales(Handle* h) {
   return cudaGetLastError();
 }
 
+// Kernel weights of every stored row, computed once per set of measurements (the rows'
+// fractional offsets do not change): y-taps in the first M x 8 floats, x-taps after.
+template <int W>
+__global__ void k_row_weights(const float4* __restrict__ rec, int M, float beta, float* __restrict__ wrow) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  float fx, fy, w;
+  int cx, cy;
+  unpack_rec(rec[m], fx, fy, w, cx, cy);
+  float wx[W], wy[W], t[8];
+  es_weights<W>(fx, beta, wx);
+  es_weights<W>(fy, beta, wy);
+  float4* py = reinterpret_cast<float4*>(wrow) + 2 * (size_t)m;
+  float4* px = reinterpret_cast<float4*>(wrow + 8 * (size_t)M) + 2 * (size_t)m;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t[k] = k < W ? wy[k] : 0.f;
+  py[0] = make_float4(t[0], t[1], t[2], t[3]);
+  py[1] = make_float4(t[4], t[5], t[6], t[7]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t[k] = k < W ? wx[k] : 0.f;
+  px[0] = make_float4(t[0], t[1], t[2], t[3]);
+  px[1] = make_float4(t[4], t[5], t[6], t[7]);
+}
+
+cudaError_t nufft_row_weights(Handle* h) {
+  if (!h->wrow || h->M == 0) return cudaSuccess;
+  const int blocks = (h->M + 255) / 256;
+  if (h->g.W == 5)
+    k_row_weights<5><<<blocks, 256, 0, h->stream>>>(h->rec, h->M, h->g.beta, h->wrow);
+  else
+    k_row_weights<7><<<blocks, 256, 0, h->stream>>>(h->rec, h->M, h->g.beta, h->wrow);
+  return cudaGetLastError();
+}
+
 template <int W, int FORM>
 static void launch_grid_form(Handle* h, const float2* in, int use_scale) {
   const GridGeom& g = h->g;
-  k_grid<W, FORM><<<h->nitems, 256, grid_smem<W, FORM>(), h->stream>>>(
-      h->items, h->gchunks, h->vblk, h->rec, in, h->cb, use_scale, g.Wd, g.full, g.K, g.beta, h->Acc);
+  k_grid<W, FORM><<<h->nitems, kGridThreads, grid_smem<W, FORM>(), h->stream>>>(
+      h->items, h->gchunks, h->vblk, h->rec, in, h->cb, use_scale, g.Wd, g.full, g.K, g.beta, h->wrow, h->M, h->Acc,
+      h->dev_flags);
 }
 
 template <int W>

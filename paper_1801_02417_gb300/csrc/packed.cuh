@@ -1,7 +1,11 @@
-// Packed FP32x2 arithmetic for the CUDA kernels (sm_100 family and later): two
-// FP32 lanes in one 64-bit register pair, one fma.rn.f32x2 for both. Each lane is
-// rounded exactly like a separate fmaf.
+// Device helpers shared by the CUDA kernels (sm_100 family and later).
+// Packed FP32x2 arithmetic: two FP32 lanes in one 64-bit register pair, one
+// fma.rn.f32x2 for both; each lane is rounded exactly like a separate fmaf.
+// Bulk copies (cp.async.bulk, global to shared) completing on mbarriers, with
+// bounded waits.
 #pragma once
+
+#include <cstdint>
 
 #include <cuda_runtime.h>
 
@@ -25,4 +29,33 @@ __device__ __forceinline__ u64 fdup(float a) { return f2pack(a, a); }
 // Ordering of generic-proxy shared-memory accesses before later bulk (async-proxy) copies.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// ---- bulk-copy (TMA) and mbarrier helpers (inline PTX, sm_90+).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Bounded wait on phase `parity`: false (and the caller raises the error flag) if it never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 }  // namespace ps
