@@ -202,59 +202,41 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;  // valid in thread 0
 }
 
-// One row of a degridding work item (all 32 lanes of the warp call it together:
-// the block-sum combination is warp-collective). Inactive lanes add nothing.
-template <int W>
-__device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& it, const float4* __restrict__ rec,
-                                           const float4* Gp, const float4* Gn, int off, int full, int K, float beta,
-                                           int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
-                                           const float* __restrict__ cb, float inv_rho2,
-                                           const uint16_t* __restrict__ vblk, bool reduce, bool private_bins,
-                                           double* bsum,
-                                           float2* __restrict__ out) {
-  constexpr int TS = kGridTile;
-  constexpr int SS = TS + W - 1;
+// FP32 -> TF32 hi part (round to nearest, ties away) and the TF32 rounding of the
+// remainder; hi + lo carries the operand to about 2^-21 of its value.
+__device__ __forceinline__ void tf32_split(float a, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(a));
+  const float r = a - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+// The same split with integer rounding of the hi part (round half up on the magnitude) and
+// the remainder left for the tensor core to truncate to TF32: |a - hi - lo_tf32| <= 2^-21 |a|.
+__device__ __forceinline__ void tf32_split_fast(float a, uint32_t& hi, uint32_t& lo) {
+  hi = (__float_as_uint(a) + 0x1000u) & 0xFFFFE000u;
+  lo = __float_as_uint(a - __uint_as_float(hi));
+}
+// d += A B for one m16n8k8 TF32 tile: A (16 x 8) fragment a[4], B (8 x 8) fragment b[2].
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Second half of a degridding row m (all 32 lanes of the warp call it together: the
+// block-sum combination is warp-collective; inactive lanes add nothing): from the
+// interpolated packed spectra sp (at +u) and sn (at -u) to the row's visibilities
+// (or residuals), and its term of the per-block sums.
+__device__ __forceinline__ void degrid_finish(int m, bool active, float w, float4 sp, float4 sn, int mode,
+                                              float2* __restrict__ R, const float2* __restrict__ Yv,
+                                              const float* __restrict__ cb, float inv_rho2,
+                                              const uint16_t* __restrict__ vblk, bool reduce, bool private_bins,
+                                              double* bsum, float2* __restrict__ out) {
   float4* R4 = reinterpret_cast<float4*>(R);
   const float4* Y4 = reinterpret_cast<const float4*>(Yv);
   int blk = -1;
   float e2 = 0.f;
   if (active) {
-    float fx, fy, w;
-    int cx, cy;
-    unpack_rec(rec[m], fx, fy, w, cx, cy);
-    float wx[W], wy[W];
-    es_weights<W>(fx, beta, wx);
-    es_weights<W>(fy, beta, wy);
-    // Local centre within the tile (tap j of +u at local j + lc; of -u at local (TS-1-lc) + j).
-    const int lcy = gidx(cy, off, full, K) - it.ty * TS, lcx = gidx(cx, off, full, K) - it.tx * TS;
-    const float4* gp = Gp + lcy * SS + lcx;
-    const float4* gn = Gn + (TS - 1 - lcy) * SS + (TS - 1 - lcx);
-    // Packed FP32x2: channels (x, y) and (z, w) of each float4 cell in one FMA each.
-    u64 sp0 = 0ull, sp1 = 0ull, sn0 = 0ull, sn1 = 0ull;
-#pragma unroll
-    for (int jy = 0; jy < W; ++jy) {
-      u64 ap0 = 0ull, ap1 = 0ull, an0 = 0ull, an1 = 0ull;
-#pragma unroll
-      for (int jx = 0; jx < W; ++jx) {
-        const ulonglong2 vp = *reinterpret_cast<const ulonglong2*>(gp + jy * SS + jx);
-        const ulonglong2 vn = *reinterpret_cast<const ulonglong2*>(gn + jy * SS + jx);
-        const u64 kp = fdup(wx[jx]), kn = fdup(wx[W - 1 - jx]);
-        ap0 = ffma2(kp, vp.x, ap0);
-        ap1 = ffma2(kp, vp.y, ap1);
-        an0 = ffma2(kn, vn.x, an0);
-        an1 = ffma2(kn, vn.y, an1);
-      }
-      const u64 ky = fdup(wy[jy]), kny = fdup(wy[W - 1 - jy]);
-      sp0 = ffma2(ky, ap0, sp0);
-      sp1 = ffma2(ky, ap1, sp1);
-      sn0 = ffma2(kny, an0, sn0);
-      sn1 = ffma2(kny, an1, sn1);
-    }
-    float4 sp, sn;
-    f2unpack(sp0, sp.x, sp.y);
-    f2unpack(sp1, sp.z, sp.w);
-    f2unpack(sn0, sn.x, sn.y);
-    f2unpack(sn1, sn.z, sn.w);
     // G1 = F(I + iQ), G2 = F(U + iV); F(I) = (G1(u) + conj G1(-u))/2, F(Q) = (G1(u) - conj G1(-u))/(2i).
     const float FIr = 0.5f * (sp.x + sn.x), FIi = 0.5f * (sp.y - sn.y);
     const float FQr = 0.5f * (sp.y + sn.y), FQi = -0.5f * (sp.x - sn.x);
@@ -303,6 +285,60 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
   }
 }
 
+// One row of a degridding work item on the CUDA cores: the 2 W^2 taps read from the
+// staged spectrum cells, then degrid_finish (warp-collective, like it).
+template <int W>
+__device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& it, const float4* __restrict__ rec,
+                                           const float4* Gp, const float4* Gn, int off, int full, int K, float beta,
+                                           int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
+                                           const float* __restrict__ cb, float inv_rho2,
+                                           const uint16_t* __restrict__ vblk, bool reduce, bool private_bins,
+                                           double* bsum,
+                                           float2* __restrict__ out) {
+  constexpr int TS = kGridTile;
+  constexpr int SS = TS + W - 1;
+  float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
+  float w = 0.f;
+  if (active) {
+    float fx, fy;
+    int cx, cy;
+    unpack_rec(rec[m], fx, fy, w, cx, cy);
+    float wx[W], wy[W];
+    es_weights<W>(fx, beta, wx);
+    es_weights<W>(fy, beta, wy);
+    // Local centre within the tile (tap j of +u at local j + lc; of -u at local (TS-1-lc) + j).
+    const int lcy = gidx(cy, off, full, K) - it.ty * TS, lcx = gidx(cx, off, full, K) - it.tx * TS;
+    const float4* gp = Gp + lcy * SS + lcx;
+    const float4* gn = Gn + (TS - 1 - lcy) * SS + (TS - 1 - lcx);
+    // Packed FP32x2: channels (x, y) and (z, w) of each float4 cell in one FMA each.
+    u64 sp0 = 0ull, sp1 = 0ull, sn0 = 0ull, sn1 = 0ull;
+#pragma unroll
+    for (int jy = 0; jy < W; ++jy) {
+      u64 ap0 = 0ull, ap1 = 0ull, an0 = 0ull, an1 = 0ull;
+#pragma unroll
+      for (int jx = 0; jx < W; ++jx) {
+        const ulonglong2 vp = *reinterpret_cast<const ulonglong2*>(gp + jy * SS + jx);
+        const ulonglong2 vn = *reinterpret_cast<const ulonglong2*>(gn + jy * SS + jx);
+        const u64 kp = fdup(wx[jx]), kn = fdup(wx[W - 1 - jx]);
+        ap0 = ffma2(kp, vp.x, ap0);
+        ap1 = ffma2(kp, vp.y, ap1);
+        an0 = ffma2(kn, vn.x, an0);
+        an1 = ffma2(kn, vn.y, an1);
+      }
+      const u64 ky = fdup(wy[jy]), kny = fdup(wy[W - 1 - jy]);
+      sp0 = ffma2(ky, ap0, sp0);
+      sp1 = ffma2(ky, ap1, sp1);
+      sn0 = ffma2(kny, an0, sn0);
+      sn1 = ffma2(kny, an1, sn1);
+    }
+    f2unpack(sp0, sp.x, sp.y);
+    f2unpack(sp1, sp.z, sp.w);
+    f2unpack(sn0, sn.x, sn.y);
+    f2unpack(sn1, sn.z, sn.w);
+  }
+  degrid_finish(m, active, w, sp, sn, mode, R, Yv, cb, inv_rho2, vblk, reduce, private_bins, bsum, out);
+}
+
 // Interpolate the packed spectra at +u and -u, unpack the four Stokes spectra,
 // mix into RR, RL, LR, LL (Section 2.1) and weight by w_m. One CTA per gridding
 // work item (rows whose tap centres lie in one kGridTile^2 tile): the spectrum
@@ -313,7 +349,9 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
 // then in FP64 through per-warp shared bins (up to kWarpBins blocks; shared FP64
 // atomics beyond) and one global FP64 atomic per block and CTA (block_sum, cleared
 // by the caller).
-template <int W, bool CHUNK>
+// FORM 0: one row per thread over the item; 1: one same-cell chunk per warp (broadcast
+// stencil reads).
+template <int W, int FORM>
 __global__ void __launch_bounds__(256) k_degrid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const float4* __restrict__ rec, const float4* __restrict__ G, int Wd,
     int off, int full, int K, float beta, int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
@@ -352,7 +390,7 @@ __global__ void __launch_bounds__(256) k_degrid(
     Gn[i] = vn;
   }
   __syncthreads();
-  if (CHUNK) {
+  if (FORM == 1) {
     // One same-cell chunk (<= 32 rows) per warp: every lane reads the same stencil
     // cells, so the shared-memory gathers are broadcasts.
     const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -436,27 +474,6 @@ constexpr int kGridV = kGridItem + 2;
 template <int W>
 __host__ __device__ constexpr int grid_plane() {
   return (kGridTile + W - 1) * (kGridTile + W - 1) + 1;
-}
-
-// FP32 -> TF32 hi part (round to nearest, ties away) and the TF32 rounding of the
-// remainder; hi + lo carries the operand to about 2^-21 of its value.
-__device__ __forceinline__ void tf32_split(float a, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(a));
-  const float r = a - __uint_as_float(hi);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
-}
-// The same split with integer rounding of the hi part (round half up on the magnitude) and
-// the remainder left for the tensor core to truncate to TF32: |a - hi - lo_tf32| <= 2^-21 |a|.
-__device__ __forceinline__ void tf32_split_fast(float a, uint32_t& hi, uint32_t& lo) {
-  hi = (__float_as_uint(a) + 0x1000u) & 0xFFFFE000u;
-  lo = __float_as_uint(a - __uint_as_float(hi));
-}
-// d += A B for one m16n8k8 TF32 tile: A (16 x 8) fragment a[4], B (8 x 8) fragment b[2].
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 // FORM 3 keeps 8 y-weights and 8 x-weights per row for kGridItem rows plus 8 spare
@@ -865,9 +882,8 @@ cudaError_t configure_nufft_kernels() {
   for (int i = 0; i < 10; ++i)
     if ((e = set_smem(grids[i], grid_bytes[i])) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
-  const void* degrids[] = {(const void*)k_degrid<5, false>, (const void*)k_degrid<7, false>,
-                           (const void*)k_degrid<9, false>, (const void*)k_degrid<5, true>,
-                           (const void*)k_degrid<7, true>,  (const void*)k_degrid<9, true>};
+  const void* degrids[] = {(const void*)k_degrid<5, 0>, (const void*)k_degrid<7, 0>, (const void*)k_degrid<9, 0>,
+                           (const void*)k_degrid<5, 1>, (const void*)k_degrid<7, 1>, (const void*)k_degrid<9, 1>};
   const size_t degrid_smem[] = {degrid_smem_tiles<5>(), degrid_smem_tiles<7>(), degrid_smem_tiles<9>()};
   for (int i = 0; i < 6; ++i)
     if ((e = set_smem(degrids[i], degrid_smem[i % 3] + 2048 * sizeof(double))) != cudaSuccess) return e;
@@ -887,7 +903,7 @@ static void launch_degrid(Handle* h, int mode, float2* out) {
   const GridGeom& g = h->g;
   const int nbins = h->nblocks <= kWarpBins ? kWarpBins * 8 : h->nblocks;   // 8 warps of 256 threads
   const size_t sm = degrid_smem_tiles<W>() + (size_t)nbins * sizeof(double);
-  auto kern = h->tune[PS_TUNE_DEGRID] ? k_degrid<W, true> : k_degrid<W, false>;
+  auto kern = h->tune[PS_TUNE_DEGRID] == 1 ? k_degrid<W, 1> : k_degrid<W, 0>;
   kern<<<h->nitems, 256, sm, h->stream>>>(h->items, h->gchunks, h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode,
                                           h->R, h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->nblocks,
                                           h->block_sum, out);

@@ -63,6 +63,27 @@ def test_phi_adjoint_on_sampled_pixels(big):
     assert _rel(got, ref) <= 1e-5
 
 
+def test_phi_every_degridding_choice(big):
+    """Every degridding launch choice at full size on sampled rows; the whole outputs of
+    all choices agree within FP32 rounding."""
+    s, uv, w = big["s"], big["uv"], big["w"]
+    rows = np.sort(big["rng"].choice(WL.M, size=64, replace=False))
+    ref = meas.phi(big["truth"].astype(np.float64), uv[rows], w[rows].astype(np.float64))
+    saved = B.ps_get_tuning(s.h)
+    outs = []
+    try:
+        for choice in range(2):
+            B.ps_set_tuning(s.h, saved[:1] + [choice] + saved[2:])
+            out = np.empty((WL.M, 4), np.complex64)
+            B.ps_apply_phi(s.h, big["truth"], out)
+            assert _rel(out[rows], ref) <= 1e-5, choice
+            outs.append(out)
+    finally:
+        B.ps_set_tuning(s.h, saved)
+    for choice, out in enumerate(outs[1:], 1):
+        assert _rel(out, outs[0]) <= 1e-6, choice
+
+
 def test_phi_adjoint_every_gridding_choice(big):
     """Every gridding launch choice at full size on sampled pixels; the whole maps of all
     choices agree within the FP32 tolerance of the atomics' order."""

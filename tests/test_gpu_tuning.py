@@ -63,7 +63,7 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
 def test_set_tuning_rejects_unknown_choices():
     pb = make_problem(32, 500, 2, 1, seed=13)
     with _solver(pb, 32, 2) as s:
-        for bad in ([2, 0, 0, 0], [0, -1, 0, 0], [0, 0, 4, 0], [0, 0, 0, 2]):
+        for bad in ([2, 0, 0, 0], [0, 2, 0, 0], [0, 0, 4, 0], [0, 0, 0, 2]):
             with pytest.raises(B.PolsaraError) as e:
                 B.ps_set_tuning(s.h, bad)
             assert e.value.status == B.PS_EINVAL
@@ -100,10 +100,12 @@ def test_autotune_keeps_the_state_and_the_iteration():
         assert rel_err(sa, sb) <= 2e-5 * 5
 
 
-def test_persistent_analysis_iterations_match_oracle():
-    """The persistent analysis form inside the iteration (dual update with staged A and
-    gamma W, refilled buffers), forced on, against Algorithm 1 of the FP64 oracle from a
-    random state, at a size whose level 1 is tiled (the form's only use)."""
+@pytest.mark.parametrize("tuning", [[0, 0, 0, 1], [0, 1, 3, 0]])
+def test_forced_launch_choices_iterate_like_oracle(tuning):
+    """Forced launch choices inside the iteration against Algorithm 1 of the FP64 oracle
+    from a random state: [0, 0, 0, 1] the persistent analysis form (dual update with
+    staged A and gamma W, refilled buffers; level 1 is tiled at this size), [0, 1, 3, 0]
+    the chunk-per-warp degridding (residual, block sums) and tensor-core gridding forms."""
     from oracle import primal_dual as opd
     from paper_1801_02417_gb300 import inputs
     n, M, levels = 128, 1500, 3
@@ -121,7 +123,7 @@ def test_persistent_analysis_iterations_match_oracle():
     with s:
         s.set_measurements(pb["uv"], pb["Y"], pb["w"], pb["off"], pb["eps"])
         s.set_sara_weights(W, gamma)
-        B.ps_set_tuning(s.h, [0, 0, 0, 1])
+        B.ps_set_tuning(s.h, tuning)
         s.set_state(st32)
         s.pd_iterate(3)
         for _ in range(3):
