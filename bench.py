@@ -497,7 +497,7 @@ def run_own(args) -> None:
     total_bytes = sum(sbytes.values())
 
     # End to end through the C ABI with host buffers (pinned), as a user runs a solve:
-    # upload of the measurements (row sort, power iteration), then per step one
+    # upload of the measurements (row sort, operator-norm estimate), then per step one
     # iteration and a device->host read of its stopping metric (the per-map relative
     # change of Eq. stop_crit), and the Stokes maps read back once at the end.
     e2e = None
@@ -530,7 +530,7 @@ def run_own(args) -> None:
         tm = time.perf_counter() - t1
         e2e = {"value": ke / te, "unit": "iter/s", "h2d_bytes_per_step": int(h2d / ke),
                "d2h_bytes_per_step": int(8 * nparts + out_p.numel() * 4 / ke),
-               "note": "pinned host measurements uploaded once (row sort, power iteration), then per step one "
+               "note": "pinned host measurements uploaded once (row sort, operator-norm estimate), then per step one "
                        "iteration + read of its relative-change metric; Stokes maps read once at the end",
                "maps_every_step": {"value": km / tm, "unit": "iter/s", "d2h_bytes_per_step": int(out_p.numel() * 4)}}
 

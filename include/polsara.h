@@ -122,7 +122,7 @@ const char* ps_last_error(const ps_handle* h);
  *   block_offsets  nblocks+1 int64, increasing, [0] = 0, [nblocks] = M
  *   eps            nblocks float64 radii eps_b > 0 (e.g. the chi^2 bound of Section 5.1)
  *   device_ptrs    for uv, vis, weights (block_offsets and eps are host arrays)
- * Sorts the rows by interpolation tile, estimates ||phi||^2 by power iteration
+ * Sorts the rows by interpolation tile, estimates ||phi||^2 by Lanczos iterations
  * (FP64 reductions on the device), sets the default step sizes, and resets the
  * state to zero. */
 ps_status ps_set_measurements(ps_handle* h, int64_t M, const double* uv, const float* vis,
@@ -156,7 +156,7 @@ ps_status ps_get_stokes(ps_handle* h, float* out, int32_t device_ptrs);
 ps_status ps_get_state(ps_handle* h, const ps_state_view* view);
 ps_status ps_set_state(ps_handle* h, const ps_state_view* view);
 
-/* Step sizes and the power-iteration estimate of ||phi||_sp^2 (Section 4.3.3). */
+/* Step sizes and the Lanczos estimate of ||phi||_sp^2 (Section 4.3.3). */
 ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, double* rho3,
                         double* opnorm_sq);
 

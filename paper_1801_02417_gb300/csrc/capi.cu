@@ -399,7 +399,7 @@ static ps_status stage_in(Handle* h, const void* src, size_t bytes, int device_p
   return PS_OK;
 }
 
-static ps_status power_iteration(Handle* h);
+static ps_status opnorm_lanczos(Handle* h);
 }  // extern "C"
 
 static __global__ void k_fill(float* p, int n, float v) {
@@ -613,13 +613,47 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   }
   CK(h, cudaStreamSynchronize(h->stream));
   h->have_meas = true;
-  ps_status st = power_iteration(h);
+  ps_status st = opnorm_lanczos(h);
   if (st != PS_OK) return st;
   set_default_steps(h);
   return reset_state(h);
 }
 
-static ps_status power_iteration(Handle* h) {
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a and
+// off-diagonal b (|b| = |a| - 1), by bisection on the Sturm count.
+static double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const size_t k = a.size();
+  double lo = a[0], hi = a[0];
+  for (size_t i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto below = [&](double x) {   // number of eigenvalues < x
+    int cnt = 0;
+    double q = a[0] - x;
+    for (size_t i = 0;; ++i) {
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++cnt;
+      if (i + 1 == k) break;
+      q = a[i + 1] - x - b[i] * b[i] / q;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), 1e-300); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) >= (int)k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// ||phi||_sp^2, the step-size bound of Section 4.3.3, as the largest eigenvalue of
+// phi^dagger phi by Lanczos iterations (three-term recurrence, FP32 vectors, FP64
+// coefficients; the largest Ritz value rises monotonically to it). Stops when that
+// value changes by <= 1e-9 relative, or the Krylov space is invariant. Scratch: tmp4,
+// Xb and Adj (all cleared by the caller's reset of the state).
+static ps_status opnorm_lanczos(Handle* h) {
   h->opnorm_sq = 0.0;
   if (h->M == 0) return PS_OK;
   const size_t N4 = 4 * (size_t)h->N;
@@ -633,27 +667,41 @@ static ps_status power_iteration(Handle* h) {
   }
   const float inv = (float)(1.0 / std::sqrt(nrm));
   for (auto& v : x) v *= inv;
+  float *v = h->tmp4, *u = h->Xb, *w = h->Adj;   // current, previous and new Lanczos vectors
   // On the handle's (non-blocking) stream, so the iterations below are ordered after the copy.
-  CK(h, cudaMemcpyAsync(h->tmp4, x.data(), N4 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(v, x.data(), N4 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemsetAsync(u, 0, N4 * sizeof(float), h->stream));
   double* dres = h->red + (size_t)h->red_cap - 600;
-  double lam = 0.0;
-  for (int it = 0; it < 1000; ++it) {
-    CK(h, ps::nufft_forward_grid(h, h->tmp4));
+  std::vector<double> al, be;
+  double theta = 0.0, beta = 0.0;
+  for (int j = 0; j < 300; ++j) {
+    CK(h, ps::nufft_forward_grid(h, v));
     CK(h, ps::nufft_degrid(h, ps::DEG_APPLY, h->vtmp));
     CK(h, ps::nufft_grid(h, h->vtmp, 0));
-    CK(h, ps::nufft_adjoint_image(h, h->Adj));
-    CK(h, ps::reduce_dot(h, h->tmp4, h->Adj, N4, dres));
-    CK(h, ps::reduce_dot(h, h->Adj, h->Adj, N4, dres + 1));
-    CK(h, cudaMemcpyAsync(h->red_host, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, ps::nufft_adjoint_image(h, w));
+    CK(h, ps::reduce_dot(h, w, v, N4, dres));
+    CK(h, cudaMemcpyAsync(h->red_host, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    const double lam_new = h->red_host[0], ny = std::sqrt(h->red_host[1]);
-    if (!(ny > 0) || !std::isfinite(ny)) return fail(h, PS_ENONFINITE, "power iteration: zero or non-finite phi^dagger phi x");
-    CK(h, ps::scale_copy(h, h->Adj, h->tmp4, N4, 1.0 / ny));
-    const bool done = it > 4 && std::fabs(lam_new - lam) <= 1e-7 * lam_new;
-    lam = lam_new;
+    const double alpha = h->red_host[0];
+    if (!std::isfinite(alpha)) return fail(h, PS_ENONFINITE, "Lanczos: non-finite phi^dagger phi x");
+    CK(h, ps::lanczos_update(h, w, v, u, N4, alpha, beta));
+    CK(h, ps::reduce_dot(h, w, w, N4, dres + 1));
+    CK(h, cudaMemcpyAsync(h->red_host + 1, dres + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double beta_new = std::sqrt(h->red_host[1]);
+    if (!std::isfinite(beta_new)) return fail(h, PS_ENONFINITE, "Lanczos: non-finite phi^dagger phi x");
+    al.push_back(alpha);
+    const double theta_new = tridiag_max_eig(al, be);
+    if (!(theta_new > 0)) return fail(h, PS_ENONFINITE, "Lanczos: zero phi^dagger phi x");
+    const bool done = (j >= 4 && std::fabs(theta_new - theta) <= 1e-9 * theta_new) || beta_new <= 1e-12 * theta_new;
+    theta = theta_new;
     if (done) break;
+    be.push_back(beta_new);
+    CK(h, ps::scale_copy(h, w, u, N4, 1.0 / beta_new));   // the new vector over the previous one
+    std::swap(u, v);
+    beta = beta_new;
   }
-  h->opnorm_sq = lam;
+  h->opnorm_sq = theta;
   return PS_OK;
 }
 

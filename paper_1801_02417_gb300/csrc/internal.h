@@ -148,6 +148,8 @@ cudaError_t violation_count(Handle* h, const float* S, double zeta, double* dev_
 cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* dev_out);
 cudaError_t max_abs(Handle* h, const float* c, size_t len, double* dev_out);
 cudaError_t scale_copy(Handle* h, const float* x, float* y, size_t len, double s);
+cudaError_t lanczos_update(Handle* h, float* w, const float* v, const float* u, size_t len, double alpha,
+                           double beta);                                    // w -= alpha v + beta u
 cudaError_t gather_vis(Handle* h, const float2* user, float2* sorted);
 cudaError_t scatter_vis(Handle* h, const float2* sorted, float2* user);
 cudaError_t scale_vis(Handle* h, float2* v);   // v = c_b v per block (state readout)

@@ -363,6 +363,20 @@ cudaError_t scale_copy(Handle* h, const float* x, float* y, size_t len, double s
   return cudaGetLastError();
 }
 
+// Lanczos three-term recurrence: w = w - alpha v - beta u (FP32 vectors, FP64 coefficients).
+__global__ void k_lanczos_update(float* __restrict__ w, const float* __restrict__ v, const float* __restrict__ u,
+                                 size_t len, double alpha, double beta) {
+  const float a = (float)alpha, b = (float)beta;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    w[i] = fmaf(-b, u[i], fmaf(-a, v[i], w[i]));
+}
+
+cudaError_t lanczos_update(Handle* h, float* w, const float* v, const float* u, size_t len, double alpha,
+                           double beta) {
+  k_lanczos_update<<<1024, 256, 0, h->stream>>>(w, v, u, len, alpha, beta);
+  return cudaGetLastError();
+}
+
 // Visibility order changes: sorted row m holds caller row perm[m].
 __global__ void k_gather_vis(int M, const int32_t* __restrict__ perm, const float4* __restrict__ user,
                              float4* __restrict__ sorted) {
