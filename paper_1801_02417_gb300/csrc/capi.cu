@@ -19,6 +19,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -70,6 +71,50 @@ static void dfree(Handle* h, T*& p, size_t count) {
 }
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Host-side row preparation on several threads: f(t, begin, end) over contiguous parts
+// [begin, end) of [0, n), part t on thread t (part 0 on the caller). The partition
+// depends only on n and `parts`, so results that are combined part by part in order
+// do not depend on the machine.
+template <typename F>
+static void parallel_parts(int64_t n, int parts, F f) {
+  std::vector<std::thread> th;
+  for (int t = 1; t < parts; ++t) {
+    try {
+      th.emplace_back([&, t] { f(t, n * t / parts, n * (t + 1) / parts); });
+    } catch (...) {   // no thread to be had: this part runs on the caller
+      f(t, n * t / parts, n * (t + 1) / parts);
+    }
+  }
+  f(0, 0, n / parts);
+  for (auto& x : th) x.join();
+}
+static int host_parts(int64_t n) {
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int64_t by_size = std::max<int64_t>(1, n / 65536);
+  return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hc ? hc : 1), 16, by_size}));
+}
+
+// Stable counting sort of idx by key(i) in [0, nb) (parallel: per-part counts, then
+// each part scatters its rows in order after the rows of the earlier parts).
+template <typename K>
+static void counting_sort(const std::vector<int32_t>& idx, std::vector<int32_t>& out, int64_t nb, int parts, K key) {
+  const int64_t n = (int64_t)idx.size();
+  std::vector<std::vector<int64_t>> cnt(parts, std::vector<int64_t>(nb, 0));
+  parallel_parts(n, parts, [&](int t, int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) ++cnt[t][key(idx[i])];
+  });
+  int64_t run = 0;
+  for (int64_t k = 0; k < nb; ++k)
+    for (int t = 0; t < parts; ++t) {
+      const int64_t c = cnt[t][k];
+      cnt[t][k] = run;
+      run += c;
+    }
+  parallel_parts(n, parts, [&](int t, int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) out[cnt[t][key(idx[i])]++] = idx[i];
+  });
+}
 
 // Device arrays are read and written as float4: caller device pointers must be 16-byte aligned.
 static bool misaligned(const void* p, int device_ptrs) { return device_ptrs && p && ((uintptr_t)p & 15u) != 0; }
@@ -439,26 +484,27 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   free_vis(h);
   h->have_meas = false;
 
-  // Host copies of the measurement rows.
-  std::vector<double> uvh(2 * (size_t)M);
-  std::vector<float> wh(M, 1.0f);
-  if (M > 0) {
-    // Caller device pointers are read on the handle's stream (its order, not the legacy stream's).
-    CK(h, cudaMemcpyAsync(uvh.data(), uv, uvh.size() * sizeof(double),
-                          device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, h->stream));
-    if (weights)
-      CK(h, cudaMemcpyAsync(wh.data(), weights, wh.size() * sizeof(float),
-                            device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, h->stream));
+  // Host views of the measurement rows: caller host arrays are read in place, caller
+  // device arrays are copied on the handle's stream (its order, not the legacy stream's).
+  const int parts = host_parts(M);
+  std::vector<double> uv_copy;
+  std::vector<float> w_copy;
+  const double* uvh = uv;
+  const float* wsrc = weights;
+  if (M > 0 && device_ptrs) {
+    uv_copy.resize(2 * (size_t)M);
+    CK(h, cudaMemcpyAsync(uv_copy.data(), uv, uv_copy.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    uvh = uv_copy.data();
+    if (weights) {
+      w_copy.resize(M);
+      CK(h, cudaMemcpyAsync(w_copy.data(), weights, w_copy.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+      wsrc = w_copy.data();
+    }
     CK(h, cudaStreamSynchronize(h->stream));
   }
-  for (int m = 0; m < M; ++m) {
-    if (!std::isfinite(uvh[2 * m]) || !std::isfinite(uvh[2 * m + 1]) || std::fabs(uvh[2 * m]) >= M_PI ||
-        std::fabs(uvh[2 * m + 1]) >= M_PI)
-      return fail(h, PS_EINVAL, "set_measurements: |omega| must be < pi (radians per pixel)");
-    if (!(wh[m] >= 0.f) || !std::isfinite(wh[m])) return fail(h, PS_EINVAL, "set_measurements: weights must be >= 0");
-  }
+  auto wrow_of = [&](int64_t m) { return wsrc ? wsrc[m] : 1.0f; };
 
-  // Grid geometry: tap centres c = floor(u + 1/2), u = omega K / (2 pi).
+  // Grid geometry: tap centres c = floor(u + 1/2), u = omega K / (2 pi); rows checked.
   ps::GridGeom& g = h->g;
   g.K = 2 * h->n;
   g.logK = 0;
@@ -468,16 +514,36 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   const int hw = g.W / 2;
   std::vector<int> cx(M), cy(M);
   std::vector<float> fx(M), fy(M);
-  int cmax = 0;
-  for (int m = 0; m < M; ++m) {
-    const double u = uvh[2 * m] * g.K / (2.0 * M_PI), v = uvh[2 * m + 1] * g.K / (2.0 * M_PI);
-    const double cu = std::floor(u + 0.5), cv = std::floor(v + 0.5);
-    cx[m] = (int)cu;
-    cy[m] = (int)cv;
-    fx[m] = (float)(u - cu);
-    fy[m] = (float)(v - cv);
-    cmax = std::max(cmax, std::max(std::abs(cx[m]), std::abs(cy[m])));
+  std::vector<int> part_cmax(parts, 0), part_bad(parts, 0);
+  parallel_parts(M, parts, [&](int t, int64_t b, int64_t e) {
+    int cm = 0, bad = 0;
+    for (int64_t m = b; m < e; ++m) {
+      const double ou = uvh[2 * m], ov = uvh[2 * m + 1];
+      const float wm = wrow_of(m);
+      if (!std::isfinite(ou) || !std::isfinite(ov) || std::fabs(ou) >= M_PI || std::fabs(ov) >= M_PI) {
+        bad |= 1;
+        continue;
+      }
+      if (!(wm >= 0.f) || !std::isfinite(wm)) bad |= 2;
+      const double u = ou * g.K / (2.0 * M_PI), v = ov * g.K / (2.0 * M_PI);
+      const double cu = std::floor(u + 0.5), cv = std::floor(v + 0.5);
+      cx[m] = (int)cu;
+      cy[m] = (int)cv;
+      fx[m] = (float)(u - cu);
+      fy[m] = (float)(v - cv);
+      cm = std::max(cm, std::max(std::abs(cx[m]), std::abs(cy[m])));
+    }
+    part_cmax[t] = cm;
+    part_bad[t] = bad;
+  });
+  int cmax = 0, bad = 0;
+  for (int t = 0; t < parts; ++t) {
+    cmax = std::max(cmax, part_cmax[t]);
+    bad |= part_bad[t];
   }
+  if (bad) h->g = ps::GridGeom{};
+  if (bad & 1) return fail(h, PS_EINVAL, "set_measurements: |omega| must be < pi (radians per pixel)");
+  if (bad & 2) return fail(h, PS_EINVAL, "set_measurements: weights must be >= 0");
   g.R = cmax + hw;
   if (2 * g.R + 1 <= g.K) {
     g.full = 0;
@@ -491,40 +557,56 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   g.tilesX = (g.Wd + ps::kGridTile - 1) / ps::kGridTile;
   auto gi = [&](int k) { return g.full ? (k & (g.K - 1)) : k + g.off; };
 
-  // Sort key of each row: gridding tile, then tap-centre cell (row-major in the tile).
-  // The keys take at most tilesX^2 kGridTile^2 values, so a stable counting sort orders
-  // the rows in O(M) (rows of one cell keep the caller's order).
-  std::vector<int32_t> perm(M);
-  std::vector<int64_t> key(M);
-  std::vector<int32_t> bucket(M);
-  const int64_t nbuckets = (int64_t)g.tilesX * g.tilesX * ps::kGridTile * ps::kGridTile;
-  std::vector<int32_t> count(nbuckets + 1, 0);
-  for (int m = 0; m < M; ++m) {
-    const int gy = gi(cy[m]), gx = gi(cx[m]);
-    const int64_t tile = (int64_t)(gy / ps::kGridTile) * g.tilesX + gx / ps::kGridTile;
-    key[m] = (tile << 26) | ((int64_t)gy << 13) | gx;
-    bucket[m] = (int32_t)(tile * ps::kGridTile * ps::kGridTile + (gy % ps::kGridTile) * ps::kGridTile +
-                          gx % ps::kGridTile);
-    ++count[bucket[m] + 1];
-  }
-  for (int64_t b = 0; b < nbuckets; ++b) count[b + 1] += count[b];
-  for (int m = 0; m < M; ++m) perm[count[bucket[m]]++] = m;
+  // Storage order: rows sorted by gridding tile, then tap-centre cell (row-major in the
+  // tile), rows of one cell in the caller's order: two stable counting-sort passes
+  // (cell within the tile, then tile).
+  const int TS = ps::kGridTile;
+  auto tile_of = [&](int32_t m) { return (int64_t)(gi(cy[m]) / TS) * g.tilesX + gi(cx[m]) / TS; };
+  auto cell_of = [&](int32_t m) { return (int64_t)((gi(cy[m]) % TS) * TS + gi(cx[m]) % TS); };
+  std::vector<int32_t> perm(M), tmp(M);
+  std::iota(tmp.begin(), tmp.end(), 0);
+  counting_sort(tmp, perm, (int64_t)TS * TS, parts, cell_of);
+  tmp.swap(perm);
+  counting_sort(tmp, perm, (int64_t)g.tilesX * g.tilesX, parts, tile_of);
+  std::vector<int64_t> skey(M);   // sorted (tile, cell) keys
+  parallel_parts(M, parts, [&](int, int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) skey[i] = tile_of(perm[i]) * TS * TS + cell_of(perm[i]);
+  });
   if (M > 0) h->offsets_host.assign(block_offsets, block_offsets + nblocks + 1);
   else h->offsets_host.assign(1, 0);
-  // Storage order: every row sorted by tap-centre cell (tile-major), blocks interleaved.
   std::vector<uint16_t> blk_user(M);
   for (int b = 0; b < (M > 0 ? nblocks : 0); ++b)
-    for (int64_t i = block_offsets[b]; i < block_offsets[b + 1]; ++i) blk_user[i] = (uint16_t)b;
+    std::fill(blk_user.begin() + block_offsets[b], blk_user.begin() + block_offsets[b + 1], (uint16_t)b);
   std::vector<uint16_t> vblk(M);
-  for (int i = 0; i < M; ++i) vblk[i] = blk_user[perm[i]];
+  std::vector<float4> rech(M);
+  parallel_parts(M, parts, [&](int, int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) {
+      const int m = perm[i];
+      vblk[i] = blk_user[m];
+      const int packed = (cx[m] & 0xFFFF) | (cy[m] << 16);
+      float pf;
+      std::memcpy(&pf, &packed, sizeof(pf));
+      rech[i] = make_float4(fx[m], fy[m], wrow_of(m), pf);
+    }
+  });
+  // 2 sum w_m^2 over a fixed partition (the same sum on every machine).
+  constexpr int kPsfParts = 16;
+  std::vector<double> part_psf(kPsfParts, 0.0);
+  parallel_parts(M, kPsfParts, [&](int t, int64_t b, int64_t e) {
+    double acc = 0.0;
+    for (int64_t m = b; m < e; ++m) acc += 2.0 * (double)wrow_of(m) * wrow_of(m);
+    part_psf[t] = acc;
+  });
+  h->psf_peak = std::accumulate(part_psf.begin(), part_psf.end(), 0.0);
+  // Work items (<= kGridItem rows of one tile) and same-cell chunks (<= kBinChunk rows).
   std::vector<ps::GridItem> items;
   std::vector<int32_t> gchunks;
   {
     int j0 = 0;
     while (j0 < M) {
-      const int64_t tile = key[perm[j0]] >> 26;
+      const int64_t tile = skey[j0] / (TS * TS);
       int j1 = j0;
-      while (j1 < M && j1 - j0 < ps::kGridItem && (key[perm[j1]] >> 26) == tile) ++j1;
+      while (j1 < M && j1 - j0 < ps::kGridItem && skey[j1] / (TS * TS) == tile) ++j1;
       ps::GridItem it{};
       it.ty = (int32_t)(tile / g.tilesX);
       it.tx = (int32_t)(tile % g.tilesX);
@@ -533,11 +615,10 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
       it.cstart = (int32_t)gchunks.size();
       int c0 = j0;
       while (c0 < j1) {
-        const int64_t cell = key[perm[c0]] & ((1LL << 26) - 1);
+        const int64_t cell = skey[c0];
         int c1 = c0;
-        while (c1 < j1 && c1 - c0 < ps::kBinChunk && (key[perm[c1]] & ((1LL << 26) - 1)) == cell) ++c1;
-        const int gy = (int)(cell >> 13), gx = (int)(cell & 8191);
-        const int ly = gy - it.ty * ps::kGridTile, lx = gx - it.tx * ps::kGridTile;
+        while (c1 < j1 && c1 - c0 < ps::kBinChunk && skey[c1] == cell) ++c1;
+        const int ly = (int)(cell % (TS * TS)) / TS, lx = (int)(cell % TS);
         gchunks.push_back((c0 - j0) | ((c1 - c0) << 10) | (ly << 16) | (lx << 24));
         c0 = c1;
       }
@@ -552,18 +633,6 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   h->ngchunks = (int)gchunks.size();
   if (M > 0) h->eps_host.assign(eps, eps + h->nblocks);
   else h->eps_host.clear();
-
-  std::vector<float4> rech(M);
-  double psf = 0.0;
-  for (int i = 0; i < M; ++i) {
-    const int m = perm[i];
-    const int packed = (cx[m] & 0xFFFF) | (cy[m] << 16);
-    float pf;
-    std::memcpy(&pf, &packed, sizeof(pf));
-    rech[i] = make_float4(fx[m], fy[m], wh[m], pf);
-    psf += 2.0 * (double)wh[m] * wh[m];
-  }
-  h->psf_peak = psf;
 
   // Device buffers for the visibility domain and the grid.
   const size_t Wd = g.Wd;
