@@ -131,3 +131,34 @@ def test_forced_launch_choices_iterate_like_oracle(tuning):
         got = s.get_state()
     for k in ("S", "Z", "A", "B", "C", "D"):
         assert rel_err(got[k], ref[k]) <= 2e-5 * 3, k
+
+
+# Relative error of the windowed NUFFT against the exact DFT of the oracle: the ES
+# kernel's aliasing error at oversampling 2 falls like exp(-pi W sqrt(1 - 1/2)),
+# about 1.5e-5 at W = 5 and below FP32 rounding at W = 9; the bound takes ten times
+# that, and never less than the FP32 operator tolerance.
+WIDTH_TOL = {5: 1.5e-4, 9: OP_TOL}
+
+
+@pytest.mark.parametrize("width", [5, 9])
+def test_other_kernel_widths_every_choice_match_oracle(width):
+    """Kernel widths 5 and 9 (W = 9 runs the CUDA-core gridding forms only; choices 2
+    and 3 fall back to 0) on every gridding and degridding launch choice."""
+    n, M, levels = 64, 3000, 3
+    pb = make_problem(n, M, levels, 2, seed=21)
+    rng = np.random.default_rng(22)
+    S = rng.normal(size=(4, n, n)).astype(np.float32)
+    ref_phi = meas.phi(S.astype(np.float64), pb["uv"], pb["w"].astype(np.float64))
+    Yr = (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))).astype(np.complex64)
+    ref_adj = meas.phi_adjoint(Yr.astype(np.complex128), pb["uv"], pb["w"].astype(np.float64), n)
+    s = PolarizedSARA(n, levels, kernel_width=width)
+    with s:
+        s.set_measurements(pb["uv"], pb["Y"], pb["w"], pb["off"], pb["eps"])
+        for deg, grd in itertools.product(range(2), range(4)):
+            B.ps_set_tuning(s.h, [0, deg, grd, 0])
+            Yg = np.empty((M, 4), np.complex64)
+            B.ps_apply_phi(s.h, S, Yg)
+            Ag = np.empty((4, n, n), np.float32)
+            B.ps_apply_phi_adjoint(s.h, Yr, Ag)
+            assert rel_err(Yg, ref_phi) <= WIDTH_TOL[width], (width, deg, grd, rel_err(Yg, ref_phi))
+            assert rel_err(Ag, ref_adj) <= WIDTH_TOL[width], (width, deg, grd, rel_err(Ag, ref_adj))
