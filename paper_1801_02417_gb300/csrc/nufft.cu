@@ -723,7 +723,6 @@ __device__ __forceinline__ void grid_flush(const float* __restrict__ acc, int ty
 }
 
 constexpr int kGridThreads = 256;   // threads of a gridding CTA
-static_assert(kGridItem % kGridThreads == 0, "whole rows per thread");
 
 template <int W, int FORM>
 __global__ void __launch_bounds__(kGridThreads) k_grid(
@@ -748,7 +747,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
   }
   const float4* v4 = reinterpret_cast<const float4*>(vin);
   // Every global load of this thread's rows is issued before the first is used.
-  constexpr int RPT = kGridItem / kGridThreads;   // rows per thread
+  constexpr int RPT = (kGridItem + kGridThreads - 1) / kGridThreads;   // rows per thread
   float4 r[RPT], b0[RPT], b1[RPT];
   int blk[RPT];
 #pragma unroll
