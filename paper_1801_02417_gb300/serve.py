@@ -3,14 +3,18 @@
 Requests (independent imaging problems) arrive over time. The server admits
 them in arrival order while their estimated device footprint
 (`ps_estimate_bytes`) fits the memory budget and a slot is free, prepares each
-admitted problem on a worker thread (handle creation, row sorting, power
-iteration), and keeps every active problem's primal/dual state resident on the
+admitted problem on a worker thread (handle creation, row sorting, operator
+norm), and keeps every active problem's primal/dual state resident on the
 GPU. Each scheduler tick launches `check_every` iterations of every active
 problem on its own CUDA stream, so the kernels of different problems overlap on
 the device, then evaluates each problem's stopping rule (relative change of
 Eq. stop_crit) and advances its Algorithm 2 phase: an NNLS cycle, then up to
 `reweights` reweighted cycles of Algorithm 1. Finished problems return their
 Stokes maps and free their memory, which admits the next requests.
+
+Two front ends share the scheduler: `Server.run(requests)` replays a recorded
+arrival schedule, and `Server.start()` / `submit(problem) -> Future` / `stop()`
+(or `with Server(...) as srv:`) serves live submissions from any thread.
 
 All arithmetic runs in libpolsara.so; this module only schedules C ABI calls.
 """
@@ -143,6 +147,7 @@ class Server:
         self._tuning: dict = {}
         self._tuning_lock = threading.Lock()
         self._thread: threading.Thread | None = None
+        self._id_lock = threading.Lock()
 
     def _prepare(self, prob: Problem) -> PolarizedSARA:
         s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS)
@@ -200,7 +205,7 @@ class Server:
         if self._thread is None or self._closing.is_set():
             raise RuntimeError("server not running: submit() before start() or after stop()")
         fut: concurrent.futures.Future = concurrent.futures.Future()
-        with self._tuning_lock:
+        with self._id_lock:
             rid = self._next_id
             self._next_id += 1
         self._futures[rid] = fut
