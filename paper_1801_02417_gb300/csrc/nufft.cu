@@ -74,10 +74,11 @@ __device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int idx) {
 // and s+1 are done together by one thread on the four elements a, a+h, a+2h, a+3h
 // (h = 2^s, bits s and s+1 of a clear), so there is one shared-memory pass and one
 // barrier per two stages; an odd stage count ends with a plain radix-2 stage.
+// Stages below s0 are taken as done (the caller wrote their output).
 template <bool INV>
-__device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK) {
+__device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK, int s0 = 0) {
   const int K = 1 << logK;
-  int s = 0;
+  int s = s0;
   for (; s + 1 < logK; s += 2) {
     const int hs = 1 << s;
     const int c1 = fsw(hs), c2 = fsw(2 * hs);
@@ -114,6 +115,18 @@ __device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK) {
   }
 }
 
+// Input of a K-point transform whose nonzero samples fill exactly one of each pair of
+// natural indices (x, x + K/2), i.e. the bit-reversed neighbours (r, r ^ 1) that the
+// first radix-2 stage combines (twiddle 1): that stage is folded into the scatter.
+// Sample v at natural index idx writes both outputs of its pair, v at the even slot
+// and +v or -v (idx < K/2 or not) at the odd one; fft_smem then starts at stage 1.
+// Every slot is written, so the buffer needs no clearing.
+__device__ __forceinline__ void scatter_stage0(float4* buf, int idx, int logK, float4 v) {
+  const int r = bitrev(idx, logK);
+  buf[fsw(r & ~1)] = v;
+  buf[fsw(r | 1)] = (idx < (1 << (logK - 1))) ? v : make_float4(-v.x, -v.y, -v.z, -v.w);
+}
+
 __device__ __forceinline__ int gidx(int k, int off, int full, int K) {
   return full ? (k & (K - 1)) : (k + off);
 }
@@ -125,19 +138,18 @@ __global__ void k_fwd_rows(const float* __restrict__ X, int n, int N, const floa
   extern __shared__ float4 sm[];
   float4* buf = sm;
   const int p = blockIdx.x;
-  for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
   const float cy = corr[p];
   const size_t row = (size_t)p * n;
+  // The n samples sit at natural indices [0, n/2) and [K - n/2, K) of K = 2n: one per pair.
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const int idx = (q - n / 2 + K) & (K - 1);
     const float c = cy * corr[q];
     const size_t o = row + q;
-    buf[fsw(bitrev(idx, logK))] = make_float4(X[o] * c, X[N + o] * c, X[2 * (size_t)N + o] * c,
-                                              X[3 * (size_t)N + o] * c);
+    scatter_stage0(buf, idx, logK, make_float4(X[o] * c, X[N + o] * c, X[2 * (size_t)N + o] * c,
+                                               X[3 * (size_t)N + o] * c));
   }
   __syncthreads();
-  fft_smem<false>(buf, tw, logK);
+  fft_smem<false>(buf, tw, logK, 1);
   for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
     const int k = full ? gx : gx - off;
     T1[(size_t)p * Wd + gx] = buf[fsw((k + K) & (K - 1))];
@@ -149,14 +161,12 @@ __global__ void k_fwd_cols(const float4* __restrict__ T1, int n, const float2* _
   extern __shared__ float4 sm[];
   float4* buf = sm;
   const int gx = blockIdx.x;
-  for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int idx = (p - n / 2 + K) & (K - 1);
-    buf[fsw(bitrev(idx, logK))] = T1[(size_t)p * Wd + gx];
+    scatter_stage0(buf, idx, logK, T1[(size_t)p * Wd + gx]);
   }
   __syncthreads();
-  fft_smem<false>(buf, tw, logK);
+  fft_smem<false>(buf, tw, logK, 1);
   for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
     const int k = full ? gy : gy - off;
     G[(size_t)gy * Wd + gx] = buf[fsw((k + K) & (K - 1))];
@@ -806,25 +816,69 @@ __global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* 
   const int kx = blockIdx.x;
   const int self = (kx == 0) || (full && kx == K / 2);
   const int gxp = gidx(kx, off, full, K), gxm = gidx(-kx, off, full, K);
-  for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) sm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
-  for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
-    const int ky = full ? (gy <= K / 2 ? gy : gy - K) : gy - off;
-    const int gym = gidx(-ky, off, full, K);
+  // H(ky) of this column pair: hp for +kx (slot ky of bp), hm for -kx (slot -ky of bm).
+  auto hpm = [&](int ky, float4& hp, float4& hm) {
+    const int gy = gidx(ky, off, full, K), gym = gidx(-ky, off, full, K);
     const float4 a0 = Acc[2 * ((size_t)gy * Wd + gxp)], a1 = Acc[2 * ((size_t)gy * Wd + gxp) + 1];
     const float4 b0 = Acc[2 * ((size_t)gym * Wd + gxm)], b1 = Acc[2 * ((size_t)gym * Wd + gxm) + 1];
     const float P1r = a0.x + b0.x, P1i = a0.y - b0.y, Q1r = a0.z + b0.z, Q1i = a0.w - b0.w;
     const float P2r = a1.x + b1.x, P2i = a1.y - b1.y, Q2r = a1.z + b1.z, Q2i = a1.w - b1.w;
-    const float4 hp = make_float4(P1r - Q1i, P1i + Q1r, P2r - Q2i, P2i + Q2r);
-    bp[fsw(bitrev((ky + K) & (K - 1), logK))] = hp;
-    if (!self) {
-      const float4 hm = make_float4(P1r + Q1i, -P1i + Q1r, P2r + Q2i, -P2i + Q2r);
-      bm[fsw(bitrev((-ky + K) & (K - 1), logK))] = hm;
+    hp = make_float4(P1r - Q1i, P1i + Q1r, P2r - Q2i, P2i + Q2r);
+    hm = make_float4(P1r + Q1i, -P1i + Q1r, P2r + Q2i, -P2i + Q2r);
+  };
+  if (!full && 8 * off < K) {
+    // As in k_adj_rows: the window [-R, R] with R < K/8 puts at most one sample in each
+    // block of natural indices x + j K/4, so the first two inverse stages are written
+    // directly (v (i^{j t})_t, j = 0 or 3) and fft_smem starts at stage 2.
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto put4 = [&](float4* b, int r0, int j, float4 v) {
+      if (j == 0) {
+        b[fsw(r0)] = b[fsw(r0 + 1)] = b[fsw(r0 + 2)] = b[fsw(r0 + 3)] = v;
+      } else if (j == 3) {
+        b[fsw(r0)] = v;
+        b[fsw(r0 + 1)] = make_float4(v.y, -v.x, v.w, -v.z);
+        b[fsw(r0 + 2)] = make_float4(-v.x, -v.y, -v.z, -v.w);
+        b[fsw(r0 + 3)] = make_float4(-v.y, v.x, -v.w, v.z);
+      } else {
+        b[fsw(r0)] = b[fsw(r0 + 1)] = b[fsw(r0 + 2)] = b[fsw(r0 + 3)] = z;
+      }
+    };
+    for (int x = threadIdx.x; x < (K >> 2); x += blockDim.x) {
+      const int r0 = bitrev(x, logK);
+      const int j = x <= off ? 0 : (x >= (K >> 2) - off ? 3 : -1);
+      const int k = j == 0 ? x : x - (K >> 2);    // the block's sample index (when j >= 0)
+      float4 hp = z, hm = z, unused;
+      if (j >= 0) {
+        hpm(k, hp, unused);                       // bp[k] = hp(k)
+        if (!self) hpm(-k, unused, hm);           // bm[k] = hm(-k)
+      }
+      put4(bp, r0, j, hp);
+      if (!self) put4(bm, r0, j, hm);
     }
+    __syncthreads();
+    fft_smem<true>(bp, tw, logK, 2);
+    if (!self) fft_smem<true>(bm, tw, logK, 2);
+  } else {
+    for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) sm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
+      const int ky = full ? (gy <= K / 2 ? gy : gy - K) : gy - off;
+      const int gym = gidx(-ky, off, full, K);
+      const float4 a0 = Acc[2 * ((size_t)gy * Wd + gxp)], a1 = Acc[2 * ((size_t)gy * Wd + gxp) + 1];
+      const float4 b0 = Acc[2 * ((size_t)gym * Wd + gxm)], b1 = Acc[2 * ((size_t)gym * Wd + gxm) + 1];
+      const float P1r = a0.x + b0.x, P1i = a0.y - b0.y, Q1r = a0.z + b0.z, Q1i = a0.w - b0.w;
+      const float P2r = a1.x + b1.x, P2i = a1.y - b1.y, Q2r = a1.z + b1.z, Q2i = a1.w - b1.w;
+      const float4 hp = make_float4(P1r - Q1i, P1i + Q1r, P2r - Q2i, P2i + Q2r);
+      bp[fsw(bitrev((ky + K) & (K - 1), logK))] = hp;
+      if (!self) {
+        const float4 hm = make_float4(P1r + Q1i, -P1i + Q1r, P2r + Q2i, -P2i + Q2r);
+        bm[fsw(bitrev((-ky + K) & (K - 1), logK))] = hm;
+      }
+    }
+    __syncthreads();
+    fft_smem<true>(bp, tw, logK);
+    if (!self) fft_smem<true>(bm, tw, logK);
   }
-  __syncthreads();
-  fft_smem<true>(bp, tw, logK);
-  if (!self) fft_smem<true>(bm, tw, logK);
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int idx = fsw((p - n / 2 + K) & (K - 1));
     T2[(size_t)p * Wd + gxp] = bp[idx];
@@ -838,14 +892,42 @@ __global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const fl
   extern __shared__ float4 sm[];
   float4* buf = sm;
   const int p = blockIdx.x;
-  for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
-  for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
-    const int k = full ? gx : gx - off;
-    buf[fsw(bitrev((k + K) & (K - 1), logK))] = T2[(size_t)p * Wd + gx];
+  if (!full && 8 * off < K) {
+    // Window [-R, R] with R < K/8: of the natural indices x + j K/4 (j = 0..3) at most
+    // one holds a sample (j = 0: k = x <= R; j = 3: k = x - K/4 >= -R), so the first two
+    // radix-2 stages reduce to the 4-point inverse DFT of one sample, v (i^{j t})_t,
+    // written straight to the four slots 4B + t of its block (x = bitrev(4B)); blocks
+    // without a sample get zeros, and fft_smem starts at stage 2.
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int x = threadIdx.x; x < (K >> 2); x += blockDim.x) {
+      const int r0 = bitrev(x, logK);
+      float4 v0 = z, v1 = z, v2 = z, v3 = z;
+      if (x <= off) {
+        v0 = v1 = v2 = v3 = T2[(size_t)p * Wd + x + off];
+      } else if (x >= (K >> 2) - off) {
+        const float4 v = T2[(size_t)p * Wd + x - (K >> 2) + off];
+        v0 = v;
+        v1 = make_float4(v.y, -v.x, v.w, -v.z);    // -i v
+        v2 = make_float4(-v.x, -v.y, -v.z, -v.w);  // -v
+        v3 = make_float4(-v.y, v.x, -v.w, v.z);    // +i v
+      }
+      buf[fsw(r0)] = v0;
+      buf[fsw(r0 + 1)] = v1;
+      buf[fsw(r0 + 2)] = v2;
+      buf[fsw(r0 + 3)] = v3;
+    }
+    __syncthreads();
+    fft_smem<true>(buf, tw, logK, 2);
+  } else {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
+      const int k = full ? gx : gx - off;
+      buf[fsw(bitrev((k + K) & (K - 1), logK))] = T2[(size_t)p * Wd + gx];
+    }
+    __syncthreads();
+    fft_smem<true>(buf, tw, logK);
   }
-  __syncthreads();
-  fft_smem<true>(buf, tw, logK);
   const float cy = 0.5f * corr[p];
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const float4 v = buf[fsw((q - n / 2 + K) & (K - 1))];
