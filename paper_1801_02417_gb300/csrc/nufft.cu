@@ -74,12 +74,14 @@ __device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int idx) {
 // and s+1 are done together by one thread on the four elements a, a+h, a+2h, a+3h
 // (h = 2^s, bits s and s+1 of a clear), so there is one shared-memory pass and one
 // barrier per two stages; an odd stage count ends with a plain radix-2 stage.
-// Stages below s0 are taken as done (the caller wrote their output).
+// Stages below s0 are taken as done (the caller wrote their output); stages from
+// s_end on are left to the caller (fft_out).
 template <bool INV>
-__device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK, int s0 = 0) {
+__device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK, int s0 = 0, int s_end = -1) {
   const int K = 1 << logK;
+  if (s_end < 0) s_end = logK;
   int s = s0;
-  for (; s + 1 < logK; s += 2) {
+  for (; s + 1 < s_end; s += 2) {
     const int hs = 1 << s;
     const int c1 = fsw(hs), c2 = fsw(2 * hs);
     for (int g = threadIdx.x; g < (K >> 2); g += blockDim.x) {
@@ -99,7 +101,7 @@ __device__ void fft_smem(float4* buf, const float2* __restrict__ tw, int logK, i
     }
     __syncthreads();
   }
-  if (s < logK) {
+  if (s < s_end) {
     const int hs = 1 << s;
     const int c1 = fsw(hs);
     for (int b = threadIdx.x; b < (K >> 1); b += blockDim.x) {
@@ -127,6 +129,36 @@ __device__ __forceinline__ void scatter_stage0(float4* buf, int idx, int logK, f
   buf[fsw(r | 1)] = (idx < (1 << (logK - 1))) ? v : make_float4(-v.x, -v.y, -v.z, -v.w);
 }
 
+// First stage fft_out finishes when the passes start at s0: the last radix-4 pass, or
+// the last radix-2 stage when the stage count from s0 is odd.
+__device__ __forceinline__ int fft_tail_start(int logK, int s0) {
+  return ((logK - s0) & 1) ? logK - 1 : logK - 2;
+}
+
+// Natural-order output k of the transform whose stages below s_last are done in buf;
+// its remaining one (s_last = logK - 1) or two (s_last = logK - 2) stages are applied
+// here for this output alone (the same arithmetic as the last pass of fft_smem), so
+// a caller that needs few outputs skips that pass, its barrier and a buffer rewrite.
+template <bool INV>
+__device__ __forceinline__ float4 fft_out(const float4* buf, const float2* __restrict__ tw, int logK, int s_last,
+                                          int k) {
+  const int hs = 1 << s_last;
+  const int g = k & (hs - 1);
+  if (s_last == logK - 2) {
+    const float2 w0 = twid<INV>(tw, hs - 1 + g), w1 = twid<INV>(tw, 2 * hs - 1 + g), w2 = twid<INV>(tw, 3 * hs - 1 + g);
+    const float4 x0 = buf[fsw(g)], x1 = buf[fsw(g + hs)], x2 = buf[fsw(g + 2 * hs)], x3 = buf[fsw(g + 3 * hs)];
+    const float4 t1 = cmul2(x1, w0), t3 = cmul2(x3, w0);
+    const int j = k >> s_last;
+    if (j == 0) return f4add(f4add(x0, t1), cmul2(f4add(x2, t3), w1));
+    if (j == 2) return f4sub(f4add(x0, t1), cmul2(f4add(x2, t3), w1));
+    if (j == 1) return f4add(f4sub(x0, t1), cmul2(f4sub(x2, t3), w2));
+    return f4sub(f4sub(x0, t1), cmul2(f4sub(x2, t3), w2));
+  }
+  const float2 w = twid<INV>(tw, hs - 1 + g);
+  const float4 u = buf[fsw(g)], v = cmul2(buf[fsw(g + hs)], w);
+  return k < hs ? f4add(u, v) : f4sub(u, v);
+}
+
 __device__ __forceinline__ int gidx(int k, int off, int full, int K) {
   return full ? (k & (K - 1)) : (k + off);
 }
@@ -149,10 +181,11 @@ __global__ void k_fwd_rows(const float* __restrict__ X, int n, int N, const floa
                                                X[3 * (size_t)N + o] * c));
   }
   __syncthreads();
-  fft_smem<false>(buf, tw, logK, 1);
+  const int st = fft_tail_start(logK, 1);
+  fft_smem<false>(buf, tw, logK, 1, st);
   for (int gx = threadIdx.x; gx < Wd; gx += blockDim.x) {
     const int k = full ? gx : gx - off;
-    T1[(size_t)p * Wd + gx] = buf[fsw((k + K) & (K - 1))];
+    T1[(size_t)p * Wd + gx] = fft_out<false>(buf, tw, logK, st, (k + K) & (K - 1));
   }
 }
 
@@ -166,10 +199,11 @@ __global__ void k_fwd_cols(const float4* __restrict__ T1, int n, const float2* _
     scatter_stage0(buf, idx, logK, T1[(size_t)p * Wd + gx]);
   }
   __syncthreads();
-  fft_smem<false>(buf, tw, logK, 1);
+  const int st = fft_tail_start(logK, 1);
+  fft_smem<false>(buf, tw, logK, 1, st);
   for (int gy = threadIdx.x; gy < Wd; gy += blockDim.x) {
     const int k = full ? gy : gy - off;
-    G[(size_t)gy * Wd + gx] = buf[fsw((k + K) & (K - 1))];
+    G[(size_t)gy * Wd + gx] = fft_out<false>(buf, tw, logK, st, (k + K) & (K - 1));
   }
 }
 
@@ -826,6 +860,7 @@ __global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* 
     hp = make_float4(P1r - Q1i, P1i + Q1r, P2r - Q2i, P2i + Q2r);
     hm = make_float4(P1r + Q1i, -P1i + Q1r, P2r + Q2i, -P2i + Q2r);
   };
+  int st;
   if (!full && 8 * off < K) {
     // As in k_adj_rows: the window [-R, R] with R < K/8 puts at most one sample in each
     // block of natural indices x + j K/4, so the first two inverse stages are written
@@ -856,8 +891,9 @@ __global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* 
       if (!self) put4(bm, r0, j, hm);
     }
     __syncthreads();
-    fft_smem<true>(bp, tw, logK, 2);
-    if (!self) fft_smem<true>(bm, tw, logK, 2);
+    st = fft_tail_start(logK, 2);
+    fft_smem<true>(bp, tw, logK, 2, st);
+    if (!self) fft_smem<true>(bm, tw, logK, 2, st);
   } else {
     for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) sm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
@@ -876,13 +912,14 @@ __global__ void k_adj_cols(const float4* __restrict__ Acc, int n, const float2* 
       }
     }
     __syncthreads();
-    fft_smem<true>(bp, tw, logK);
-    if (!self) fft_smem<true>(bm, tw, logK);
+    st = fft_tail_start(logK, 0);
+    fft_smem<true>(bp, tw, logK, 0, st);
+    if (!self) fft_smem<true>(bm, tw, logK, 0, st);
   }
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int idx = fsw((p - n / 2 + K) & (K - 1));
-    T2[(size_t)p * Wd + gxp] = bp[idx];
-    if (!self) T2[(size_t)p * Wd + gxm] = bm[idx];
+    const int k = (p - n / 2 + K) & (K - 1);
+    T2[(size_t)p * Wd + gxp] = fft_out<true>(bp, tw, logK, st, k);
+    if (!self) T2[(size_t)p * Wd + gxm] = fft_out<true>(bm, tw, logK, st, k);
   }
 }
 
@@ -892,6 +929,7 @@ __global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const fl
   extern __shared__ float4 sm[];
   float4* buf = sm;
   const int p = blockIdx.x;
+  int st;
   if (!full && 8 * off < K) {
     // Window [-R, R] with R < K/8: of the natural indices x + j K/4 (j = 0..3) at most
     // one holds a sample (j = 0: k = x <= R; j = 3: k = x - K/4 >= -R), so the first two
@@ -917,7 +955,8 @@ __global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const fl
       buf[fsw(r0 + 3)] = v3;
     }
     __syncthreads();
-    fft_smem<true>(buf, tw, logK, 2);
+    st = fft_tail_start(logK, 2);
+    fft_smem<true>(buf, tw, logK, 2, st);
   } else {
     for (int i = threadIdx.x; i < K; i += blockDim.x) buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
@@ -926,11 +965,12 @@ __global__ void k_adj_rows(const float4* __restrict__ T2, int n, int N, const fl
       buf[fsw(bitrev((k + K) & (K - 1), logK))] = T2[(size_t)p * Wd + gx];
     }
     __syncthreads();
-    fft_smem<true>(buf, tw, logK);
+    st = fft_tail_start(logK, 0);
+    fft_smem<true>(buf, tw, logK, 0, st);
   }
   const float cy = 0.5f * corr[p];
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const float4 v = buf[fsw((q - n / 2 + K) & (K - 1))];
+    const float4 v = fft_out<true>(buf, tw, logK, st, (q - n / 2 + K) & (K - 1));
     const float c = cy * corr[q];
     const size_t o = (size_t)p * n + q;
     out[o] = v.x * c;
