@@ -355,6 +355,26 @@ def served_measure(pool, rate: float, duration: float, seed: int) -> dict:
             "continuous_batching": cont, "one_at_a_time": solo}
 
 
+def hyperspectral_measure(nchan: int = 8, n: int = 256, M: int = 50000, seed: int = 0) -> dict:
+    """Multi-frequency observation (20% bandwidth, spectral index -0.7, Faraday rotation):
+    one independent Polarized SARA solve per channel, all channels submitted at once to the
+    continuous-batching server (each on its own stream, overlapping) vs one after another."""
+    from paper_1801_02417_gb300.serve import Policy, Server, summarize, synthesize_channels
+    chans = synthesize_channels(n, 4, M, nchan, seed, nblocks=8)
+    pol = Policy(rel_tol=1e-4, max_iter=2000, reweights=5, check_every=20)
+    reqs = [(0.0, p) for p in chans]
+    t0 = time.perf_counter()
+    cont = Server(hbm_budget=64 << 30, max_active=nchan, policy=pol).run(reqs)
+    t_cont = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Server(hbm_budget=64 << 30, max_active=1, policy=pol).run(reqs)
+    t_seq = time.perf_counter() - t0
+    s = summarize(cont)
+    return {"channels": nchan, "n": n, "rows_per_channel": M, "frac_bandwidth": 0.2,
+            "batched_s": t_cont, "sequential_s": t_seq, "speedup": t_seq / t_cont,
+            "channels_per_s": nchan / t_cont, "iterations_mean": s["iterations_mean"]}
+
+
 # ------------------------------------------------------------------ arms
 def aggregate_replicas(ms: float, steps: int, world: int, device: str = "cuda"):
     """Replicas (one independent solve per rank, no collective on the data path): the job's
@@ -550,13 +570,14 @@ def run_own(args) -> None:
                "note": "PS_SOC: polarization cone as one dual (no Z, D), same problem as the epigraph split"}
         s.set_mode(B.PS_POLARIZED)
 
-    batched = served = np_cmp = None
+    batched = served = np_cmp = hyper = None
     if rank == 0 and world == 1 and not args.no_serve:
         np_cmp = np_comparison()
         s.close()
         pool = draw_requests(args.batch, seed=wl.seed + 50)
         batched = batched_measure(pool, iters=50)
         served = served_measure(pool, rate=args.serve_rate, duration=args.serve_seconds, seed=wl.seed + 60)
+        hyper = hyperspectral_measure(seed=wl.seed + 70)
         s = None
 
     cpu = None
@@ -596,6 +617,7 @@ def run_own(args) -> None:
             "cpu_baseline": cpu,
             "batched": batched,
             "served": served,
+            "hyperspectral": hyper,
             "np_comparison": np_cmp,
         }
         print(json.dumps(line), flush=True)

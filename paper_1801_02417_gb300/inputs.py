@@ -156,6 +156,42 @@ def uv_coverage(w: Workload, omega_max: float = EHT_OMEGA_MAX) -> np.ndarray:
     return uv * (omega_max / rmax)
 
 
+# ---- multi-frequency (hyperspectral) channel sets: the polarization constraint acts
+# at each wavelength on its own (Section 6), so each channel is an independent
+# Stokes imaging problem; these generators give the channels' inputs.
+def channel_ratios(nchan: int, frac_bw: float) -> np.ndarray:
+    """Channel frequencies over the reference frequency, evenly over the band [1 - bw/2, 1 + bw/2]."""
+    if nchan == 1:
+        return np.ones(1)
+    return 1.0 + frac_bw * (np.arange(nchan) / (nchan - 1) - 0.5)
+
+
+def channel_uv(uv0: np.ndarray, ratio: float) -> np.ndarray:
+    """Sampled frequencies of a channel: baselines in wavelengths grow with frequency."""
+    return uv0 * ratio
+
+
+def rotation_measure_map(n: int, seed: int, peak: float) -> np.ndarray:
+    """Smooth Faraday depth map, expressed as RM lambda_0^2 in radians, |.| <= peak."""
+    rng = np.random.default_rng(seed + 17)
+    f = 2.0 * _smooth_field(rng, n) - 1.0
+    return peak * f / max(float(np.abs(f).max()), 1e-30)
+
+
+def channel_stokes(S0: np.ndarray, ratio: float, alpha: float, rm_l0sq: np.ndarray) -> np.ndarray:
+    """Stokes maps of one channel from the reference-frequency maps S0 (4, n, n).
+
+    I and V follow a power law ratio^alpha; the linear polarization P = Q + iU follows
+    the same law and turns by 2 RM (lambda_c^2 - lambda_0^2) = 2 RM lambda_0^2 (ratio^-2 - 1)
+    (Faraday rotation), which keeps |P| and so the constraint sqrt(Q^2+U^2+V^2) <= I.
+    """
+    amp = ratio ** alpha
+    turn = 2.0 * rm_l0sq * (ratio ** -2 - 1.0)
+    c, s = np.cos(turn), np.sin(turn)
+    Q, U = S0[1], S0[2]
+    return np.stack([amp * S0[0], amp * (c * Q - s * U), amp * (s * Q + c * U), amp * S0[3]])
+
+
 def random_uv(M: int, seed: int, omega_max: float) -> np.ndarray:
     """Uniformly scattered frequencies in a square of half-width ``omega_max`` rad/pixel."""
     rng = np.random.default_rng(seed)

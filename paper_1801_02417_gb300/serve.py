@@ -372,6 +372,50 @@ def synthesize_problem(n: int, levels: int, M: int, seed: int, nblocks: int = 1,
     return Problem(n, levels, uv, Y, w, off, eps, gamma)
 
 
+def synthesize_channels(n: int, levels: int, M: int, nchan: int, seed: int, nblocks: int = 1,
+                        frac_bw: float = 0.2, alpha: float = -0.7, rm_peak: float = 2.0, snr_db: float = 30.0,
+                        gamma_factor: float = 1e-3) -> list[Problem]:
+    """Multi-frequency (hyperspectral) observation of one polarized source as independent
+    per-channel problems (the polarization constraint acts at each wavelength on its own).
+
+    One uv track set at the reference frequency, scaled per channel; the source follows a
+    power law of index `alpha` with Faraday rotation by a smooth RM lambda_0^2 map of peak
+    `rm_peak` rad; clean visibilities from the library's phi, noise at `snr_db` per channel,
+    chi^2 radii and gamma per channel as in `synthesize_problem`.
+    """
+    from . import inputs
+    stations = 8
+    pairs = stations * (stations - 1) // 2
+    while pairs * 16 < M:
+        stations += 2
+        pairs = stations * (stations - 1) // 2
+    wl = inputs.Workload("channels", n, M, stations, M // pairs + 2, levels, nblocks, 0, 0, snr_db, 0, seed)
+    ratios = inputs.channel_ratios(nchan, frac_bw)
+    uv0 = inputs.uv_coverage(wl, omega_max=inputs.EHT_OMEGA_MAX / float(ratios.max()))
+    S0 = inputs.stokes_source(n, seed)
+    rm = inputs.rotation_measure_map(n, seed, rm_peak)
+    w = np.ones(M, np.float32)
+    off = inputs.block_offsets(M, nblocks)
+    out = []
+    for c, ratio in enumerate(ratios):
+        uv = inputs.channel_uv(uv0, float(ratio))
+        truth = inputs.channel_stokes(S0, float(ratio), alpha, rm).astype(np.float32)
+        with PolarizedSARA(n, levels) as s:
+            s.set_measurements(uv, np.zeros((M, 4), np.complex64), w, off, np.ones(nblocks))
+            clean = np.empty((M, 4), np.complex64)
+            B.ps_apply_phi(s.h, truth, clean)
+            sigma = inputs.sigma_for_snr(clean, snr_db)
+            Y = (clean + inputs.complex_noise(M, sigma, seed + 101 * c)).astype(np.complex64)
+            B.ps_set_visibilities(s.h, Y)
+            dirty = np.empty((4, n, n), np.float32)
+            B.ps_apply_phi_adjoint(s.h, Y, dirty)
+            s.set_state({"S": dirty})
+            gamma = gamma_factor * B.ps_max_abs_analysis(s.h) / B.ps_get_params(s.h)["opnorm_sq"]
+        eps = np.array([chi2_epsilon(int(off[b + 1] - off[b]), sigma) for b in range(nblocks)])
+        out.append(Problem(n, levels, uv, Y, w, off, eps, gamma))
+    return out
+
+
 SIZE_MIX = ((64, 0.4), (128, 0.3), (256, 0.2), (512, 0.1))
 
 
