@@ -13,6 +13,8 @@ It is a plain, slow, direct restatement of the paper:
                   (P_U, P_V, P_E1, P_E2, l2 ball, soft threshold);
   primal_dual.py  Algorithm 1 (one iteration, step order as printed),
                   Algorithm 2 (reweighting), NNLS start, stop-rule statistics.
+  tv.py           Algorithm 3 (Section 4.4): TV and l1 + TV problems with and
+                  without the polarization constraint.
 
 Every function cites the passage it follows. Where the paper is silent or
 inconsistent the oracle takes one documented reading (listed in each module).
