@@ -570,6 +570,25 @@ def run_own(args) -> None:
                "note": "PS_SOC: polarization cone as one dual (no Z, D), same problem as the epigraph split"}
         s.set_mode(B.PS_POLARIZED)
 
+    # The TV problem with the constraint (Algorithm 3) on the same data and launch path:
+    # the gradient step replaces the data dual, grad replaces the SARA dictionary.
+    tvv = None
+    if rank == 0:
+        B.ps_set_tv_weights(s.h, [1e-3 * gamma * 3.0] * 4)
+        s.set_mode(B.PS_TV)
+        s.pd_iterate(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.pd_iterate(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_tv = ev0.elapsed_time(ev1) / args.steps
+        tvv = {"iters_per_s": 1000.0 / ms_tv, "ms_per_step": ms_tv,
+               "kernels_per_iteration": B.ps_kernels_per_iteration(s.h),
+               "note": "PS_TV: Algorithm 3 (TV prior, gradient step on the data term, polarization "
+                       "constraint by the epigraph split) on the same measurements"}
+        s.set_mode(B.PS_POLARIZED)
+
     batched = served = np_cmp = hyper = None
     if rank == 0 and world == 1 and not args.no_serve:
         np_cmp = np_comparison()
@@ -614,6 +633,7 @@ def run_own(args) -> None:
             "gpu_launches": launches,
             "e2e": e2e,
             "soc_variant": soc,
+            "tv_variant": tvv,
             "cpu_baseline": cpu,
             "batched": batched,
             "served": served,

@@ -58,17 +58,27 @@ enum {
   PS_POLARIZED = 0,      /* Algorithm 1 in full: S, Z, A, B, C, D */
   PS_NO_CONSTRAINT = 1,  /* S, A, B only, with P_U' (Stokes I >= 0) */
   PS_NNLS = 2,           /* S, B only, with P_U' and g = 0: the initialisation of Alg. 2 */
-  PS_SOC = 3             /* not in the paper: the problem of PS_POLARIZED with the polarization
+  PS_SOC = 3,            /* not in the paper: the problem of PS_POLARIZED with the polarization
                             constraint (Eq. pol_const, a second-order cone per pixel) given one
                             dual C under the identity, C = C~ - rho3 P_P(C~/rho3) with the
                             closed-form cone projection, instead of the epigraph split of
                             Section 4.3.1: S, A, B, C only (no Z, D; 32 bytes/pixel less) */
+  /* The TV problems of Section 4.4 (Algorithm 3, Eqs. Akiyama and Akiyama_2): data term
+   * 1/2 ||Y L^-1 - phi(S) L^-1||^2 by its gradient 1/2 phi^dagger(phi(S) - Y) (no B, no l2
+   * ball), sparsity prior sum_i mu_i ||grad S_i||_{2,1} (TV) or that plus sum_i nu_i
+   * ||S_i||_1 (l1 + TV), grad = periodic forward differences; weights from
+   * ps_set_tv_weights. The dual A of the prior lives in the SARA coefficient array:
+   * A_tv of map c in its planes 0 (x) and 1 (y), A_l1 in plane 2 (ps_get/set_state). */
+  PS_TV = 4,             /* TV with the polarization constraint: S, Z, A, C, D (steps 3-10) */
+  PS_TV_NC = 5,          /* TV without it: S, A only, with P_U' (Stokes I >= 0) */
+  PS_L1TV = 6,           /* l1 + TV with the constraint */
+  PS_L1TV_NC = 7         /* l1 + TV without it */
 };
 
 typedef struct {
   int32_t n;             /* image side: power of two, 16 <= n <= 2048 */
   int32_t levels;        /* wavelet levels, 1 <= levels, n divisible by 2^levels */
-  int32_t mode;          /* PS_POLARIZED | PS_NO_CONSTRAINT | PS_NNLS | PS_SOC */
+  int32_t mode;          /* PS_POLARIZED | PS_NO_CONSTRAINT | PS_NNLS | PS_SOC | PS_TV .. PS_L1TV_NC */
   int32_t literal_ball;  /* 0: l2-ball radius eps (Moreau reading of Alg. 1 step 8);
                             1: the printed radius eps / rho2 */
   int32_t kernel_width;  /* NUFFT interpolation width W: 5, 7 or 9; 0 => 7 */
@@ -145,9 +155,18 @@ ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter);
  * dual state is kept (warm start). delta > 0. */
 ps_status ps_reweight(ps_handle* h, double delta);
 
-/* Switch the problem variant (PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS, PS_SOC) keeping the
- * state; step sizes that were defaulted are recomputed for the new mode. */
+/* Switch the problem variant (PS_POLARIZED ... PS_L1TV_NC) keeping the state; step sizes
+ * that were defaulted are recomputed for the new mode. Switching between the SARA modes
+ * (0-3) and the TV modes (4-7) clears A (its layout differs). The TV modes' default tau is
+ * 0.99 / (||phi||^2 / 4 + rho1 ||Psi||^2 [+ rho3 with the constraint]), ||Psi||^2 = 8 (TV)
+ * or 9 (l1 + TV): the data gradient is Lipschitz with ||phi||^2 / 2. */
 ps_status ps_set_mode(ps_handle* h, int32_t mode);
+
+/* Weights of the TV modes: tv[i] = mu_i > 0 of ||grad S_i||_{2,1}, l1[i] = nu_i >= 0 of
+ * ||S_i||_1 (used by PS_L1TV and PS_L1TV_NC; may be null otherwise), i = I, Q, U, V
+ * (Section 4.4, the thresholds Lambda of Algorithm 3 step 6). PS_EINVAL on negative or
+ * non-finite values. */
+ps_status ps_set_tv_weights(ps_handle* h, const double* tv, const double* l1);
 
 /* Current Stokes maps S (4 x N floats). */
 ps_status ps_get_stokes(ps_handle* h, float* out, int32_t device_ptrs);

@@ -18,6 +18,7 @@ from . import _build
 
 PS_OK, PS_EINVAL, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINITE, PS_ESTATE = range(7)
 PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS, PS_SOC = 0, 1, 2, 3
+PS_TV, PS_TV_NC, PS_L1TV, PS_L1TV_NC = 4, 5, 6, 7
 STATUS_NAMES = {0: "PS_OK", 1: "PS_EINVAL", 2: "PS_ENOMEM", 3: "PS_ECUDA", 4: "PS_ETIMEOUT",
                 5: "PS_ENONFINITE", 6: "PS_ESTATE"}
 
@@ -63,6 +64,7 @@ _SIGS = {
     "ps_pd_iterate": (_I32, [_H, _I32]),
     "ps_reweight": (_I32, [_H, _F64]),
     "ps_set_mode": (_I32, [_H, _I32]),
+    "ps_set_tv_weights": (_I32, [_H, _P, _P]),
     "ps_get_stokes": (_I32, [_H, _P, _I32]),
     "ps_get_state": (_I32, [_H, ctypes.POINTER(ps_state_view)]),
     "ps_set_state": (_I32, [_H, ctypes.POINTER(ps_state_view)]),
@@ -193,6 +195,14 @@ def ps_reweight(h, delta: float) -> None:
 
 def ps_set_mode(h, mode: int) -> None:
     _check(h, lib().ps_set_mode(h, int(mode)))
+
+
+def ps_set_tv_weights(h, tv, l1=None) -> None:
+    """TV weights mu_i (and l1 weights nu_i) per Stokes map I, Q, U, V (Algorithm 3)."""
+    t = np.ascontiguousarray(np.asarray(tv, dtype=np.float64).reshape(4))
+    a = None if l1 is None else np.ascontiguousarray(np.asarray(l1, dtype=np.float64).reshape(4))
+    _check(h, lib().ps_set_tv_weights(h, ctypes.c_void_p(t.ctypes.data),
+                                      ctypes.c_void_p(a.ctypes.data) if a is not None else None))
 
 
 def ps_get_stokes(h, out) -> None:

@@ -165,6 +165,12 @@ static void set_default_steps(Handle* h) {
   double denom = h->rho2 * on;
   if (h->mode != PS_NNLS) denom += h->rho1;
   if (h->mode == PS_POLARIZED || h->mode == PS_SOC) denom += h->rho3;
+  if (ps::tv_mode(h->mode)) {
+    // Algorithm 3: the data gradient is Lipschitz with beta = ||phi||^2 / 2 (phi~ = phi L^-1,
+    // L L^H = 2 I); 1/tau - rho1 ||Psi||^2 - rho3 >= beta / 2, ||grad||^2 = 8, ||[Id; grad]||^2 = 9.
+    denom = on / 4.0 + h->rho1 * ((h->mode == PS_L1TV || h->mode == PS_L1TV_NC) ? 9.0 : 8.0);
+    if (ps::constrained_mode(h->mode)) denom += h->rho3;
+  }
   h->tau = c.tau > 0 ? c.tau : (denom > 0 ? 0.99 / denom : 0.99);
 }
 
@@ -191,7 +197,18 @@ static ps_status reset_state(Handle* h) {
 }
 
 // Psi A and phi^dagger(c_b R) of the current state.
+static cudaError_t nufft_gradient_chain(Handle* h, cudaEvent_t* ev);
 static ps_status compute_derived(Handle* h) {
+  if (ps::tv_mode(h->mode)) {   // Psi A = grad^T A (+ A_l1) and phi^dagger(Y - phi S) of the current state
+    CK(h, ps::tv_adjoint(h));
+    if (h->M > 0) {
+      CK(h, nufft_gradient_chain(h, nullptr));
+    } else {
+      CK(h, cudaMemsetAsync(h->Adj, 0, 4 * (size_t)h->N * sizeof(float), h->stream));
+    }
+    h->derived_valid = true;
+    return PS_OK;
+  }
   CK(h, ps::sara_synthesis(h, h->A, h->PsiA));
   if (h->M > 0) {
     CK(h, ps::nufft_grid(h, h->R, 1));
@@ -231,11 +248,60 @@ static cudaError_t nufft_chain(Handle* h, cudaEvent_t* ev) {
   return mark(PS_NSTAGES);
 }
 
+// Algorithm 3: the data-term gradient of the next primal step, at the new S:
+// Adj = phi^dagger(Y - phi(S)) (k_primal takes -Adj / 2). Stage events as in nufft_chain
+// (the ball stage is empty).
+static cudaError_t nufft_gradient_chain(Handle* h, cudaEvent_t* ev) {
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], h->stream) : cudaSuccess; };
+  cudaError_t e;
+  if ((e = mark(PS_STAGE_FWD_FFT)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_forward_grid(h, h->S)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_DEGRID)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_degrid(h, ps::DEG_RESID, h->vtmp)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_BALL)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_GRID)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_grid(h, h->vtmp, 0)) != cudaSuccess) return e;
+  if ((e = mark(PS_STAGE_ADJ_FFT)) != cudaSuccess) return e;
+  if (h->M > 0 && (e = ps::nufft_adjoint_image(h, h->Adj)) != cudaSuccess) return e;
+  return mark(PS_NSTAGES);
+}
+
+// Algorithm 3 steps 5-6 and the next Psi A.
+static cudaError_t tv_chain(Handle* h) {
+  cudaError_t e = ps::tv_dual(h);
+  if (e != cudaSuccess) return e;
+  return ps::tv_adjoint(h);
+}
+
 static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], h->stream) : cudaSuccess; };
   cudaError_t e;
   if ((e = mark(PS_STAGE_PRIMAL)) != cudaSuccess) return e;
   if ((e = ps::primal_sweep(h)) != cudaSuccess) return e;
+  if (ps::tv_mode(h->mode)) {
+    // The TV chain (sparsity duals, next Psi A) and the data-gradient chain (on the new S)
+    // read disjoint inputs and write disjoint buffers: concurrent branches as in Alg. 1.
+    if (ev || h->M == 0 || !h->aux) {
+      if ((e = mark(PS_STAGE_ANALYSIS)) != cudaSuccess) return e;
+      if ((e = ps::tv_dual(h)) != cudaSuccess) return e;
+      if ((e = mark(PS_STAGE_ANALYSIS_COARSE)) != cudaSuccess) return e;
+      if ((e = mark(PS_STAGE_SYNTHESIS_COARSE)) != cudaSuccess) return e;
+      if ((e = mark(PS_STAGE_SYNTHESIS)) != cudaSuccess) return e;
+      if ((e = ps::tv_adjoint(h)) != cudaSuccess) return e;
+      return nufft_gradient_chain(h, ev);
+    }
+    if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0)) != cudaSuccess) return e;
+    cudaStream_t main = h->stream;
+    h->stream = h->aux;
+    e = tv_chain(h);
+    cudaError_t e2 = cudaEventRecord(h->ev_join, h->aux);
+    h->stream = main;
+    if (e != cudaSuccess) return e;
+    if (e2 != cudaSuccess) return e2;
+    if ((e = nufft_gradient_chain(h, nullptr)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+  }
   const bool sara = (h->mode != PS_NNLS);
   if (ev || !sara || h->M == 0 || !h->aux) {
     if ((e = mark(PS_STAGE_ANALYSIS)) != cudaSuccess) return e;
@@ -303,7 +369,7 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
     return fail(nullptr, PS_EINVAL, "ps_create: n must be a power of two in [16, 2048]");
   if (L < 1 || (n % (1 << L)) != 0 || (n >> L) < 1)
     return fail(nullptr, PS_EINVAL, "ps_create: levels must satisfy 1 <= levels and n divisible by 2^levels");
-  if (cfg->mode < PS_POLARIZED || cfg->mode > PS_SOC) return fail(nullptr, PS_EINVAL, "ps_create: bad mode");
+  if (cfg->mode < PS_POLARIZED || cfg->mode > PS_L1TV_NC) return fail(nullptr, PS_EINVAL, "ps_create: bad mode");
   const int W = cfg->kernel_width == 0 ? 7 : cfg->kernel_width;
   if (W != 5 && W != 7 && W != 9) return fail(nullptr, PS_EINVAL, "ps_create: kernel_width must be 5, 7 or 9");
   if (cfg->tau < 0 || cfg->rho1 < 0 || cfg->rho2 < 0 || cfg->rho3 < 0)
@@ -794,11 +860,34 @@ ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_
 
 ps_status ps_set_mode(ps_handle* h, int32_t mode) {
   if (!h) return PS_EINVAL;
-  if (mode < PS_POLARIZED || mode > PS_SOC) return fail(h, PS_EINVAL, "set_mode: bad mode");
+  if (mode < PS_POLARIZED || mode > PS_L1TV_NC) return fail(h, PS_EINVAL, "set_mode: bad mode");
+  if (ps::tv_mode(mode) != ps::tv_mode(h->mode)) {   // A changes meaning: start it from zero
+    CK(h, cudaMemsetAsync(h->A, 0, 36 * (size_t)h->N * sizeof(float), h->stream));
+    h->derived_valid = false;
+  } else if (ps::tv_mode(mode) && mode != h->mode) {
+    h->derived_valid = false;                          // the l1 part of Psi A may change
+  }
   h->mode = mode;
   h->cfg.mode = mode;
   set_default_steps(h);
   drop_graph(h);
+  ++h->version;
+  return PS_OK;
+}
+
+ps_status ps_set_tv_weights(ps_handle* h, const double* tv, const double* l1) {
+  if (!h) return PS_EINVAL;
+  if (!tv) return fail(h, PS_EINVAL, "set_tv_weights: null TV weights");
+  for (int i = 0; i < 4; ++i) {
+    if (!(tv[i] >= 0) || !std::isfinite(tv[i])) return fail(h, PS_EINVAL, "set_tv_weights: weights must be >= 0");
+    if (l1 && (!(l1[i] >= 0) || !std::isfinite(l1[i])))
+      return fail(h, PS_EINVAL, "set_tv_weights: weights must be >= 0");
+  }
+  for (int i = 0; i < 4; ++i) {
+    h->tv_mu[i] = tv[i];
+    h->l1_mu[i] = l1 ? l1[i] : 0.0;
+  }
+  drop_graph(h);   // the weights are kernel arguments of the captured iteration
   ++h->version;
   return PS_OK;
 }
@@ -824,6 +913,7 @@ ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter) {
 ps_status ps_reweight(ps_handle* h, double delta) {
   if (!h) return PS_EINVAL;
   if (!(delta > 0) || !std::isfinite(delta)) return fail(h, PS_EINVAL, "reweight: delta must be > 0");
+  if (ps::tv_mode(h->mode)) return fail(h, PS_ESTATE, "reweight: the TV modes have no SARA weights");
   CK(h, ps::dirac_apply(h, h->S, nullptr, h->T, ps::SARA_REWEIGHT, 1.0f / 3.0f, (float)h->gamma, (float)delta));
   CK(h, ps::sara_analysis(h, h->S, nullptr, h->T, ps::SARA_REWEIGHT, 1.0f / 3.0f, (float)h->gamma, (float)delta));
   return PS_OK;
@@ -1162,6 +1252,7 @@ ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms) 
     st = pick(PS_TUNE_GRID, [&] { return ps::nufft_grid(h, h->R, 1); });
     if (st != PS_OK) return st;
   }
+  if (ps::tv_mode(h->mode)) h->derived_valid = false;   // the SARA synthesis timing wrote PsiA
   drop_graph(h);
   ++h->version;
   if (choices) std::memcpy(choices, h->tune, sizeof(h->tune));
@@ -1190,6 +1281,7 @@ ps_status ps_set_tuning(ps_handle* h, const int32_t* choices) {
 int32_t ps_kernels_per_iteration(const ps_handle* h) {
   if (!h) return 0;
   int k = 1;                                   // k_primal
+  if (ps::tv_mode(h->mode)) return k + 2 + (h->M > 0 ? 2 + 1 + 1 + 2 : 0);   // TV dual + adjoint, gradient chain
   if (h->mode != PS_NNLS) k += 2 * h->L;       // analysis + synthesis levels
   if (h->M > 0) k += 2 + 1 + 1 + 1 + 2;        // fwd rows/cols, degrid, block scale, grid, adj cols/rows
   return k;

@@ -54,6 +54,7 @@ struct Handle {
   std::string err;
   int n = 0, N = 0, L = 0, mode = PS_POLARIZED;
   double tau = 0, rho1 = 1, rho2 = 1, rho3 = 1, opnorm_sq = 0, gamma = 1;
+  double tv_mu[4] = {0, 0, 0, 0}, l1_mu[4] = {0, 0, 0, 0};   // TV and l1 weights (Algorithm 3)
   bool have_meas = false;
   bool derived_valid = false;     // PsiA and Adj hold Psi A and phi^dagger B of the current state
   int64_t iterations = 0;
@@ -129,6 +130,10 @@ cudaError_t nufft_forward_grid(Handle* h, const float* X);                 // X 
 cudaError_t nufft_degrid(Handle* h, int mode, float2* out);                // G -> visibilities
 cudaError_t nufft_grid(Handle* h, const float2* in, int use_block_scale);  // visibilities -> Acc
 cudaError_t nufft_row_weights(Handle* h);                                   // rec -> wrow (W <= 8)
+cudaError_t tv_dual(Handle* h);      // Algorithm 3 steps 5-6 on Xb -> A (TV layout)
+cudaError_t tv_adjoint(Handle* h);   // Psi A = grad^T A_tv (+ A_l1) -> PsiA
+__host__ __device__ inline bool tv_mode(int m) { return m >= PS_TV && m <= PS_L1TV_NC; }
+__host__ __device__ inline bool constrained_mode(int m) { return m == PS_POLARIZED || m == PS_SOC || m == PS_TV || m == PS_L1TV; }
 cudaError_t nufft_adjoint_image(Handle* h, float* out);                    // Acc -> 4 planes
 cudaError_t block_scales(Handle* h);                                        // chunk partials -> c_b
 

@@ -5,7 +5,9 @@
 // 9-12 (epigraph duals C, D through P_E1 and P_E2, Eqs. proj_e1 and
 // proj_e2_def) and the Dirac part of steps 5-6 (A_dirac = clamp(A + rho1 Xb/3,
 // +-gamma W)). In PS_SOC mode the epigraph steps are replaced by the direct
-// cone dual C = C~ - rho3 P_P(C~ / rho3) (Z and D are not touched). It also writes per-CTA FP64 partials of ||S^(k+1) - S^(k)||^2 and
+// cone dual C = C~ - rho3 P_P(C~ / rho3) (Z and D are not touched). In the TV modes
+// (Algorithm 3) the same sweep takes the data gradient -phi^dagger(Y - phi S) / 2 in place
+// of phi^dagger B, Psi A = grad^T A from k_tv_adj, and skips the SARA Dirac part. It also writes per-CTA FP64 partials of ||S^(k+1) - S^(k)||^2 and
 // ||S^(k)||^2 per map for the relative-change rule (Eq. stop_crit).
 #include <cuda_runtime.h>
 
@@ -81,17 +83,20 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
     for (int c = 0; c < 4; ++c) {
       const size_t o = (size_t)c * N + i;
       float4 g = ld4(Adj + o);
+      // TV modes (Algorithm 3 step 3): Adj holds phi^dagger(Y - phi(S)), so the data
+      // gradient 1/2 phi^dagger(phi(S) - Y) is -Adj / 2.
+      if (tv_mode(mode)) g = make_float4(-0.5f * g.x, -0.5f * g.y, -0.5f * g.z, -0.5f * g.w);
       if (mode != PS_NNLS) {
         const float4 p = ld4(PsiA + o);
         g = make_float4(g.x + p.x, g.y + p.y, g.z + p.z, g.w + p.w);
       }
-      if (mode == PS_POLARIZED || mode == PS_SOC) {
+      if (constrained_mode(mode)) {
         const float4 q = ld4(C + o);
         g = make_float4(g.x + q.x, g.y + q.y, g.z + q.z, g.w + q.w);
       }
       const float4 so = ld4(S + o);
       float4 sn = make_float4(so.x - tau * g.x, so.y - tau * g.y, so.z - tau * g.z, so.w - tau * g.w);   // step 3
-      if ((mode == PS_NO_CONSTRAINT || mode == PS_NNLS) && c == 0)                                    // P_U'
+      if (!constrained_mode(mode) && c == 0)                                                          // P_U'
         sn = make_float4(fmaxf(sn.x, 0.f), fmaxf(sn.y, 0.f), fmaxf(sn.z, 0.f), fmaxf(sn.w, 0.f));
       xb[c] = make_float4(2.f * sn.x - so.x, 2.f * sn.y - so.y, 2.f * sn.z - so.z, 2.f * sn.w - so.w);
       dss[c] += (sn.x - so.x) * (sn.x - so.x) + (sn.y - so.y) * (sn.y - so.y) + (sn.z - so.z) * (sn.z - so.z) +
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
       ss[c] += so.x * so.x + so.y * so.y + so.z * so.z + so.w * so.w;
       st4(S + o, sn);
       st4(Xb + o, xb[c]);
-      if (mode != PS_NNLS) {                                            // Dirac part of steps 5-6
+      if (mode != PS_NNLS && !tv_mode(mode)) {                          // Dirac part of steps 5-6
         const size_t ao = (size_t)c * cstride + i;
         const float4 t = ld4(T + ao), a = ld4(A + ao);
         st4(A + ao, make_float4(fminf(fmaxf(fmaf(r1_3, xb[c].x, a.x), -t.x), t.x),
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
                                 fminf(fmaxf(fmaf(r1_3, xb[c].w, a.w), -t.w), t.w)));
       }
     }
-    if (mode == PS_POLARIZED) {
+    if (mode == PS_POLARIZED || mode == PS_TV || mode == PS_L1TV) {   // epigraph split (Alg. 1 / Alg. 3)
       const float4 z1o = ld4(Z + i), z2o = ld4(Z + (size_t)N + i);
       const float4 d1o = ld4(D + i), d2o = ld4(D + (size_t)N + i);
       float4 c0 = ld4(C + i), c1 = ld4(C + (size_t)N + i), c2 = ld4(C + 2 * (size_t)N + i),

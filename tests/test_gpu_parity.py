@@ -298,3 +298,52 @@ def test_literal_ball_radius_matches_oracle():
         assert rel_err(got[k], ref[k]) <= 2e-5 * 3, k
     scale = float(np.abs(st32["B"]).max())
     assert np.abs(got["B"]).max() <= 1e-6 * scale and np.abs(ref["B"]).max() <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("mode", [B.PS_TV, B.PS_TV_NC, B.PS_L1TV, B.PS_L1TV_NC])
+@pytest.mark.parametrize("n,M,coverage", [(32, 1500, "tracks"), (16, 333, "random")])
+def test_tv_iterations_from_random_state_match_oracle(mode, n, M, coverage):
+    """Algorithm 3 (TV and l1 + TV, with and without the constraint) from a random state
+    against the FP64 oracle, with weights that make the dual clamps active."""
+    from oracle import tv as otv
+    pb = make_problem(n, M, 2, 2, seed=12, coverage=coverage)
+    uv, w64, Y = pb["uv"], pb["w"].astype(np.float64), pb["Y"].astype(np.complex128)
+    on = meas.op_norm_sq_lanczos(uv, w64, n)
+    mu, nu = [0.05, 0.03, 0.03, 0.02], [0.03, 0.02, 0.02, 0.01]
+    p = otv.step_sizes(on, mode, mu, nu)
+    rng = np.random.default_rng(23)
+    ref = otv.zero_state(n)
+    for k in ("S", "Atv", "Al1", "C", "Z", "D"):
+        ref[k] = 0.05 * rng.normal(size=ref[k].shape)
+    if mode not in otv.CONSTRAINED:
+        for k in ("Z", "C", "D"):
+            ref[k][:] = 0
+    if mode not in otv.WITH_L1:
+        ref["Al1"][:] = 0
+    ref = {k: v.astype(np.float32).astype(np.float64) for k, v in ref.items()}
+    A = np.zeros((4, 9, n, n), np.float32)
+    A[:, 0:2] = ref["Atv"]
+    A[:, 2] = ref["Al1"]
+    st32 = {"S": ref["S"].astype(np.float32), "Z": ref["Z"].astype(np.float32), "A": A,
+            "B": np.zeros((M, 4), np.complex64), "C": ref["C"].astype(np.float32),
+            "D": ref["D"].astype(np.float32)}
+    s = PolarizedSARA(n, 2, mode=mode, tau=p.tau, rho1=p.rho1, rho3=p.rho3)
+    with s:
+        s.set_measurements(pb["uv"], pb["Y"], pb["w"], pb["off"], pb["eps"])
+        B.ps_set_tv_weights(s.h, mu, nu)
+        s.set_state(st32)
+        done = 0
+        for k_iter in (1, 3):
+            s.pd_iterate(k_iter)
+            for _ in range(k_iter):
+                ref = otv.tv_iteration(ref, uv, w64, Y, p, mode)
+            done += k_iter
+            got = s.get_state()
+            pairs = [("S", got["S"], ref["S"]), ("Atv", got["A"][:, 0:2], ref["Atv"])]
+            if mode in otv.WITH_L1:
+                pairs.append(("Al1", got["A"][:, 2], ref["Al1"]))
+            if mode in otv.CONSTRAINED:
+                pairs += [("Z", got["Z"], ref["Z"]), ("C", got["C"], ref["C"]), ("D", got["D"], ref["D"])]
+            for name, g, r in pairs:
+                err = rel_err(g, r)
+                assert err <= 2e-5 * done, (done, name, err)
