@@ -157,9 +157,10 @@ ps_status ps_reweight(ps_handle* h, double delta);
 
 /* Switch the problem variant (PS_POLARIZED ... PS_L1TV_NC) keeping the state; step sizes
  * that were defaulted are recomputed for the new mode. Switching between the SARA modes
- * (0-3) and the TV modes (4-7) clears A (its layout differs). The TV modes' default tau is
- * 0.99 / (||phi||^2 / 4 + rho1 ||Psi||^2 [+ rho3 with the constraint]), ||Psi||^2 = 8 (TV)
- * or 9 (l1 + TV): the data gradient is Lipschitz with ||phi||^2 / 2. */
+ * (0-3) and the TV modes (4-7) clears A (its layout differs). In the TV modes the data
+ * gradient is Lipschitz with beta = ||phi||^2 / 2; the defaults are rho1 = beta / (2 ||Psi||^2),
+ * rho3 = beta / 2 and tau = 0.99 / (beta / 2 + rho1 ||Psi||^2 [+ rho3 with the constraint]),
+ * ||Psi||^2 = 8 (TV) or 9 (l1 + TV). */
 ps_status ps_set_mode(ps_handle* h, int32_t mode);
 
 /* Weights of the TV modes: tv[i] = mu_i > 0 of ||grad S_i||_{2,1}, l1[i] = nu_i >= 0 of

@@ -20,9 +20,12 @@ Readings (the paper leaves these open):
   * The data gradient: phi~^dagger(phi~(S) - Y~) = Re(Phi^H (Phi S - Y L^-1)), and
     because L L^H = 2 I this equals 1/2 phi^dagger(phi(S) - Y).
   * Step sizes: the smooth term's gradient is Lipschitz with beta = ||phi~||^2 =
-    ||phi||^2 / 2; with rho1 = rho3 = 1, tau = 0.99 / (beta / 2 + rho1 ||Psi||^2
-    [+ rho3]) meets the forward-backward primal-dual condition 1/tau - sum rho_i
-    ||K_i||^2 >= beta / 2. ||Psi||^2 = 8 (TV) or 9 (l1 + TV: Id stacked on grad).
+    ||phi||^2 / 2, and tau = 0.99 / (beta / 2 + rho1 ||Psi||^2 [+ rho3]) meets the
+    forward-backward primal-dual condition 1/tau - sum rho_i ||K_i||^2 >= beta / 2,
+    ||Psi||^2 = 8 (TV) or 9 (l1 + TV: Id stacked on grad). The dual steps are balanced
+    against beta, rho1 ||Psi||^2 = rho3 = beta / 2, so that the duals move on the data
+    term's scale (with rho = 1 they move ~||phi||^2 times slower than the primal and the
+    constraint takes far longer to act).
   * Modes: TV and L1TV carry the constraint (steps 3-12 of Algorithm 3: S with P_U,
     Z, and the epigraph duals C, D as in Algorithm 1); TV_NC and L1TV_NC are the
     problems without it (steps 3, 5, 6 only, S with P_U': Stokes I >= 0).
@@ -83,10 +86,13 @@ class TVParams:
     nu: np.ndarray            # (4,) l1 weights per Stokes map (l1 + TV only)
 
 
-def step_sizes(opnorm_sq: float, mode: int, mu, nu=(0.0, 0.0, 0.0, 0.0), rho1: float = 1.0,
-               rho3: float = 1.0, safety: float = 0.99) -> TVParams:
+def step_sizes(opnorm_sq: float, mode: int, mu, nu=(0.0, 0.0, 0.0, 0.0), rho1: float | None = None,
+               rho3: float | None = None, safety: float = 0.99) -> TVParams:
     beta = opnorm_sq / 2.0
-    denom = beta / 2.0 + rho1 * (9.0 if mode in WITH_L1 else 8.0)
+    npsi = 9.0 if mode in WITH_L1 else 8.0
+    rho1 = beta / (2.0 * npsi) if rho1 is None else rho1
+    rho3 = beta / 2.0 if rho3 is None else rho3
+    denom = beta / 2.0 + rho1 * npsi
     if mode in CONSTRAINED:
         denom += rho3
     return TVParams(tau=safety / denom, rho1=rho1, rho3=rho3, mu=np.asarray(mu, float), nu=np.asarray(nu, float))

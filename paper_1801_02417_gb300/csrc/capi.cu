@@ -168,7 +168,11 @@ static void set_default_steps(Handle* h) {
   if (ps::tv_mode(h->mode)) {
     // Algorithm 3: the data gradient is Lipschitz with beta = ||phi||^2 / 2 (phi~ = phi L^-1,
     // L L^H = 2 I); 1/tau - rho1 ||Psi||^2 - rho3 >= beta / 2, ||grad||^2 = 8, ||[Id; grad]||^2 = 9.
-    denom = on / 4.0 + h->rho1 * ((h->mode == PS_L1TV || h->mode == PS_L1TV_NC) ? 9.0 : 8.0);
+    // Default dual steps balanced against beta: rho1 ||Psi||^2 = rho3 = beta / 2.
+    const double beta = on / 2.0, npsi = (h->mode == PS_L1TV || h->mode == PS_L1TV_NC) ? 9.0 : 8.0;
+    if (!(c.rho1 > 0) && beta > 0) h->rho1 = beta / (2.0 * npsi);
+    if (!(c.rho3 > 0) && beta > 0) h->rho3 = beta / 2.0;
+    denom = beta / 2.0 + h->rho1 * npsi;
     if (ps::constrained_mode(h->mode)) denom += h->rho3;
   }
   h->tau = c.tau > 0 ? c.tau : (denom > 0 ? 0.99 / denom : 0.99);

@@ -125,11 +125,12 @@ def test_converges_to_a_feasible_lower_objective(mode):
         assert gap.max() <= 2e-3 * np.abs(S).max()
     else:
         assert S[0].min() >= 0.0
-    # The TV dual stays in its discs: |A_tv| <= mu per pixel and map.
+    # The TV dual stays in its discs: |A_tv| <= mu per pixel and map (up to the rounding of
+    # A~ - rho1 prox(A~ / rho1), whose terms are ~rho1 |grad Xb| >> mu).
     norm = np.sqrt(np.sum(st["Atv"] ** 2, axis=1))
-    assert np.all(norm <= p.mu[:, None, None] * (1 + 1e-12))
+    assert np.all(norm <= p.mu[:, None, None] * (1 + 1e-8))
     if mode in tv.WITH_L1:
-        assert np.all(np.abs(st["Al1"]) <= p.nu[:, None, None] * (1 + 1e-12))
+        assert np.all(np.abs(st["Al1"]) <= p.nu[:, None, None] * (1 + 1e-8))
 
 
 def test_step_sizes_meet_the_condition():
