@@ -82,22 +82,46 @@ typedef struct {
   int32_t literal_ball;  /* 0: l2-ball radius eps (Moreau reading of Alg. 1 step 8);
                             1: the printed radius eps / rho2 */
   int32_t kernel_width;  /* NUFFT interpolation width W: 5, 7 or 9; 0 => 7 */
-  int32_t reserved;
+  int32_t reserved;      /* 0 */
   double tau, rho1, rho2, rho3;  /* step sizes; 0 => default of Section 4.3.3:
                                     rho1 = rho3 = 1, rho2 = 1/||phi||^2,
                                     tau = 0.99 / (sum of rho_i ||K_i||^2 in the mode) */
+  double alpha;          /* NUFFT oversampling factor of the grid K = alpha n (Section 5.1 leaves it
+                            open); 0 => 2, the only value accepted */
+  double gamma;          /* gamma of Algorithm 1 step 6 (Section 4.2: it only affects the speed of
+                            convergence); 0 => 1e-3 max|Psi^dagger phi^dagger Y| / ||phi||^2, computed by
+                            ps_set_measurements (image units: phi^dagger phi peaks at ||phi||^2) */
+  double noise_sigma;    /* sigma of the noise E (variance sigma^2 / 2 per real and imaginary part);
+                            used only when ps_set_measurements receives eps = NULL, for the chi^2
+                            bound of Section 5.1 */
+  double rel_tol;        /* epsilon of Eq. stop_crit (relative change per map); 0 => 1e-5 */
+  double resid_tol;      /* vartheta of Section 5.5: ||phi(S) - Y||_b <= (1 + vartheta) eps_b; 0 => 5e-3 */
+  double np_tol;         /* varrho of Section 5.5: N_p <= varrho, in percent of the pixels; 0 => 0.5 */
+  double zeta_sigma;     /* zeta = zeta_sigma x rms of the Stokes I residual image (Section 5.2); 0 => 3 */
 } ps_config;
+
+/* Criteria of the stopping rule of Section 5.5 (bits of ps_stats.stop_flags). */
+enum {
+  PS_STOP_REL = 1,     /* max_i ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| <= rel_tol (Eq. stop_crit) */
+  PS_STOP_RESID = 2,   /* ||phi(S) - Y||_b <= (1 + resid_tol) eps_b for every block */
+  PS_STOP_NP = 4       /* N_p = 100 violations / N <= np_tol */
+};
 
 typedef struct {
   int32_t nblocks;          /* number of l2 blocks the next fields describe */
-  int32_t reserved;
+  int32_t stop_flags;       /* out: PS_STOP_* criteria met (criteria that do not apply in the mode count
+                               as met: the residual rule in the TV modes, which have no l2 ball, and the
+                               N_p rule in the modes without the polarization constraint) */
   double* block_residual;   /* out, nblocks entries (may be NULL): ||phi(S) - Y||_2 per block */
-  double rel_change[4];     /* ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| of the last iteration (Eq. stop_crit) */
+  double rel_change[4];     /* ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| of the last iteration (Eq. stop_crit),
+                               0 for a map that stayed zero, +inf for a map that left zero */
   double zeta;              /* violation threshold used (Section 5.2) */
   int64_t violations;       /* pixels with -I + ||(Q,U,V)|| > zeta */
   int64_t violations_raw;   /* pixels with -I + ||(Q,U,V)|| > 0 */
   double weighted_l1;       /* sum |T .* Psi^dagger S| (gamma ||Psi^dagger S||_{W,1}) */
   int64_t iterations;       /* iterations run on this handle */
+  int32_t converged;        /* out: 1 when every PS_STOP_* criterion holds (Section 5.5), else 0 */
+  int32_t reserved;
 } ps_stats;
 
 /* Primal and dual state of Algorithm 1 (the warm start Algorithm 2 passes on).
@@ -130,25 +154,38 @@ const char* ps_last_error(const ps_handle* h);
  *   weights        M float32 per-row weights w_m >= 0 (phi = diag(w) F ...), NULL = 1
  *   nblocks        number of l2 blocks (>= 1 when M > 0)
  *   block_offsets  nblocks+1 int64, increasing, [0] = 0, [nblocks] = M
- *   eps            nblocks float64 radii eps_b > 0 (e.g. the chi^2 bound of Section 5.1)
+ *   eps            nblocks float64 radii eps_b > 0, or NULL: the chi^2 bound of Section 5.1 from
+ *                  cfg.noise_sigma, eps_b^2 = (8 M_b + 2 sqrt(16 M_b)) sigma^2 / 2 (8 M_b real degrees
+ *                  of freedom of variance sigma^2 / 2, two standard deviations above the mean;
+ *                  PS_EINVAL if noise_sigma <= 0)
  *   device_ptrs    for uv, vis, weights (block_offsets and eps are host arrays)
- * Sorts the rows by interpolation tile, estimates ||phi||^2 by Lanczos iterations
- * (FP64 reductions on the device), sets the default step sizes, and resets the
- * state to zero. */
+ * Sorts the rows by interpolation tile, estimates ||phi||^2 by Lanczos iterations,
+ * sets the default step sizes and (cfg.gamma = 0) the default gamma, fills the
+ * thresholds with gamma W, W = 1, and resets the state to zero.
+ * Precision: the Lanczos vectors and the operator products are FP32, the Lanczos
+ * coefficients and their reductions FP64 (the estimate agrees with an FP64 Lanczos
+ * within 1e-5 relative). The per-block l2 norms of step 8 and of the stopping rule
+ * accumulate in FP64 across warps and CTAs; within one warp (at most 32 rows) the
+ * partial sum is FP32. Both are departures from an all-FP64 reduction, bounded by
+ * the per-operator tolerance. */
 ps_status ps_set_measurements(ps_handle* h, int64_t M, const double* uv, const float* vis,
                               const float* weights, int32_t nblocks, const int64_t* block_offsets,
                               const double* eps, int32_t device_ptrs);
 
 /* Soft-threshold sizes gamma W of Algorithm 1 step 6 (W >= 0: 4 x 9 x N floats in
- * the coefficient layout; NULL = all ones). gamma > 0. */
+ * the coefficient layout; NULL = all ones). gamma > 0, or 0 for the handle's gamma
+ * (cfg.gamma, else the default computed by ps_set_measurements). */
 ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_t device_ptrs);
 
 /* Current soft-threshold sizes gamma W (4 x 9 x N floats, coefficient layout). */
 ps_status ps_get_sara_weights(ps_handle* h, float* out, int32_t device_ptrs);
 
 /* Run n_iter iterations of Algorithm 1 (steps 3-12) in the handle's mode.
- * Asynchronous on the handle's stream (a CUDA graph of one iteration is replayed). */
-ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter);
+ * Asynchronous on the handle's stream (a CUDA graph of one iteration is replayed)
+ * when `stats` is NULL. With `stats`, the call then computes the stopping-rule
+ * statistics of the new state as ps_compute_stats does with the handle's zeta_sigma
+ * (synchronises; PS_ENONFINITE if the state holds a NaN or infinity). */
+ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter, ps_stats* stats);
 
 /* Reweighting of Algorithm 2 (Eq. weights): W = delta / (delta + |Psi^dagger S|),
  * thresholds gamma W with the gamma of the last ps_set_sara_weights. All primal and
@@ -176,14 +213,23 @@ ps_status ps_get_stokes(ps_handle* h, float* out, int32_t device_ptrs);
 ps_status ps_get_state(ps_handle* h, const ps_state_view* view);
 ps_status ps_set_state(ps_handle* h, const ps_state_view* view);
 
+/* The handle's configuration with every default resolved: kernel_width, alpha and the
+ * stopping tolerances as used, mode the current mode, and gamma the handle's gamma
+ * (cfg.gamma, else the default that ps_set_measurements computed; 1 before it). */
+ps_status ps_get_config(const ps_handle* h, ps_config* out);
+
 /* Step sizes and the Lanczos estimate of ||phi||_sp^2 (Section 4.3.3). */
 ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, double* rho3,
                         double* opnorm_sq);
 
 /* Stopping-rule statistics of Section 5.5 for the current S: per-block residual
  * norms, relative change of the last iteration, violation count N_p with
- * zeta = zeta_sigma * rms(Stokes I residual image) / PSF peak (Section 5.2),
- * and the weighted l1 objective. Synchronises the stream. */
+ * zeta = zeta_sigma * rms(Stokes I residual image) / PSF peak (Section 5.2; zeta_sigma
+ * <= 0 takes the handle's), the weighted l1 objective, and which criteria of the
+ * stopping rule hold with the handle's rel_tol, resid_tol and np_tol (stop_flags,
+ * converged). The FP64 sums of the relative change also test the state: a NaN or an
+ * infinity in S (which any non-finite dual reaches within one iteration) returns
+ * PS_ENONFINITE. Synchronises the stream. */
 ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out);
 
 /* Operators of the method on caller data, using the handle's measurement set:
@@ -226,7 +272,7 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms);
 /* Number of kernel launches in one iteration of the handle's current mode. */
 int32_t ps_kernels_per_iteration(const ps_handle* h);
 
-/* Allocation-free variant of ps_apply_psi: S = Psi A (Section 4.1 synthesis) for
+/* Allocation-free variant of ps_apply_psi: S = Psi A, the SARA synthesis, for
  * callers that cannot call cudaMalloc, such as code whose device memory is all
  * owned by another allocator (a framework's caching allocator or a fixed
  * pre-reserved pool) or that must not risk an allocation failing or stalling
@@ -243,10 +289,30 @@ int32_t ps_kernels_per_iteration(const ps_handle* h);
  * call before capturing a stream. All calls share the one array and leave their
  * intermediate values in it; it needs no clearing, but calls that overlap on the
  * GPU (different streams, or different host threads on the same device) race on it
- * and must be serialised by the caller. Pointers must be 16-byte aligned; sizes
- * beyond the limit return PS_EINVAL with a message in ps_last_error(NULL).
- * Asynchronous: the result is ready when the stream is synchronised. */
+ * and must be serialised by the caller. A and S must be 16-byte aligned pointers to
+ * device (or managed) memory of the current device, else PS_EINVAL; sizes beyond the
+ * limit return PS_EINVAL with a message in ps_last_error(NULL).
+ * Asynchronous: the result is ready when the stream is synchronised. If a bounded
+ * in-kernel wait for a bulk copy gives up, the tiles it served are left unwritten and
+ * a device flag (cleared at the start of every call) is raised: ps_static_status
+ * reports it. */
 ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, int32_t levels, void* cuda_stream);
+
+/* Status of the last ps_apply_psi_static call on the current device: synchronises
+ * `cuda_stream` (NULL: the legacy default stream), then returns PS_ETIMEOUT if one of
+ * that call's bounded waits gave up (its S is then incomplete), else PS_OK. Allocates
+ * nothing. Like ps_apply_psi_static, the paper has no counterpart of it. */
+ps_status ps_static_status(void* cuda_stream);
+
+/* Test hook of the failure path of the bounded in-kernel waits: the number of
+ * polls a kernel makes on a bulk-copy barrier before it gives up, raises the error
+ * flag that the next synchronising call reports as PS_ETIMEOUT, lets the copies in
+ * flight land (a second wait with the full budget) and leaves its tile unwritten.
+ * polls = 0 gives up at the first wait (deterministically); polls < 0 restores the
+ * default (2^22). Applies to every handle and to ps_apply_psi_static on the current
+ * device; call it with no kernel of this library in flight. No counterpart in the
+ * paper. */
+ps_status ps_debug_set_wait_polls(int32_t polls);
 
 /* Replace the measurements Y of the current coverage (same rows, same caller
  * order, same blocks and radii) without re-sorting or re-estimating ||phi||: for a
@@ -254,8 +320,10 @@ ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, int32_t level
 ps_status ps_set_visibilities(ps_handle* h, const float* vis, int32_t device_ptrs);
 
 /* Relative change ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| of the last iteration for the
- * four maps (Eq. stop_crit), from FP64 partials the iteration already wrote; cheaper
- * than ps_compute_stats. Synchronises the handle's stream. */
+ * four maps (Eq. stop_crit; 0 for a map that stayed zero, +inf for one that left zero),
+ * from FP64 partials the iteration already wrote; cheaper than ps_compute_stats.
+ * PS_ENONFINITE when those sums are not finite (a NaN or infinity in S).
+ * Synchronises the handle's stream. */
 ps_status ps_get_rel_change(ps_handle* h, double* out4);
 
 /* max_j |[Psi^dagger S]_j| over all four maps (FP32 values, exact maximum): the scale

@@ -157,16 +157,37 @@ def residual_norms(S: np.ndarray, prob: Problem) -> np.ndarray:
 
 
 def relative_change(S_new: np.ndarray, S_old: np.ndarray) -> np.ndarray:
-    """Per-map ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| (Eq. stop_crit); inf where ||S_i^(k)|| = 0."""
+    """Per-map ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| (Eq. stop_crit).
+
+    Where ||S_i^(k)|| = 0: 0 if the map stays zero (V in the paper's data), inf if it moves.
+    """
     num = np.sqrt(np.sum((S_new - S_old) ** 2, axis=(1, 2)))
     den = np.sqrt(np.sum(S_old ** 2, axis=(1, 2)))
-    return np.where(den > 0, num / np.where(den > 0, den, 1.0), np.inf)
+    return np.where(den > 0, num / np.where(den > 0, den, 1.0), np.where(num > 0, np.inf, 0.0))
 
 
 def violation_count(S: np.ndarray, zeta: float) -> int:
     """Pixels of the polarization error image p (Section 5.2) above zeta: -I + ||(Q,U,V)|| > zeta."""
     pv = -S[0] + np.sqrt(S[1] ** 2 + S[2] ** 2 + S[3] ** 2)
     return int(np.count_nonzero(pv > zeta))
+
+
+def stop_rule(S_new: np.ndarray, S_old: np.ndarray, prob: Problem, rel_tol: float = 1e-5,
+              resid_tol: float = 5e-3, np_tol: float = 0.5, zeta_sigma: float = 3.0,
+              constrained: bool = True) -> dict:
+    """The stopping rule of Section 5.5 after the iteration S_old -> S_new.
+
+    rel: max over the maps of the relative change (Eq. stop_crit) <= rel_tol; the paper
+    takes i = 1..3 because its V is zero, and all four maps are taken here (a map that
+    stays zero contributes 0). resid: ||phi(S) - Y||_b <= (1 + vartheta) eps_b for every
+    block. np: with the polarization constraint, N_p = 100 * (pixels above zeta) / N <= varrho
+    (percent, Section 5.2). converged: all three.
+    """
+    rel = bool(np.max(relative_change(S_new, S_old)) <= rel_tol)
+    resid = bool(np.all(residual_norms(S_new, prob) <= (1.0 + resid_tol) * prob.eps))
+    n_p = 100.0 * violation_count(S_new, zeta_threshold(S_new, prob, zeta_sigma)) / S_new[0].size
+    np_ok = (not constrained) or n_p <= np_tol
+    return {"rel": rel, "resid": resid, "np": np_ok, "N_p": n_p, "converged": rel and resid and np_ok}
 
 
 def zeta_threshold(S: np.ndarray, prob: Problem, zeta_sigma: float = 3.0) -> float:

@@ -19,6 +19,7 @@ from . import _build
 PS_OK, PS_EINVAL, PS_ENOMEM, PS_ECUDA, PS_ETIMEOUT, PS_ENONFINITE, PS_ESTATE = range(7)
 PS_POLARIZED, PS_NO_CONSTRAINT, PS_NNLS, PS_SOC = 0, 1, 2, 3
 PS_TV, PS_TV_NC, PS_L1TV, PS_L1TV_NC = 4, 5, 6, 7
+PS_STOP_REL, PS_STOP_RESID, PS_STOP_NP = 1, 2, 4
 STATUS_NAMES = {0: "PS_OK", 1: "PS_EINVAL", 2: "PS_ENOMEM", 3: "PS_ECUDA", 4: "PS_ETIMEOUT",
                 5: "PS_ENONFINITE", 6: "PS_ESTATE"}
 
@@ -33,14 +34,17 @@ class ps_config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("levels", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("literal_ball", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("tau", ctypes.c_double), ("rho1", ctypes.c_double),
-                ("rho2", ctypes.c_double), ("rho3", ctypes.c_double)]
+                ("rho2", ctypes.c_double), ("rho3", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("noise_sigma", ctypes.c_double), ("rel_tol", ctypes.c_double),
+                ("resid_tol", ctypes.c_double), ("np_tol", ctypes.c_double), ("zeta_sigma", ctypes.c_double)]
 
 
 class ps_stats(ctypes.Structure):
-    _fields_ = [("nblocks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("nblocks", ctypes.c_int32), ("stop_flags", ctypes.c_int32),
                 ("block_residual", ctypes.POINTER(ctypes.c_double)), ("rel_change", ctypes.c_double * 4),
                 ("zeta", ctypes.c_double), ("violations", ctypes.c_int64), ("violations_raw", ctypes.c_int64),
-                ("weighted_l1", ctypes.c_double), ("iterations", ctypes.c_int64)]
+                ("weighted_l1", ctypes.c_double), ("iterations", ctypes.c_int64), ("converged", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ps_state_view(ctypes.Structure):
@@ -61,7 +65,7 @@ _SIGS = {
     "ps_set_measurements": (_I32, [_H, _I64, _P, _P, _P, _I32, _P, _P, _I32]),
     "ps_set_sara_weights": (_I32, [_H, _P, _F64, _I32]),
     "ps_get_sara_weights": (_I32, [_H, _P, _I32]),
-    "ps_pd_iterate": (_I32, [_H, _I32]),
+    "ps_pd_iterate": (_I32, [_H, _I32, ctypes.POINTER(ps_stats)]),
     "ps_reweight": (_I32, [_H, _F64]),
     "ps_set_mode": (_I32, [_H, _I32]),
     "ps_set_tv_weights": (_I32, [_H, _P, _P]),
@@ -69,6 +73,7 @@ _SIGS = {
     "ps_get_state": (_I32, [_H, ctypes.POINTER(ps_state_view)]),
     "ps_set_state": (_I32, [_H, ctypes.POINTER(ps_state_view)]),
     "ps_get_params": (_I32, [_H] + [ctypes.POINTER(_F64)] * 5),
+    "ps_get_config": (_I32, [_H, ctypes.POINTER(ps_config)]),
     "ps_compute_stats": (_I32, [_H, _F64, ctypes.POINTER(ps_stats)]),
     "ps_apply_phi": (_I32, [_H, _P, _P, _I32]),
     "ps_apply_phi_adjoint": (_I32, [_H, _P, _P, _I32]),
@@ -76,6 +81,8 @@ _SIGS = {
     "ps_apply_psi": (_I32, [_H, _P, _P, _I32]),
     "ps_wavelet_filters": (_I32, [_P]),
     "ps_apply_psi_static": (_I32, [_P, _P, _I32, _I32, _P]),
+    "ps_static_status": (_I32, [_P]),
+    "ps_debug_set_wait_polls": (_I32, [_I32]),
     "ps_set_visibilities": (_I32, [_H, _P, _I32]),
     "ps_get_rel_change": (_I32, [_H, _P]),
     "ps_max_abs_analysis": (_I32, [_H, ctypes.POINTER(_F64)]),
@@ -162,17 +169,19 @@ def ps_last_error(h) -> str:
 
 
 def ps_set_measurements(h, uv, vis, weights, block_offsets, eps) -> None:
+    """eps None: the chi^2 radii from the handle's noise_sigma."""
     puv, d1, k1 = _arg(uv, np.float64)
     pv, d2, k2 = _arg(vis, np.complex64)
     pw, d3, k3 = _arg(weights, np.float32)
     off = np.ascontiguousarray(block_offsets, dtype=np.int64)
-    e = np.ascontiguousarray(eps, dtype=np.float64)
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
     dev = d1 or d2 or d3
     if weights is not None and d3 != dev or d1 != d2:
         raise ValueError("uv, vis and weights must all be host arrays or all device tensors")
     M = int(uv.shape[0])
-    _check(h, lib().ps_set_measurements(h, M, puv, pv, pw, len(e), ctypes.c_void_p(off.ctypes.data),
-                                        ctypes.c_void_p(e.ctypes.data), dev))
+    nb = len(off) - 1 if e is None else len(e)
+    _check(h, lib().ps_set_measurements(h, M, puv, pv, pw, nb, ctypes.c_void_p(off.ctypes.data),
+                                        None if e is None else ctypes.c_void_p(e.ctypes.data), dev))
 
 
 def ps_set_sara_weights(h, W, gamma: float) -> None:
@@ -185,8 +194,15 @@ def ps_get_sara_weights(h, out) -> None:
     _check(h, lib().ps_get_sara_weights(h, p, d))
 
 
-def ps_pd_iterate(h, n_iter: int) -> None:
-    _check(h, lib().ps_pd_iterate(h, int(n_iter)))
+def ps_pd_iterate(h, n_iter: int, stats_nblocks: int | None = None):
+    """n_iter iterations; with stats_nblocks (the handle's block count) also returns the
+    stopping-rule statistics of the new state (a dict as ps_compute_stats)."""
+    if stats_nblocks is None:
+        _check(h, lib().ps_pd_iterate(h, int(n_iter), None))
+        return None
+    st, res = _stats_struct(stats_nblocks)
+    _check(h, lib().ps_pd_iterate(h, int(n_iter), ctypes.byref(st)))
+    return _stats_dict(st, res, stats_nblocks)
 
 
 def ps_reweight(h, delta: float) -> None:
@@ -245,15 +261,32 @@ def ps_get_params(h) -> dict:
     return dict(zip(("tau", "rho1", "rho2", "rho3", "opnorm_sq"), (v.value for v in vals)))
 
 
-def ps_compute_stats(h, zeta_sigma: float, nblocks: int) -> dict:
+def _stats_struct(nblocks: int):
     res = (ctypes.c_double * max(1, nblocks))()
     st = ps_stats()
     st.nblocks = nblocks
     st.block_residual = ctypes.cast(res, ctypes.POINTER(ctypes.c_double))
-    _check(h, lib().ps_compute_stats(h, float(zeta_sigma), ctypes.byref(st)))
+    return st, res
+
+
+def _stats_dict(st, res, nblocks: int) -> dict:
     return {"block_residual": np.array(res[:nblocks]), "rel_change": np.array(st.rel_change[:]),
             "zeta": st.zeta, "violations": st.violations, "violations_raw": st.violations_raw,
-            "weighted_l1": st.weighted_l1, "iterations": st.iterations}
+            "weighted_l1": st.weighted_l1, "iterations": st.iterations, "stop_flags": st.stop_flags,
+            "converged": bool(st.converged)}
+
+
+def ps_get_config(h) -> ps_config:
+    cfg = ps_config()
+    _check(h, lib().ps_get_config(h, ctypes.byref(cfg)))
+    return cfg
+
+
+def ps_compute_stats(h, zeta_sigma: float, nblocks: int) -> dict:
+    """Stopping-rule statistics (zeta_sigma <= 0: the handle's)."""
+    st, res = _stats_struct(nblocks)
+    _check(h, lib().ps_compute_stats(h, float(zeta_sigma), ctypes.byref(st)))
+    return _stats_dict(st, res, nblocks)
 
 
 def _op(name, h, x, out, in_dtype, out_dtype):
@@ -288,6 +321,17 @@ def ps_apply_psi_static(A, S, n: int, levels: int, stream=None) -> None:
         raise ValueError("ps_apply_psi_static takes device tensors only")
     st = ctypes.c_void_p(int(stream)) if stream else None
     _check(None, lib().ps_apply_psi_static(pa, ps_, int(n), int(levels), st))
+
+
+def ps_static_status(stream=None) -> None:
+    """Raises PolsaraError(PS_ETIMEOUT) if the last ps_apply_psi_static call on this device gave up."""
+    st = ctypes.c_void_p(int(stream)) if stream else None
+    _check(None, lib().ps_static_status(st))
+
+
+def ps_debug_set_wait_polls(polls: int) -> None:
+    """Test hook: bounded-wait poll budget of every kernel (0: give up at once; < 0: default)."""
+    _check(None, lib().ps_debug_set_wait_polls(int(polls)))
 
 
 def ps_wavelet_filters() -> np.ndarray:

@@ -378,6 +378,11 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
   if (W != 5 && W != 7 && W != 9) return fail(nullptr, PS_EINVAL, "ps_create: kernel_width must be 5, 7 or 9");
   if (cfg->tau < 0 || cfg->rho1 < 0 || cfg->rho2 < 0 || cfg->rho3 < 0)
     return fail(nullptr, PS_EINVAL, "ps_create: step sizes must be >= 0");
+  if (!(cfg->alpha == 0.0 || cfg->alpha == 2.0))
+    return fail(nullptr, PS_EINVAL, "ps_create: alpha (NUFFT oversampling) must be 0 or 2");
+  for (double v : {cfg->gamma, cfg->noise_sigma, cfg->rel_tol, cfg->resid_tol, cfg->np_tol, cfg->zeta_sigma})
+    if (!(v >= 0) || !std::isfinite(v))
+      return fail(nullptr, PS_EINVAL, "ps_create: gamma, noise_sigma and the stopping tolerances must be finite and >= 0");
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
     return fail(nullptr, PS_ECUDA, "ps_create: no CUDA device");
@@ -385,6 +390,14 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
   ps_handle* h = new ps_handle();
   h->cfg = *cfg;
   h->cfg.kernel_width = W;
+  // Defaults of Section 5.5 (rel_tol = epsilon, resid_tol = vartheta, np_tol = varrho in
+  // percent) and Section 5.2 (zeta = 3 rms), and the oversampling 2.
+  h->cfg.alpha = 2.0;
+  if (!(h->cfg.rel_tol > 0)) h->cfg.rel_tol = 1e-5;
+  if (!(h->cfg.resid_tol > 0)) h->cfg.resid_tol = 5e-3;
+  if (!(h->cfg.np_tol > 0)) h->cfg.np_tol = 0.5;
+  if (!(h->cfg.zeta_sigma > 0)) h->cfg.zeta_sigma = 3.0;
+  h->gamma_default = cfg->gamma > 0 ? cfg->gamma : 1.0;
   h->n = n;
   h->N = n * n;
   h->L = L;
@@ -515,6 +528,7 @@ static ps_status stage_in(Handle* h, const void* src, size_t bytes, int device_p
 }
 
 static ps_status opnorm_lanczos(Handle* h);
+static ps_status default_gamma(Handle* h);
 }  // extern "C"
 
 static __global__ void k_fill(float* p, int n, float v) {
@@ -539,15 +553,28 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   CHECK_ALIGN(h, uv, device_ptrs, "set_measurements");
   CHECK_ALIGN(h, vis, device_ptrs, "set_measurements");
   CHECK_ALIGN(h, weights, device_ptrs, "set_measurements");
-  if (M > 0 && (!uv || !vis || !block_offsets || !eps || nblocks < 1 || nblocks > 2047))
-    return fail(h, PS_EINVAL, "set_measurements: need uv, vis, block_offsets, eps and 1 <= nblocks <= 2047");
+  if (M > 0 && (!uv || !vis || !block_offsets || nblocks < 1 || nblocks > 2047))
+    return fail(h, PS_EINVAL, "set_measurements: need uv, vis, block_offsets and 1 <= nblocks <= 2047");
+  std::vector<double> eps_chi2;
   if (M > 0) {
     if (block_offsets[0] != 0 || block_offsets[nblocks] != M64)
       return fail(h, PS_EINVAL, "set_measurements: block_offsets must start at 0 and end at M");
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = 0; b < nblocks; ++b)
       if (block_offsets[b + 1] < block_offsets[b]) return fail(h, PS_EINVAL, "set_measurements: offsets decrease");
-      if (!(eps[b] > 0) || !std::isfinite(eps[b])) return fail(h, PS_EINVAL, "set_measurements: eps must be > 0");
+    if (!eps) {
+      // Section 5.1: ||E_b||^2 / (sigma^2 / 2) is chi^2 with 8 M_b degrees of freedom; the radius
+      // sits two standard deviations above the mean, eps_b^2 = (8 M_b + 2 sqrt(16 M_b)) sigma^2 / 2.
+      const double sig = h->cfg.noise_sigma;
+      if (!(sig > 0)) return fail(h, PS_EINVAL, "set_measurements: eps = NULL needs cfg.noise_sigma > 0");
+      eps_chi2.resize(nblocks);
+      for (int b = 0; b < nblocks; ++b) {
+        const double dof = 8.0 * (double)(block_offsets[b + 1] - block_offsets[b]);
+        eps_chi2[b] = std::sqrt((dof + 2.0 * std::sqrt(2.0 * dof)) * sig * sig / 2.0);
+      }
+      eps = eps_chi2.data();
     }
+    for (int b = 0; b < nblocks; ++b)
+      if (!(eps[b] > 0) || !std::isfinite(eps[b])) return fail(h, PS_EINVAL, "set_measurements: eps must be > 0");
   }
   CK(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
@@ -755,6 +782,7 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   ps_status st = opnorm_lanczos(h);
   if (st != PS_OK) return st;
   set_default_steps(h);
+  if ((st = default_gamma(h)) != PS_OK) return st;
   return reset_state(h);
 }
 
@@ -844,10 +872,40 @@ static ps_status opnorm_lanczos(Handle* h) {
   return PS_OK;
 }
 
+// gamma of step 6: cfg.gamma, else 1e-3 max|Psi^dagger phi^dagger Y| / ||phi||^2 (image
+// units; 1 without data); then the thresholds gamma W with W = 1. Scratch: Adj and A,
+// which the caller's reset of the state clears.
+static ps_status default_gamma(Handle* h) {
+  if (h->cfg.gamma > 0) {
+    h->gamma_default = h->cfg.gamma;
+  } else if (h->M > 0 && h->opnorm_sq > 0) {
+    double* dres = h->red + (size_t)h->red_cap - 600;
+    CK(h, ps::nufft_grid(h, h->Y, 0));
+    CK(h, ps::nufft_adjoint_image(h, h->Adj));
+    CK(h, ps::dirac_apply(h, h->Adj, h->A, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+    CK(h, ps::sara_analysis(h, h->Adj, h->A, nullptr, ps::SARA_APPLY, 1.0f / 3.0f, 0.f, 0.f));
+    CK(h, ps::max_abs(h, h->A, 36 * (size_t)h->N, dres + 8));
+    CK(h, cudaMemcpyAsync(h->red_host, dres + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double g = 1e-3 * h->red_host[0] / h->opnorm_sq;
+    if (!std::isfinite(g)) return fail(h, PS_ENONFINITE, "set_measurements: non-finite phi^dagger Y");
+    h->gamma_default = g > 0 ? g : 1.0;
+  } else {
+    h->gamma_default = 1.0;
+  }
+  h->gamma = h->gamma_default;
+  const size_t len = 36 * (size_t)h->N;
+  k_fill4<<<1024, 256, 0, h->stream>>>(reinterpret_cast<float4*>(h->T), len / 4, (float)h->gamma);
+  CK(h, cudaGetLastError());
+  return PS_OK;
+}
+
 ps_status ps_set_sara_weights(ps_handle* h, const float* W, double gamma, int32_t device_ptrs) {
   if (!h) return PS_EINVAL;
   CHECK_ALIGN(h, W, device_ptrs, "set_sara_weights");
-  if (!(gamma > 0) || !std::isfinite(gamma)) return fail(h, PS_EINVAL, "set_sara_weights: gamma must be > 0");
+  if (gamma == 0) gamma = h->gamma_default;
+  if (!(gamma > 0) || !std::isfinite(gamma))
+    return fail(h, PS_EINVAL, "set_sara_weights: gamma must be > 0 (or 0 for the handle's gamma)");
   const size_t len = 36 * (size_t)h->N;
   if (W) {
     ps_status st = stage_in(h, W, len * sizeof(float), device_ptrs, h->T);
@@ -896,22 +954,23 @@ ps_status ps_set_tv_weights(ps_handle* h, const double* tv, const double* l1) {
   return PS_OK;
 }
 
-ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter) {
+ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter, ps_stats* stats) {
   if (!h) return PS_EINVAL;
   if (n_iter < 0) return fail(h, PS_EINVAL, "pd_iterate: n_iter < 0");
   if (!h->have_meas) return fail(h, PS_ESTATE, "pd_iterate: call ps_set_measurements first");
-  if (n_iter == 0) return PS_OK;
-  if (!h->derived_valid) {
-    ps_status st = compute_derived(h);
-    if (st != PS_OK) return st;
+  if (n_iter > 0) {
+    if (!h->derived_valid) {
+      ps_status st = compute_derived(h);
+      if (st != PS_OK) return st;
+    }
+    if (!h->graph || h->graph_mode != h->mode) {
+      ps_status st = build_graph(h);
+      if (st != PS_OK) return st;
+    }
+    for (int i = 0; i < n_iter; ++i) CK(h, cudaGraphLaunch(h->graph, h->stream));
+    h->iterations += n_iter;
   }
-  if (!h->graph || h->graph_mode != h->mode) {
-    ps_status st = build_graph(h);
-    if (st != PS_OK) return st;
-  }
-  for (int i = 0; i < n_iter; ++i) CK(h, cudaGraphLaunch(h->graph, h->stream));
-  h->iterations += n_iter;
-  return PS_OK;
+  return stats ? ps_compute_stats(h, 0.0, stats) : PS_OK;
 }
 
 ps_status ps_reweight(ps_handle* h, double delta) {
@@ -996,6 +1055,14 @@ ps_status ps_set_state(ps_handle* h, const ps_state_view* v) {
   return PS_OK;
 }
 
+ps_status ps_get_config(const ps_handle* h, ps_config* out) {
+  if (!h || !out) return PS_EINVAL;
+  *out = h->cfg;
+  out->mode = h->mode;
+  out->gamma = h->gamma_default;
+  return PS_OK;
+}
+
 ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, double* rho3, double* opnorm_sq) {
   if (!h) return PS_EINVAL;
   if (tau) *tau = h->tau;
@@ -1003,6 +1070,24 @@ ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, d
   if (rho2) *rho2 = h->rho2;
   if (rho3) *rho3 = h->rho3;
   if (opnorm_sq) *opnorm_sq = h->opnorm_sq;
+  return PS_OK;
+}
+
+// Relative change per map (Eq. stop_crit) from the FP64 partials k_primal wrote: 0/0 = 0
+// (a map that stayed zero), x/0 = +inf. Non-finite sums mean a NaN or infinity in S.
+static ps_status rel_change_from_partials(Handle* h, const std::vector<double>& part, double out4[4]) {
+  const int nb = sweep_blocks_host(h->N);
+  bool finite = true;
+  for (int c = 0; c < 4; ++c) {
+    double num = 0, den = 0;
+    for (int b = 0; b < nb; ++b) {
+      num += part[8 * (size_t)b + c];
+      den += part[8 * (size_t)b + 4 + c];
+    }
+    finite = finite && std::isfinite(num) && std::isfinite(den);
+    out4[c] = den > 0 ? std::sqrt(num / den) : (num > 0 ? INFINITY : 0.0);
+  }
+  if (!finite) return fail(h, PS_ENONFINITE, "the state holds a NaN or an infinity (relative-change sums are not finite)");
   return PS_OK;
 }
 
@@ -1014,12 +1099,20 @@ static ps_status ensure_tmp36(Handle* h) {
 ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
   if (!h || !out) return PS_EINVAL;
   if (!h->have_meas) return fail(h, PS_ESTATE, "compute_stats: call ps_set_measurements first");
+  if (!(zeta_sigma > 0)) zeta_sigma = h->cfg.zeta_sigma;
   const size_t N = h->N;
   double* dres = h->red + (size_t)h->red_cap - 600;
   // Relative change of the last iteration (partials written by k_primal).
   const int nb = sweep_blocks_host((int)N);
   std::vector<double> part(8 * (size_t)nb);
   CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  out->stop_flags = 0;
+  out->converged = 0;
+  {
+    ps_status st = rel_change_from_partials(h, part, out->rel_change);
+    if (st != PS_OK) return st;
+  }
   // Residual Y - phi(S) per block, and the residual image.
   std::vector<double> bsum(h->nblocks);
   double rms = 0.0;
@@ -1035,14 +1128,6 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
     rms = std::sqrt(h->red_host[0] / (double)N);
   }
   CK(h, cudaStreamSynchronize(h->stream));
-  for (int c = 0; c < 4; ++c) {
-    double num = 0, den = 0;
-    for (int b = 0; b < nb; ++b) {
-      num += part[8 * (size_t)b + c];
-      den += part[8 * (size_t)b + 4 + c];
-    }
-    out->rel_change[c] = den > 0 ? std::sqrt(num / den) : INFINITY;
-  }
   if (out->block_residual)
     for (int b = 0; b < std::min(out->nblocks, h->nblocks); ++b) out->block_residual[b] = std::sqrt(bsum[b]);
   out->zeta = h->psf_peak > 0 ? zeta_sigma * rms / h->psf_peak : 0.0;
@@ -1058,6 +1143,19 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
   out->violations_raw = (int64_t)h->red_host[3];
   out->weighted_l1 = h->red_host[4];
   out->iterations = h->iterations;
+  // Stopping rule of Section 5.5: every criterion that applies in the mode.
+  int flags = 0;
+  double rc = 0.0;
+  for (int c = 0; c < 4; ++c) rc = std::max(rc, out->rel_change[c]);
+  if (rc <= h->cfg.rel_tol) flags |= PS_STOP_REL;
+  bool fit = true;
+  if (!ps::tv_mode(h->mode))
+    for (int b = 0; b < h->nblocks; ++b) fit = fit && std::sqrt(bsum[b]) <= (1.0 + h->cfg.resid_tol) * h->eps_host[b];
+  if (fit) flags |= PS_STOP_RESID;
+  if (!ps::constrained_mode(h->mode) || 100.0 * (double)out->violations / (double)N <= h->cfg.np_tol)
+    flags |= PS_STOP_NP;
+  out->stop_flags = flags;
+  out->converged = flags == (PS_STOP_REL | PS_STOP_RESID | PS_STOP_NP);
   return check_flags(h);
 }
 
@@ -1309,15 +1407,9 @@ ps_status ps_get_rel_change(ps_handle* h, double* out4) {
   std::vector<double> part(8 * (size_t)nb);
   CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  for (int c = 0; c < 4; ++c) {
-    double num = 0, den = 0;
-    for (int b = 0; b < nb; ++b) {
-      num += part[8 * (size_t)b + c];
-      den += part[8 * (size_t)b + 4 + c];
-    }
-    out4[c] = den > 0 ? std::sqrt(num / den) : INFINITY;
-  }
-  return check_flags(h);
+  ps_status st = check_flags(h);
+  if (st != PS_OK) return st;
+  return rel_change_from_partials(h, part, out4);
 }
 
 ps_status ps_max_abs_analysis(ps_handle* h, double* out) {
@@ -1332,6 +1424,15 @@ ps_status ps_max_abs_analysis(ps_handle* h, double* out) {
   CK(h, cudaStreamSynchronize(h->stream));
   *out = h->red_host[0];
   return check_flags(h);
+}
+
+ps_status ps_debug_set_wait_polls(int32_t polls) {
+  cudaError_t e = ps::set_wait_polls_sara(polls);
+  if (e == cudaSuccess) e = ps::set_wait_polls_nufft(polls);
+  // The copies run on the legacy stream, which non-blocking streams do not wait for.
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(nullptr, PS_ECUDA, std::string("debug_set_wait_polls: ") + cudaGetErrorString(e));
+  return PS_OK;
 }
 
 ps_status ps_wavelet_filters(double* out) {

@@ -54,6 +54,7 @@ struct Handle {
   std::string err;
   int n = 0, N = 0, L = 0, mode = PS_POLARIZED;
   double tau = 0, rho1 = 1, rho2 = 1, rho3 = 1, opnorm_sq = 0, gamma = 1;
+  double gamma_default = 0;       // cfg.gamma, else 1e-3 max|Psi^dagger phi^dagger Y| / ||phi||^2
   double tv_mu[4] = {0, 0, 0, 0}, l1_mu[4] = {0, 0, 0, 0};   // TV and l1 weights (Algorithm 3)
   bool have_meas = false;
   bool derived_valid = false;     // PsiA and Adj hold Psi A and phi^dagger B of the current state
@@ -112,6 +113,10 @@ struct Handle {
   int graph_mode = -1;
   uint64_t version = 1;       // bumped when mode, state or measurements change (batch graphs rebuild)
 };
+
+// Bounded-wait poll budget of each translation unit with bulk-copy waits (polls < 0: default).
+cudaError_t set_wait_polls_sara(int polls);
+cudaError_t set_wait_polls_nufft(int polls);
 
 // Message returned by ps_last_error(NULL) (calls without a handle).
 void set_global_error(const std::string& msg);

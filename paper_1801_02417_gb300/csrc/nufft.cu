@@ -26,6 +26,9 @@
 
 namespace ps {
 
+// Sets this file's bounded-wait poll budget (ps_debug_set_wait_polls).
+cudaError_t set_wait_polls_nufft(int polls) { return set_wait_polls_here(polls); }
+
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
@@ -823,7 +826,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        (void)mbar_wait(&wbar, 0);
+        (void)mbar_drain(&wbar, 0);
       }
       return;
     }

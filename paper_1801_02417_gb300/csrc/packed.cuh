@@ -44,10 +44,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-// Bounded wait on phase `parity`: false (and the caller raises the error flag) if it never completes.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Poll budget of the bounded waits. c_wait_polls (one copy per translation unit,
+// set by set_wait_polls_here) bounds the first wait on a barrier phase; a CTA
+// whose wait gave up drains its copies still in flight with the full budget
+// (mbar_drain) before it returns, so no copy lands after it has exited.
+constexpr uint32_t kWaitPolls = 1u << 22;
+static __constant__ uint32_t c_wait_polls = kWaitPolls;
+
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, uint32_t parity, uint32_t polls) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+  for (uint32_t i = 0; i < polls; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -57,5 +63,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (ok) return true;
   }
   return false;
+}
+// Bounded wait on phase `parity`: false (and the caller raises the error flag) if it never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_poll(bar, parity, c_wait_polls); }
+// Second wait of a CTA that gave up: the copies it issued get the full budget to land.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) { return mbar_poll(bar, parity, kWaitPolls); }
+
+// Host side: sets this translation unit's c_wait_polls (polls < 0: the default).
+static inline cudaError_t set_wait_polls_here(int polls) {
+  const uint32_t v = polls < 0 ? kWaitPolls : (uint32_t)polls;
+  return cudaMemcpyToSymbol(c_wait_polls, &v, sizeof(v));
 }
 }  // namespace ps

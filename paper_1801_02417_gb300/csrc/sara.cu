@@ -391,8 +391,8 @@ __device__ __forceinline__ AnaSmem ana_smem(float4* sma) {
 __device__ __forceinline__ void ana_abort(const AnaSmem& S, int staged, int* err) {
   if (threadIdx.x == 0) {
     atomicExch(err, 1);
-    (void)mbar_wait(&S.bar[0], 0);
-    if (staged) (void)mbar_wait(&S.bar[1], 0);
+    (void)mbar_drain(&S.bar[0], 0);
+    if (staged) (void)mbar_drain(&S.bar[1], 0);
   }
 }
 
@@ -415,7 +415,7 @@ __device__ __forceinline__ void ana_basis(const float* src, int m, const AnaSmem
   __syncthreads();
   if (mode == SARA_DUAL && !mbar_wait(&S.bar[1], 0)) {
     atomicExch(err, 1);
-    (void)mbar_wait(&S.bar[1], 0);
+    (void)mbar_drain(&S.bar[1], 0);
     return;
   }
   ana_cols<LF>(S.lo_s, S.hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta,
@@ -515,9 +515,9 @@ __global__ void __launch_bounds__(256, 2) k_ana_pers(const float* __restrict__ i
   auto abort_all = [&]() {
     if (threadIdx.x == 0) {
       atomicExch(err, 1);
-      if (issued_in) (void)mbar_wait(&bar[0], (issued_in - 1) & 1);
+      if (issued_in) (void)mbar_drain(&bar[0], (issued_in - 1) & 1);
       for (int q = 0; q < 2; ++q)
-        if (issued_st[q]) (void)mbar_wait(&bar[1 + q], (issued_st[q] - 1) & 1);
+        if (issued_st[q]) (void)mbar_drain(&bar[1 + q], (issued_st[q] - 1) & 1);
     }
   };
   int u = blockIdx.x;
@@ -844,8 +844,8 @@ static size_t syn2_smem(int sets) { return (size_t)(sets * kC2Set + 2 * kLoSize)
 __device__ __forceinline__ void syn2_abort(uint64_t* b0, uint32_t p0, uint64_t* b1, uint32_t p1, int* err) {
   if (threadIdx.x == 0) {
     if (err) atomicExch(err, 1);
-    (void)mbar_wait(b0, p0);
-    if (b1) (void)mbar_wait(b1, p1);
+    (void)mbar_drain(b0, p0);
+    if (b1) (void)mbar_drain(b1, p1);
   }
   __syncthreads();
 }
@@ -1264,10 +1264,27 @@ cudaError_t sara_synthesis(Handle* h, const float* coef, float* out, cudaEvent_t
 constexpr int kStaticMaxN = 256;
 constexpr size_t kStaticScratchFloats = 2ull * kDb * 4 * (kStaticMaxN / 2) * (kStaticMaxN / 2);   // 4 MiB
 static __device__ __align__(256) float g_static_scratch[kStaticScratchFloats];
+// Raised by a kernel of ps_apply_psi_static whose bounded wait gave up (cleared by each call).
+static __device__ int g_static_err;
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_static_mu;
 static float* g_static_ptr[kMaxDevices] = {};    // device address of g_static_scratch, per device
+static int* g_static_err_ptr[kMaxDevices] = {};  // device address of g_static_err, per device
+
+// Sets this file's bounded-wait poll budget (ps_debug_set_wait_polls).
+cudaError_t set_wait_polls_sara(int polls) { return set_wait_polls_here(polls); }
+
+// A caller pointer of ps_apply_psi_static must be device or managed memory of the current device.
+static bool device_pointer_here(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
 
 }  // namespace ps
 
@@ -1289,17 +1306,24 @@ extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, in
     set_global_error(std::string("apply_psi_static: no usable current device: ") + cudaGetErrorString(e));
     return PS_ECUDA;
   }
+  if (!device_pointer_here(A, dev) || !device_pointer_here(S, dev))
+    return bad("A and S must point to device (or managed) memory of the current device");
   float* scratch = nullptr;
+  int* flag = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_ptr[dev]) {
-      // Set-up on this device, once: the scratch's device address and the filter taps.
+      // Set-up on this device, once: the device addresses of the scratch and the error
+      // flag, and the filter taps.
       void* p = nullptr;
+      void* q = nullptr;
       e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_static_err);
       if (e != cudaSuccess) {
         set_global_error(std::string("apply_psi_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         return PS_ECUDA;
       }
+      g_static_err_ptr[dev] = static_cast<int*>(q);
       double filt[kDb][kMaxTaps];
       daubechies_filters(filt);
       e = upload_filters(filt, (cudaStream_t)cuda_stream);
@@ -1315,16 +1339,46 @@ extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, in
       g_static_ptr[dev] = static_cast<float*>(p);
     }
     scratch = g_static_ptr[dev];
+    flag = g_static_err_ptr[dev];
   }
-  e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, nullptr, 0);
+  e = cudaMemsetAsync(flag, 0, sizeof(int), (cudaStream_t)cuda_stream);
+  if (e == cudaSuccess) e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, flag, 0);
   if (e != cudaSuccess) {
     set_global_error(std::string("apply_psi_static: launch: ") + cudaGetErrorString(e));
     return PS_ECUDA;
   }
   return PS_OK;
 }
+
+extern "C" ps_status ps_static_status(void* cuda_stream) {
+  using namespace ps;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_global_error(std::string("static_status: no usable current device: ") + cudaGetErrorString(e));
+    return PS_ECUDA;
+  }
+  int* flag = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    flag = g_static_err_ptr[dev];
+  }
+  e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("static_status: ") + cudaGetErrorString(e));
+    return PS_ECUDA;
+  }
+  if (!flag) return PS_OK;   // ps_apply_psi_static has not run on this device
+  int v = 0;
+  e = cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("static_status: ") + cudaGetErrorString(e));
+    return PS_ECUDA;
+  }
+  if (v) {
+    set_global_error("apply_psi_static: a bounded device wait (bulk-copy barrier) gave up; S is incomplete");
+    return PS_ETIMEOUT;
+  }
+  return PS_OK;
+}
 #pragma GCC visibility pop
-
-namespace ps {
-
-}  // namespace ps

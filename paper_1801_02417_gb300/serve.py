@@ -7,9 +7,11 @@ admitted problem on a worker thread (handle creation, row sorting, operator
 norm), and keeps every active problem's primal/dual state resident on the
 GPU. Each scheduler tick launches `check_every` iterations of every active
 problem on its own CUDA stream, so the kernels of different problems overlap on
-the device, then evaluates each problem's stopping rule (relative change of
-Eq. stop_crit) and advances its Algorithm 2 phase: an NNLS cycle, then up to
-`reweights` reweighted cycles of Algorithm 1. Finished problems return their
+the device, then evaluates each problem's stopping rule (Section 5.5: the
+relative change of Eq. stop_crit, the data fit within (1 + vartheta) eps_b and,
+with the constraint, N_p <= varrho) and advances its Algorithm 2 phase: an NNLS
+cycle, then up to `reweights` reweighted cycles of Algorithm 1. A request whose
+state turns non-finite (PS_ENONFINITE from the library's FP64 sums) fails alone. Finished problems return their
 Stokes maps and free their memory, which admits the next requests.
 
 Two front ends share the scheduler: `Server.run(requests)` replays a recorded
@@ -64,6 +66,7 @@ class Result:
 @dataclasses.dataclass
 class Policy:
     rel_tol: float = 1e-4          # Eq. stop_crit tolerance per cycle
+    rule: str = "paper"            # "paper": every criterion of Section 5.5; "rel": the relative change only
     max_iter: int = 2000           # per request
     reweights: int = 5             # reweighted cycles after the NNLS cycle
     check_every: int = 20          # iterations between stop-rule checks
@@ -92,8 +95,11 @@ class _Active:
 
     def advance(self) -> bool:
         """Check the stop rule after the launched iterations; True when the request is done."""
-        rel = B.ps_get_rel_change(self.s.h)
-        cycle_done = (float(np.max(rel[:3])) <= self.policy.rel_tol or self.in_cycle >= self.per_cycle)
+        if self.policy.rule == "paper":
+            met = B.ps_compute_stats(self.s.h, 0.0, self.s.nblocks)["converged"]
+        else:
+            met = float(np.max(B.ps_get_rel_change(self.s.h))) <= self.policy.rel_tol
+        cycle_done = met or self.in_cycle >= self.per_cycle
         if self.used >= self.policy.max_iter:
             return True
         if not cycle_done:
@@ -150,7 +156,7 @@ class Server:
         self._id_lock = threading.Lock()
 
     def _prepare(self, prob: Problem) -> PolarizedSARA:
-        s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS)
+        s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS, rel_tol=self.policy.rel_tol)
         try:
             s.set_measurements(prob.uv, prob.vis, prob.weights, prob.offsets, prob.eps)
             if self.autotune:

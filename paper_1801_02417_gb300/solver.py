@@ -32,9 +32,13 @@ class PolarizedSARA:
 
     def __init__(self, n: int, levels: int, mode: int = B.PS_POLARIZED, kernel_width: int = 7,
                  literal_ball: bool = False, tau: float = 0.0, rho1: float = 0.0, rho2: float = 0.0,
-                 rho3: float = 0.0, stream=None):
+                 rho3: float = 0.0, stream=None, gamma: float = 0.0, noise_sigma: float = 0.0,
+                 rel_tol: float = 0.0, resid_tol: float = 0.0, np_tol: float = 0.0, zeta_sigma: float = 0.0):
+        """Zero for a parameter takes the library default (include/polsara.h, ps_config)."""
         cfg = B.ps_config(n=n, levels=levels, mode=mode, literal_ball=int(literal_ball),
-                          kernel_width=kernel_width, reserved=0, tau=tau, rho1=rho1, rho2=rho2, rho3=rho3)
+                          kernel_width=kernel_width, reserved=0, tau=tau, rho1=rho1, rho2=rho2, rho3=rho3,
+                          alpha=0.0, gamma=gamma, noise_sigma=noise_sigma, rel_tol=rel_tol,
+                          resid_tol=resid_tol, np_tol=np_tol, zeta_sigma=zeta_sigma)
         self.n, self.levels = n, levels
         self.h = B.ps_create(cfg, stream)
         self.nblocks = 0
@@ -58,9 +62,10 @@ class PolarizedSARA:
             pass
 
     # Thin forwards to the C ABI.
-    def set_measurements(self, uv, vis, weights, block_offsets, eps) -> None:
+    def set_measurements(self, uv, vis, weights, block_offsets, eps=None) -> None:
+        """eps None: the chi^2 radii of Section 5.1 from the handle's noise_sigma."""
         B.ps_set_measurements(self.h, uv, vis, weights, block_offsets, eps)
-        self.nblocks = len(eps)
+        self.nblocks = len(block_offsets) - 1
         self.M = int(uv.shape[0])
 
     def set_sara_weights(self, W, gamma: float) -> None:
@@ -71,8 +76,9 @@ class PolarizedSARA:
         B.ps_get_sara_weights(self.h, out)
         return out
 
-    def pd_iterate(self, n_iter: int) -> None:
-        B.ps_pd_iterate(self.h, n_iter)
+    def pd_iterate(self, n_iter: int, stats: bool = False):
+        """n_iter iterations; with stats=True returns the stopping-rule statistics after them."""
+        return B.ps_pd_iterate(self.h, n_iter, self.nblocks if stats else None)
 
     def reweight(self, delta: float) -> None:
         B.ps_reweight(self.h, delta)
@@ -100,7 +106,11 @@ class PolarizedSARA:
     def params(self) -> dict:
         return B.ps_get_params(self.h)
 
-    def stats(self, zeta_sigma: float = 3.0) -> dict:
+    def config(self):
+        """The handle's ps_config with every default resolved (gamma: the handle's default gamma)."""
+        return B.ps_get_config(self.h)
+
+    def stats(self, zeta_sigma: float = 0.0) -> dict:
         return B.ps_compute_stats(self.h, zeta_sigma, self.nblocks)
 
     def synchronize(self) -> None:
@@ -127,22 +137,34 @@ class PolarizedSARA:
             delta *= sch.delta_decay
         return self.get_stokes()
 
-    def solve_until(self, gamma: float, rel_tol: float = 1e-4, max_iter: int = 2000, reweights: int = 5,
-                    check_every: int = 20, delta_factor: float = 0.1, delta_decay: float = 0.5) -> dict:
-        """Stop each cycle when max_i rel-change <= rel_tol (Eq. stop_crit) or at the iteration cap."""
+    def solve_until(self, gamma: float = 0.0, max_iter: int = 2000, reweights: int = 5, check_every: int = 20,
+                    delta_factor: float = 0.1, delta_decay: float = 0.5, rule: str = "paper") -> dict:
+        """Algorithm 2 with each cycle stopped by the rule of Section 5.5 or at the iteration cap.
+
+        rule "paper": every criterion of Section 5.5 with the handle's tolerances (ps_config
+        rel_tol, resid_tol, np_tol): the relative change of Eq. stop_crit, the data fit
+        ||phi(S) - Y||_b <= (1 + vartheta) eps_b and, with the constraint, N_p <= varrho.
+        rule "rel": the relative change alone (cheaper: no residual evaluation).
+        The relative change covers all four maps (a map that stays zero does not count).
+        gamma 0 takes the handle's gamma."""
         used = 0
         per_cap = max(check_every, max_iter // (reweights + 1))
+        rel_tol = B.ps_get_config(self.h).rel_tol
 
         def cycle():
             nonlocal used
             k = 0
             while k < per_cap and used < max_iter:
                 step = min(check_every, per_cap - k, max_iter - used)
-                self.pd_iterate(step)
                 k += step
                 used += step
-                if float(np.max(B.ps_get_rel_change(self.h)[:3])) <= rel_tol:
-                    break
+                if rule == "paper":
+                    if self.pd_iterate(step, stats=True)["converged"]:
+                        break
+                else:
+                    self.pd_iterate(step)
+                    if float(np.max(B.ps_get_rel_change(self.h))) <= rel_tol:
+                        break
         self.set_mode(B.PS_NNLS)
         cycle()
         delta = delta_factor * B.ps_max_abs_analysis(self.h)

@@ -12,9 +12,13 @@ faint V map).
 import numpy as np
 import pytest
 
+from oracle import measurement as meas
+from oracle import primal_dual as opd
+from oracle import wavelets as wav
 from paper_1801_02417_gb300 import binding as B
-from paper_1801_02417_gb300.serve import Policy, Server, synthesize_problem
+from paper_1801_02417_gb300.serve import Policy, Problem, Server, synthesize_problem
 from paper_1801_02417_gb300.solver import PolarizedSARA
+from problems import make_channel_problem, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -63,7 +67,7 @@ def test_batch_graph_matches_individual_iterations(problems):
 
 
 def test_each_request_same_alone_and_in_the_mix(problems):
-    pol = Policy(rel_tol=0.0, max_iter=300, reweights=2, check_every=25)   # fixed iteration counts
+    pol = Policy(rule="rel", rel_tol=0.0, max_iter=300, reweights=2, check_every=25)   # fixed iteration counts
     alone = {}
     for i, p in enumerate(problems):
         res = Server(hbm_budget=1 << 40, max_active=1, policy=pol).run([(0.0, p)])
@@ -118,7 +122,7 @@ def test_live_submissions_resolve_like_solo_runs(problems):
     import concurrent.futures
     import dataclasses
 
-    pol = Policy(rel_tol=0.0, max_iter=200, reweights=1, check_every=25)
+    pol = Policy(rule="rel", rel_tol=0.0, max_iter=200, reweights=1, check_every=25)
     alone = [Server(hbm_budget=1 << 40, max_active=1, policy=pol).run([(0.0, p)])[0].S for p in problems]
     bad = dataclasses.replace(problems[0], eps=-np.abs(problems[0].eps))
     budget = sum(p.footprint() for p in problems[:3])
@@ -148,7 +152,7 @@ def test_multifrequency_channels_solved_together_like_alone():
     chans = synthesize_channels(64, 3, 2500, 4, seed=31)
     assert not np.allclose(chans[0].vis, chans[-1].vis)
     assert np.allclose(chans[-1].uv, chans[0].uv * (1.1 / 0.9))
-    pol = Policy(rel_tol=0.0, max_iter=200, reweights=1, check_every=25)
+    pol = Policy(rule="rel", rel_tol=0.0, max_iter=200, reweights=1, check_every=25)
     alone = [Server(hbm_budget=1 << 40, max_active=1, policy=pol).run([(0.0, p)])[0].S for p in chans]
     res = Server(hbm_budget=1 << 40, max_active=8, policy=pol).run([(0.0, p) for p in chans])
     assert sorted(r.rid for r in res) == list(range(len(chans)))
@@ -156,3 +160,41 @@ def test_multifrequency_channels_solved_together_like_alone():
         assert np.all(np.isfinite(r.S))
         for k in range(4):
             assert _rel(r.S[k], alone[r.rid][k]) <= TOL_FINAL, (r.rid, k)
+
+
+def test_multifrequency_channel_solve_matches_oracle():
+    """One channel of a multi-frequency observation (scaled uv tracks, power-law spectrum,
+    Faraday-rotated Q and U; clean visibilities from the oracle's phi) solved through the server
+    on the fixed schedule of the 64 x 64 workload (300 iterations, 3 reweights, NNLS start)
+    against the FP64 oracle's Algorithm 2: each Stokes map within 1e-3 relative l2."""
+    n, M, L = 64, 2000, 4
+    pb = make_channel_problem(n, M, L, nchan=8, chan=6, seed=43)
+    prob = pb["prob"]
+    on = meas.op_norm_sq_lanczos(pb["uv"], prob.w, n)
+    gamma = 1e-3 * float(np.max(np.abs(wav.psi_adjoint(meas.phi_adjoint(prob.Y, pb["uv"], prob.w, n), L)))) / on
+    ref = opd.solve(prob, 300, 3, gamma, on)["S"]
+    req = Problem(n, L, pb["uv"], pb["Y"], pb["w"], pb["off"], pb["eps"], gamma)
+    pol = Policy(rule="rel", rel_tol=0.0, max_iter=300, reweights=3, check_every=25)
+    res = Server(hbm_budget=1 << 40, max_active=4, policy=pol).run([(0.0, req)])
+    assert res[0].iterations == 300
+    errs = [rel_err(res[0].S[k], ref[k]) for k in range(4)]
+    assert max(errs) <= 1e-3, errs
+
+
+def test_nonfinite_request_fails_alone():
+    """A request whose visibilities hold a NaN reaches a non-finite state, which the library's
+    FP64 sums report as PS_ENONFINITE: that request's future fails and the others resolve."""
+    import dataclasses
+    base = synthesize_problem(64, 3, 1500, 44, 1)
+    vis = base.vis.copy()
+    vis[17, 2] = np.nan
+    bad = dataclasses.replace(base, vis=vis)
+    pol = Policy(max_iter=200, reweights=1, check_every=20)
+    with Server(hbm_budget=1 << 40, max_active=4, policy=pol) as srv:
+        futs = [srv.submit(p) for p in (base, bad, base)]
+        ok = [futs[0].result(timeout=300), futs[2].result(timeout=300)]
+        with pytest.raises(B.PolsaraError) as e:
+            futs[1].result(timeout=300)
+    assert e.value.status == B.PS_ENONFINITE
+    for r in ok:
+        assert np.all(np.isfinite(r.S))

@@ -158,6 +158,115 @@ def test_reweight_formula_bounds():
     assert np.allclose(W * (0.5 + c), 0.5)
 
 
+def test_reweight_hand_computed_haar_and_constant_maps():
+    """Eq. weights W = delta / (delta + |Psi^dagger S|) on maps whose SARA coefficients are known in
+    closed form. A constant map c: every Daubechies basis puts c 2^L (the filters sum to sqrt 2
+    per axis) in its coarsest approximation block and zero in every detail, the Dirac basis c
+    everywhere; scaled by 1/3. A point of value v at pixel (0, 0) in the Haar basis (db1):
+    level-1 details v/2 at (0, n/2), (n/2, 0), (n/2, n/2), level-2 details and approximation
+    v/4 at (0, n/4), (n/4, 0), (n/4, n/4), (0, 0); zero elsewhere."""
+    n, L, delta = 8, 2, 0.05
+    consts = np.array([1.0, -0.5, 0.25, 2.0])
+    S = consts[:, None, None] * np.ones((4, n, n))
+    W = pd.reweight(S, L, delta)
+    for i, c in enumerate(consts):
+        assert np.allclose(W[i, 0], delta / (delta + abs(c) / 3.0), rtol=1e-12)
+        for b in range(1, 9):
+            expect = np.ones((n, n))
+            expect[: n >> L, : n >> L] = delta / (delta + abs(c) * 2 ** L / 3.0)
+            assert np.allclose(W[i, b], expect, rtol=1e-12, atol=1e-12), (i, b)
+    v = 1.5
+    S = np.zeros((4, n, n))
+    S[:, 0, 0] = v
+    W = pd.reweight(S, L, delta)
+    mag = np.zeros((n, n))
+    for (r, c) in ((0, n // 2), (n // 2, 0), (n // 2, n // 2)):
+        mag[r, c] = v / 2
+    for (r, c) in ((0, n // 4), (n // 4, 0), (n // 4, n // 4), (0, 0)):
+        mag[r, c] = v / 4
+    assert np.allclose(W[0, 1], delta / (delta + mag / 3.0), rtol=1e-12)
+    dirac = np.zeros((n, n))
+    dirac[0, 0] = v
+    assert np.allclose(W[0, 0], delta / (delta + dirac / 3.0), rtol=1e-12)
+
+
+def test_zeta_threshold_against_the_dense_operator():
+    """zeta = 3 rms(Stokes I part of phi^dagger(Y - phi S)) / PSF peak, with the adjoint taken as the
+    transpose of the dense real matrix of phi and the PSF peak as its (I centre, I centre) Gram
+    entry, which the brightness rows of L fix at 2 sum w_m^2 (|L_I,RR|^2 + |L_I,LL|^2 = 2)."""
+    prob, Strue = _problem(n=8, M=40, levels=1, nblocks=1, seed=2)
+    n, N = 8, 64
+    P = meas.phi_dense(prob.uv, prob.w, n)
+    c = (n // 2) * n + n // 2
+    peak = float(P[:, c] @ P[:, c])
+    assert abs(peak - 2.0 * np.sum(prob.w ** 2)) <= 1e-10 * peak
+    S = 0.8 * Strue
+    r = prob.Y - meas.phi(S, prob.uv, prob.w)
+    img = (P.T @ np.concatenate([r.real.ravel(), r.imag.ravel()]))[:N]
+    zeta = 3.0 * np.sqrt(np.mean(img ** 2)) / peak
+    assert abs(pd.zeta_threshold(S, prob, 3.0) - zeta) <= 1e-10 * zeta
+
+
+def test_solve_follows_the_algorithm2_schedule(monkeypatch):
+    """Algorithm 2 with the NNLS start: iterations // (reweights + 1) per cycle, the first in NNLS
+    mode (g = 0, tau = 0.99 / (rho2 ||phi||^2)), then one reweight before each later cycle with
+    delta^(1) = 0.1 max |Psi^dagger S_nnls| halved at every reweight (Section 4.3.4)."""
+    prob, _ = _problem(n=8, M=60, levels=1, nblocks=1, seed=6)
+    on = meas.op_norm_sq(prob.uv, prob.w, prob.n)
+    runs, deltas = [], []
+    real_run, real_rw = pd.run, pd.reweight
+
+    def spy_run(st, prob_, T, p, iters, mode=pd.POLARIZED):
+        runs.append((mode, iters, float(np.max(np.abs(T))), p.tau))
+        return real_run(st, prob_, T, p, iters, mode)
+
+    def spy_rw(S, levels, delta):
+        deltas.append(delta)
+        return real_rw(S, levels, delta)
+    monkeypatch.setattr(pd, "run", spy_run)
+    monkeypatch.setattr(pd, "reweight", spy_rw)
+    gamma = 0.02
+    pd.solve(prob, iterations=14, reweights=3, gamma=gamma, opnorm_sq=on)
+    assert [r[0] for r in runs] == [pd.NNLS, pd.POLARIZED, pd.POLARIZED, pd.POLARIZED]
+    assert [r[1] for r in runs] == [3, 3, 3, 3]
+    assert runs[0][2] == 0.0 and abs(runs[0][3] - 0.99) < 1e-12
+    assert all(0 < r[2] <= gamma and abs(r[3] - 0.99 / 3.0) < 1e-12 for r in runs[1:])
+    S_nnls = real_run(pd.zero_state(8, 60), prob, np.zeros((4, 9, 8, 8)), pd.step_sizes(on, pd.NNLS), 3,
+                      pd.NNLS)["S"]
+    d1 = 0.1 * float(np.max(np.abs(wav.psi_adjoint(S_nnls, 1))))
+    assert np.allclose(deltas, [d1, d1 / 2, d1 / 4], rtol=1e-12)
+
+
+def test_relative_change_and_stop_rule():
+    """Eq. stop_crit per map with a zero map (V in the paper) that stays zero contributing 0 and one
+    that leaves zero contributing inf; the three criteria of Section 5.5 on constructed states."""
+    rng = np.random.default_rng(3)
+    S0 = rng.normal(size=(4, 8, 8))
+    S0[3] = 0.0
+    S1 = S0 * (1.0 + np.array([1e-3, 2e-3, 3e-3, 0.0]))[:, None, None]
+    assert np.allclose(pd.relative_change(S1, S0), [1e-3, 2e-3, 3e-3, 0.0])
+    S2 = S1.copy()
+    S2[3, 0, 0] = 1e-9
+    assert np.isinf(pd.relative_change(S2, S0)[3])
+    # Noise-free data of a feasible source: its residual is 0 <= (1 + theta) eps and N_p = 0.
+    prob, Strue = _problem(n=16, M=200, levels=2, nblocks=2, seed=8)
+    prob = pd.Problem(prob.n, prob.levels, prob.uv, prob.w, meas.phi(Strue, prob.uv, prob.w), prob.offsets,
+                      prob.eps)
+    st = pd.stop_rule(Strue * (1 + 1e-6), Strue, prob, rel_tol=1e-5)
+    assert st["rel"] and st["resid"] and st["np"] and st["converged"] and st["N_p"] == 0.0
+    st = pd.stop_rule(Strue * (1 + 1e-4), Strue, prob, rel_tol=1e-5)
+    assert not st["rel"] and not st["converged"]
+    # Far from the data: the fit criterion fails.
+    assert not pd.stop_rule(0.5 * Strue, 0.5 * Strue, prob)["resid"]
+    # Q made larger than I on 2% of the pixels (beyond zeta): N_p = 2 > 0.5 fails with the constraint only.
+    bad = Strue.copy()
+    idx = np.unravel_index(np.argsort(Strue[0], axis=None)[-5:], (16, 16))
+    bad[1][idx] = bad[0][idx] + 10.0
+    st = pd.stop_rule(bad, bad, prob)
+    assert abs(st["N_p"] - 100.0 * 5 / 256) < 1e-12 and not st["np"]
+    assert pd.stop_rule(bad, bad, prob, constrained=False)["np"]
+
+
 def test_stats_helpers():
     prob, Strue = _problem()
     assert pd.violation_count(Strue, 0.0) == 0
