@@ -125,6 +125,29 @@ def stage_bytes(n: int, L: int, M: int, Wd: int) -> dict:
     }
 
 
+def model_bytes(n: int, M: int) -> dict:
+    """The byte model of the path (each state array read and written once, read-only inputs
+    read once, X^bar and the wavelet pyramid kept on chip by fusion, the NUFFT grids at the
+    minimum two-pass FFT): 912 N + 108 M per iteration, and the share of each single-kernel
+    stage under it. Level 1 of the analysis holds 24 N of the 36 N coefficients (A read and
+    written, gamma W read: 12 B each); the primal sweep reads and writes S, Z, C, D and the Dirac
+    coefficients (with their thresholds)."""
+    N = n * n
+    return {"iteration": 912 * N + 108 * M, "analysis": 12 * 24 * N, "primal": 96 * N + 12 * 4 * N}
+
+
+def stage_flops(n: int, M: int, W: int = 7) -> dict:
+    """Algorithmic FP32 FLOPs of the stages with a compute ceiling (2 per FMA). One level of one
+    basis of filter length LF over an m x m map costs 2 m^2 LF FMAs (rows, then columns, in the
+    polyphase form) in either direction, and the bases' lengths sum to 72 (db1..db8: 2..16):
+    1152 N at the finest level over 4 maps, plus the step-6 update (an FMA per level-1 detail).
+    Degridding: W^2 taps x 2 spectrum positions x 4 real FMAs per row, plus the mixing and the
+    dual update; gridding the mirror."""
+    N = n * n
+    return {"analysis": 1152 * N + 2 * 24 * N, "synthesis": 1152 * N + 8 * N,
+            "degrid": M * (W * W * 2 * 8 + 96), "grid": M * (W * W * 2 * 8 + 48)}
+
+
 # Stages that are a single kernel launch per iteration, and that kernel's name in ncu.
 SINGLE_KERNEL_STAGES = {"primal": "k_primal", "analysis": "k_ana_l1", "synthesis": "k_syn2_fine",
                         "degrid": "k_degrid", "grid": "k_grid"}
@@ -134,6 +157,10 @@ def stage_kernel(stage: str, tuning: list) -> str:
     """Name of the kernel a single-kernel stage launches under the handle's launch choices."""
     if stage == "analysis" and tuning[3] == 1:
         return "k_ana_pers"
+    if stage == "analysis" and tuning[3] >= 2:
+        return "k_ana_l1m"
+    if stage == "synthesis" and tuning[0] == 2:
+        return "k_syn2_fine_pers"
     return SINGLE_KERNEL_STAGES[stage]
 
 
@@ -239,66 +266,68 @@ def cpu_threads() -> int:
 
 
 # ------------------------------------------------------------------ batched and served
-def draw_requests(count: int, seed: int):
+def draw_requests(count: int, seed: int, large: bool = False):
     """Independent problems of the batched workload: sizes 64/128/256/512 with weights
-    0.4/0.3/0.2/0.1, M uniform in [2k, 200k], input SNR uniform in [20, 40] dB."""
-    from paper_1801_02417_gb300.serve import SIZE_MIX, synthesize_problem
+    0.4/0.3/0.2/0.1, M uniform in [2k, 200k], input SNR uniform in [20, 40] dB, 4 levels.
+    large=True: the served stream's large jobs instead, 1024^2 with M uniform in [200k, 2M]."""
+    from paper_1801_02417_gb300.serve import LARGE_JOBS, SIZE_MIX, synthesize_problem
     rng = np.random.default_rng(seed)
     sizes = [n for n, _ in SIZE_MIX]
     probs = [p for _, p in SIZE_MIX]
     out = []
     for i in range(count):
-        n = int(rng.choice(sizes, p=probs))
-        M = int(rng.integers(2000, 200001))
-        nb = 1 if M < 50000 else 4
+        if large:
+            n, (m0, m1) = LARGE_JOBS[0], LARGE_JOBS[2]
+        else:
+            n, (m0, m1) = int(rng.choice(sizes, p=probs)), (2000, 200000)
+        M = int(rng.integers(m0, m1 + 1))
+        nb = 1 if M < 50000 else (4 if M < 500000 else 32)
         out.append(synthesize_problem(n, 4, M, seed + 100 + i, nb, snr_db=float(rng.uniform(20, 40))))
     return out
 
 
-def batched_measure(problems, iters: int) -> dict:
-    """All problems advanced by one graph launch per iteration vs the same problems one after another."""
-    import torch
-    from paper_1801_02417_gb300 import binding as B
-    from paper_1801_02417_gb300.solver import PolarizedSARA
+def batched_measure(problems, iterations: int = 500, reweights: int = 5) -> dict:
+    """Whole Algorithm 2 solves (NNLS start, `reweights` reweighted cycles, `iterations` in
+    all) of every problem: the batched path (every cycle advances all problems by one batch
+    graph launch per iteration, solver.solve_batched) against the same solves one after
+    another on the plain single-solve path. Launch choices from the autotuner, one run per
+    size class, for both."""
+    from paper_1801_02417_gb300.serve import apply_tuning
+    from paper_1801_02417_gb300.solver import PolarizedSARA, Schedule, solve_batched
 
     def start(p):
         s = PolarizedSARA(p.n, p.levels)
         s.set_measurements(p.uv, p.vis, p.weights, p.offsets, p.eps)
-        s.set_sara_weights(None, p.gamma)
+        apply_tuning(s, p.n, p.uv.shape[0], cache)
         return s
-    from paper_1801_02417_gb300.serve import apply_tuning
-    cache = {}                          # launch choices from the autotuner, one run per size class
+    cache = {}
+    schedules = [Schedule(iterations, reweights, p.gamma) for p in problems]
+    # Preparation (handles, row sort, operator norm, tuning) is outside both timings.
     seq = 0.0
-    for p in problems:
+    for p, sch in zip(problems, schedules):
         with start(p) as s:
-            apply_tuning(s, p.n, p.uv.shape[0], cache)
-            s.pd_iterate(3)
             s.synchronize()
             t = time.perf_counter()
-            s.pd_iterate(iters)
+            s.solve(sch)
             s.synchronize()
             seq += time.perf_counter() - t
     ss = [start(p) for p in problems]
-    for p, s in zip(problems, ss):
-        apply_tuning(s, p.n, p.uv.shape[0], cache)
-    b = B.ps_batch_create([s.h for s in ss])
     try:
-        B.ps_batch_iterate(b, 3)
-        B.ps_batch_synchronize(b)
-        torch.cuda.synchronize()
+        for s in ss:
+            s.synchronize()
         t = time.perf_counter()
-        B.ps_batch_iterate(b, iters)
-        B.ps_batch_synchronize(b)
+        solve_batched(ss, schedules)
         bat = time.perf_counter() - t
     finally:
-        B.ps_batch_destroy(b)
         for s in ss:
             s.close()
     k = len(problems)
-    return {"problems": k, "iterations": iters, "sizes": sorted({p.n for p in problems}),
-            "tuning": {f"n{key[0]}_M<2^{key[1]}": v[:2] for key, v in sorted(cache.items())},
+    return {"problems": k, "iterations": iterations, "reweights": reweights,
+            "sizes": {str(n): sum(p.n == n for p in problems) for n in sorted({p.n for p in problems})},
+            "tuning": {f"n{key[0]}_M<2^{key[1]}": v for key, v in sorted(cache.items())},
             "batched_s": bat, "sequential_s": seq, "speedup": seq / bat,
-            "solve_iters_per_s_batched": k * iters / bat, "solve_iters_per_s_sequential": k * iters / seq}
+            "solves_per_s_batched": k / bat, "solves_per_s_sequential": k / seq,
+            "solve_iters_per_s_batched": k * iterations / bat, "solve_iters_per_s_sequential": k * iterations / seq}
 
 
 def default_gamma(s, dirty: np.ndarray, factor: float = 1e-3) -> float:
@@ -367,13 +396,28 @@ def np_comparison(wl_name: str = "img256_m50k", iterations: int = 0, reweights: 
     return out
 
 
-def served_measure(pool, rate: float, duration: float, seed: int) -> dict:
-    from paper_1801_02417_gb300.serve import Policy, Server, request_stream, summarize
-    reqs = request_stream(rate, duration, seed, pool)
-    pol = Policy(rel_tol=1e-4, max_iter=2000, reweights=5, check_every=20)
-    cont = summarize(Server(hbm_budget=64 << 30, max_active=32, policy=pol).run(reqs))
-    solo = summarize(Server(hbm_budget=64 << 30, max_active=1, policy=pol).run(reqs))
+def served_measure(pool, large_pool, rate: float, duration: float, seed: int, solo_seconds: float) -> dict:
+    """The served stream: Poisson arrivals at `rate`/s for `duration` s drawn from the batched
+    mix plus a 5 % share of large (1024^2) jobs, each solved to a relative change of 1e-4 per
+    cycle (Eq. stop_crit, <= 2000 iterations, 5 reweights), admitted by device footprint,
+    state resident, overlapping on the device (continuous batching). The one-at-a-time path
+    serves the first `solo_seconds` of the same arrivals (a bounded sample: it falls behind the
+    arrival rate, so its queue, and its latencies, grow with the window)."""
+    from paper_1801_02417_gb300.serve import LARGE_JOBS, Policy, Server, request_stream, summarize
+    reqs = request_stream(rate, duration, seed, pool, large_pool, LARGE_JOBS[1])
+    pol = Policy(rule="rel", rel_tol=1e-4, max_iter=2000, reweights=5, check_every=20)
+    t0 = time.perf_counter()
+    res = Server(hbm_budget=64 << 30, max_active=32, policy=pol).run(reqs)
+    wall = time.perf_counter() - t0
+    cont = summarize(res)
+    big = [r for r in res if reqs[r.rid][1].n == LARGE_JOBS[0]]
+    cont["large_jobs"] = summarize(big) if big else {"solves": 0}
+    solo_reqs = [r for r in reqs if r[0] <= solo_seconds]
+    solo = summarize(Server(hbm_budget=64 << 30, max_active=1, policy=pol).run(solo_reqs))
+    solo["window_s"] = solo_seconds
     return {"rate_per_s": rate, "duration_s": duration, "requests": len(reqs),
+            "large_share": LARGE_JOBS[1], "large_requests": sum(1 for _, p in reqs if p.n == LARGE_JOBS[0]),
+            "rule": "relative change <= 1e-4 per cycle (Eq. stop_crit)", "wall_s": wall,
             "continuous_batching": cont, "one_at_a_time": solo}
 
 
@@ -383,7 +427,7 @@ def hyperspectral_measure(nchan: int = 8, n: int = 256, M: int = 50000, seed: in
     continuous-batching server (each on its own stream, overlapping) vs one after another."""
     from paper_1801_02417_gb300.serve import Policy, Server, summarize, synthesize_channels
     chans = synthesize_channels(n, 4, M, nchan, seed, nblocks=8)
-    pol = Policy(rel_tol=1e-4, max_iter=2000, reweights=5, check_every=20)
+    pol = Policy(rule="rel", rel_tol=1e-4, max_iter=2000, reweights=5, check_every=20)
     reqs = [(0.0, p) for p in chans]
     t0 = time.perf_counter()
     cont = Server(hbm_budget=64 << 30, max_active=nchan, policy=pol).run(reqs)
@@ -524,7 +568,11 @@ def run_own(args) -> None:
     stages = B.ps_profile_stages(s.h, prof_iters)
     Wd = window_side(uv, n)
     sbytes = stage_bytes(n, L, M, Wd)
-    # Dominant kernel: the slowest stage that is one kernel launch per iteration.
+    mbytes = model_bytes(n, M)
+    sflops = stage_flops(n, M)
+    # Dominant kernel: the slowest stage that is one kernel launch per iteration. Its bytes are
+    # the byte model's share where the model assigns one (the level-1 analysis: A read and
+    # written, gamma W read), else every array it touches once.
     dom = max(SINGLE_KERNEL_STAGES, key=lambda k: stages[k])
     peaks = {}
     try:
@@ -533,27 +581,32 @@ def run_own(args) -> None:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    achieved = sbytes[dom] / (stages[dom] * 1e-3) / 1e9
+    dom_bytes = mbytes.get(dom, sbytes[dom])
+    achieved = dom_bytes / (stages[dom] * 1e-3) / 1e9
     dom_kernel = stage_kernel(dom, B.ps_get_tuning(s.h))
     traffic, traffic_src = dram_traffic(dom_kernel, wl.name)
     total_bytes = sum(sbytes.values())
+    fp32 = {"packed_flops": B.ps_fp32_peak(True), "scalar_flops": B.ps_fp32_peak(False)}
+    fp32_peak = max(fp32["packed_flops"], fp32["scalar_flops"])
 
     # End to end through the C ABI with host buffers (pinned), as a user runs a solve:
     # upload of the measurements (row sort, operator-norm estimate), then per step one
     # iteration and a device->host read of its stopping metric (the per-map relative
     # change of Eq. stop_crit), and the Stokes maps read back once at the end.
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.kernels_only:
         uv_p = torch.from_numpy(uv).pin_memory()
         Y_p = torch.from_numpy(Y.view(np.float32)).pin_memory()
         w_p = torch.from_numpy(w).pin_memory()
         out_p = torch.empty((4, n, n), dtype=torch.float32).pin_memory()
-        ke = max(1, args.steps)
+        ke = wl.iterations                              # one solve of the workload's length (1,000 iterations)
         nparts = 8 * ((n * n + 1023) // 1024)          # FP64 partials behind ps_get_rel_change
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         B.ps_set_measurements(s.h, uv_p, Y_p, w_p, off, eps)
         s.set_sara_weights(None, gamma)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
         for _ in range(ke):
             s.pd_iterate(1)
             B.ps_get_rel_change(s.h)
@@ -572,13 +625,15 @@ def run_own(args) -> None:
         tm = time.perf_counter() - t1
         e2e = {"value": ke / te, "unit": "iter/s", "h2d_bytes_per_step": int(h2d / ke),
                "d2h_bytes_per_step": int(8 * nparts + out_p.numel() * 4 / ke),
-               "note": "pinned host measurements uploaded once (row sort, operator-norm estimate), then per step one "
-                       "iteration + read of its relative-change metric; Stokes maps read once at the end",
+               "solve_iterations": ke, "setup_s": t_setup, "steps_only_value": ke / (te - t_setup),
+               "note": f"one {ke}-iteration solve through the C ABI from pinned host buffers: measurements uploaded "
+                       "once (row sort, operator-norm estimate, default gamma: setup_s), then per step one iteration "
+                       "+ read of its relative-change metric; Stokes maps read once at the end",
                "maps_every_step": {"value": km / tm, "unit": "iter/s", "d2h_bytes_per_step": int(out_p.numel() * 4)}}
 
     # The direct cone-dual variant (PS_SOC: no Z, D) on the same problem and launch path.
     soc = None
-    if rank == 0:
+    if rank == 0 and not args.kernels_only:
         s.set_mode(B.PS_SOC)
         s.pd_iterate(args.warmup)
         torch.cuda.synchronize()
@@ -595,7 +650,7 @@ def run_own(args) -> None:
     # The TV problem with the constraint (Algorithm 3) on the same data and launch path:
     # the gradient step replaces the data dual, grad replaces the SARA dictionary.
     tvv = None
-    if rank == 0:
+    if rank == 0 and not args.kernels_only:
         B.ps_set_tv_weights(s.h, [1e-3 * gamma * 3.0] * 4)
         s.set_mode(B.PS_TV)
         s.pd_iterate(args.warmup)
@@ -612,17 +667,19 @@ def run_own(args) -> None:
         s.set_mode(B.PS_POLARIZED)
 
     batched = served = np_cmp = hyper = None
-    if rank == 0 and world == 1 and not args.no_serve:
+    if rank == 0 and world == 1 and not args.no_serve and not args.kernels_only:
         np_cmp = np_comparison()
         s.close()
         pool = draw_requests(args.batch, seed=wl.seed + 50)
-        batched = batched_measure(pool, iters=50)
-        served = served_measure(pool, rate=args.serve_rate, duration=args.serve_seconds, seed=wl.seed + 60)
+        batched = batched_measure(pool)
+        large = draw_requests(4, seed=wl.seed + 55, large=True)
+        served = served_measure(pool, large, rate=args.serve_rate, duration=args.serve_seconds, seed=wl.seed + 60,
+                                solo_seconds=min(args.serve_seconds, args.solo_seconds))
         hyper = hyperspectral_measure(seed=wl.seed + 70)
         s = None
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernels_only:
         r = oracle_sample(n, L, uv, w.astype(np.float64), M, budget_s=20.0)
         cpu = {"value": 1.0 / r["seconds_per_iter"], "unit": "iter/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": (f"FP64 oracle: per-pixel steps on full {n}^2 maps ({r['t_pixels']:.2f}s), "
@@ -643,13 +700,25 @@ def run_own(args) -> None:
             "roofline": {"bound": "hbm", "kernel": dom_kernel, "stage": dom, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_source": traffic_src, "peak_source": peak_src + " hbm_gbs (copy)",
-                         "algorithmic_bytes": sbytes[dom], "launch_ms": stages[dom]},
+                         "algorithmic_bytes": dom_bytes, "bytes_model": "byte model share" if dom in mbytes
+                         else "every array touched once", "all_arrays_bytes": sbytes[dom],
+                         "launch_ms": stages[dom]},
             "stage_roofline": {k: {"ms": stages[k], "algorithmic_bytes": sbytes[k],
-                                   "frac": sbytes[k] / (stages[k] * 1e-3) / 1e9 / peak if stages[k] > 0 else None}
+                                   "frac": sbytes[k] / (stages[k] * 1e-3) / 1e9 / peak if stages[k] > 0 else None,
+                                   **({"model_bytes": mbytes[k],
+                                       "model_frac": mbytes[k] / (stages[k] * 1e-3) / 1e9 / peak} if k in mbytes
+                                      else {}),
+                                   **({"flops": sflops[k],
+                                       "fp32_frac": sflops[k] / (stages[k] * 1e-3) / fp32_peak} if k in sflops
+                                      else {})}
                                for k in stages},
-            "iteration_roofline": {"algorithmic_bytes": total_bytes,
-                                   "achieved_gbs": total_bytes / (ms_per_step * 1e-3) / 1e9,
-                                   "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+            "fp32_peak": {"packed_tflops": fp32["packed_flops"] / 1e12, "scalar_tflops": fp32["scalar_flops"] / 1e12,
+                          "source": "ps_fp32_peak, measured in this run (FMA chains on every SM)"},
+            "iteration_roofline": {"algorithmic_bytes": mbytes["iteration"], "model": "912 N + 108 M",
+                                   "achieved_gbs": mbytes["iteration"] / (ms_per_step * 1e-3) / 1e9,
+                                   "frac": mbytes["iteration"] / (ms_per_step * 1e-3) / 1e9 / peak,
+                                   "stage_bytes_sum": total_bytes,
+                                   "stage_bytes_frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
             "stages_ms": stages,
             "clocks": clk,
             "gpu_launches": launches,
@@ -679,9 +748,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="", help="force the launch choices (comma-separated PS_TUNE_* values)")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the timed iterations and the stage timing (for profiler runs)")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batched measurement")
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-seconds", type=float, default=120.0)
+    ap.add_argument("--solo-seconds", type=float, default=15.0,
+                    help="arrival window served by the one-at-a-time comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -335,7 +335,9 @@ ps_status ps_max_abs_analysis(ps_handle* h, double* out);
  * joined back to the batch stream, so one launch advances all problems and their
  * kernels overlap on the device. Handles keep their own state, mode and step sizes;
  * they must have distinct streams and measurements set. The graph is rebuilt when a
- * handle's mode or state changes. The batch does not own the handles. */
+ * handle's mode or state changes. ps_batch_iterate orders the work already queued on
+ * each handle's stream (a reweight, new thresholds) before its iterations, and each
+ * handle's later calls after them. The batch does not own the handles. */
 typedef struct ps_batch ps_batch;
 ps_status ps_batch_create(ps_handle* const* handles, int32_t count, void* cuda_stream, ps_batch** out);
 ps_status ps_batch_iterate(ps_batch* b, int32_t n_iter);   /* asynchronous on the batch stream */
@@ -348,16 +350,25 @@ void ps_batch_destroy(ps_batch* b);
  * so it is measured on the handle's own problem). Values index the candidates: */
 enum {
   PS_TUNE_SYNTHESIS = 0,  /* finest synthesis level: 0 double-buffered subband staging (2 CTAs/SM),
-                             1 single-buffered, refilled during the x-pass (4 CTAs/SM) */
+                             1 single-buffered, refilled during the x-pass (4 CTAs/SM),
+                             2 as 1 in persistent CTAs looping over (tile, map) units, the staging
+                               running on from one unit into the next */
   PS_TUNE_DEGRID = 1,     /* 0 one row per thread over a work item,
                              1 one same-cell chunk per warp (broadcast stencil reads) */
   PS_TUNE_GRID = 2,       /* 0 one warp per same-cell chunk (2 kernel cells per lane),
                              1 half-warps on alternate rows of a chunk (4 cells per lane),
                              2 lanes own (stencil row, channel pair) (W <= 8; W = 9 runs 0),
                              3 tensor cores: each chunk's block as a small matrix product
-                               (TF32 hi/lo split, FP32 accumulation) (W <= 8; W = 9 runs 0) */
+                               (TF32 hi/lo split, FP32 accumulation), kernel weights copied from a
+                               per-row table made once per measurement set (W <= 8; W = 9 runs 0),
+                             4 as 3 with the kernel weights evaluated in the kernel (no table
+                               traffic) (W <= 8; W = 9 runs 0) */
   PS_TUNE_ANALYSIS = 3,   /* tiled analysis levels: 0 one (tile, basis, map) unit per CTA,
-                             1 persistent (2 CTAs/SM looping over units, next unit's copies in flight) */
+                             1 persistent (2 CTAs/SM looping over units, next unit's copies in flight),
+                             2 level 1 with one CTA per (tile, map): the map's input tile copied once for
+                               the 8 bases, each basis' staged A and gamma W in flight during the previous
+                               basis (levels >= 2 as 0),
+                             3 as 2 with one CTA per (tile, 4 bases, map) */
   PS_TUNE_COUNT = 4
 };
 
@@ -377,6 +388,13 @@ ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms);
  * outside a slot's candidates). The defaults are 0. */
 ps_status ps_get_tuning(const ps_handle* h, int32_t* choices);
 ps_status ps_set_tuning(ps_handle* h, const int32_t* choices);
+
+/* Measured FP32 throughput of the current device, the compute ceiling of the FP32
+ * interpolation and wavelet kernels: independent FMA chains on every SM, packed FP32x2
+ * (fma.rn.f32x2, packed = 1) or scalar (packed = 0); *flops_per_s counts 2 FLOPs per
+ * FMA (a packed FMA is two). Allocates 4 bytes and a stream for the measurement,
+ * synchronises. No counterpart in the paper. */
+ps_status ps_fp32_peak(int32_t packed, double* flops_per_s);
 
 /* Synchronise the handle's stream; reports a pending CUDA error. */
 ps_status ps_synchronize(ps_handle* h);

@@ -83,6 +83,7 @@ _SIGS = {
     "ps_apply_psi_static": (_I32, [_P, _P, _I32, _I32, _P]),
     "ps_static_status": (_I32, [_P]),
     "ps_debug_set_wait_polls": (_I32, [_I32]),
+    "ps_fp32_peak": (_I32, [_I32, ctypes.POINTER(_F64)]),
     "ps_set_visibilities": (_I32, [_H, _P, _I32]),
     "ps_get_rel_change": (_I32, [_H, _P]),
     "ps_max_abs_analysis": (_I32, [_H, ctypes.POINTER(_F64)]),
@@ -332,6 +333,13 @@ def ps_static_status(stream=None) -> None:
 def ps_debug_set_wait_polls(polls: int) -> None:
     """Test hook: bounded-wait poll budget of every kernel (0: give up at once; < 0: default)."""
     _check(None, lib().ps_debug_set_wait_polls(int(polls)))
+
+
+def ps_fp32_peak(packed: bool = True) -> float:
+    """Measured FP32 FLOP/s of the current device (packed FP32x2 or scalar FMA chains)."""
+    v = _F64()
+    _check(None, lib().ps_fp32_peak(int(bool(packed)), ctypes.byref(v)))
+    return v.value
 
 
 def ps_wavelet_filters() -> np.ndarray:

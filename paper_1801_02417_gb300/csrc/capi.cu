@@ -1282,7 +1282,7 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms) {
 
 // ---------------------------------------------------------------------------
 // Autotuner: candidates per PS_TUNE_* slot, each timed on the handle's own data.
-static const int kTuneCandidates[PS_TUNE_COUNT] = {2, 2, 4, 2};
+static const int kTuneCandidates[PS_TUNE_COUNT] = {3, 2, 5, 4};
 
 // Mean milliseconds of `reps` launches of f after one untimed launch.
 extern "C++" {
@@ -1448,7 +1448,9 @@ struct ps_batch {
   std::vector<Handle*> hs;
   std::vector<uint64_t> versions;
   std::vector<cudaEvent_t> join;
+  std::vector<cudaEvent_t> pre;    // each handle's own pending work, ordered before the batch's launches
   cudaEvent_t fork = nullptr;
+  cudaEvent_t done = nullptr;      // the batch's launches, ordered before each handle's later work
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaGraphExec_t graph = nullptr;
@@ -1464,7 +1466,9 @@ extern "C" void ps_batch_destroy(ps_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->pre) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -1501,13 +1505,16 @@ extern "C" ps_status ps_batch_create(ps_handle* const* handles, int32_t count, v
   } else {
     b->own_stream = true;
   }
-  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) {
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess) {
     ps_batch_destroy(b);
     return batch_fail(e, "batch_create: event");
   }
   b->join.resize(count, nullptr);
+  b->pre.resize(count, nullptr);
   for (int i = 0; i < count; ++i)
-    if ((e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming)) != cudaSuccess) {
+    if ((e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->pre[i], cudaEventDisableTiming)) != cudaSuccess) {
       ps_batch_destroy(b);
       return batch_fail(e, "batch_create: event");
     }
@@ -1573,10 +1580,20 @@ extern "C" ps_status ps_batch_iterate(ps_batch* b, int32_t n_iter) {
     ps_status st = batch_build(b);
     if (st != PS_OK) return st;
   }
+  // Work already queued on a handle's own stream (a reweight, new thresholds, a state
+  // upload) runs before the batch's iterations, and the handle's later work after them.
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    cudaError_t e = cudaEventRecord(b->pre[i], b->hs[i]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->pre[i], 0);
+    if (e != cudaSuccess) return batch_fail(e, "batch: ordering");
+  }
   for (int i = 0; i < n_iter; ++i) {
     cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
     if (e != cudaSuccess) return batch_fail(e, "batch: graph launch");
   }
+  cudaError_t e = cudaEventRecord(b->done, b->stream);
+  for (size_t i = 0; i < b->hs.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->hs[i]->stream, b->done, 0);
+  if (e != cudaSuccess) return batch_fail(e, "batch: ordering");
   for (Handle* h : b->hs) h->iterations += n_iter;
   return PS_OK;
 }

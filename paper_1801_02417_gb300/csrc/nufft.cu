@@ -529,7 +529,7 @@ constexpr int kGridRows3 = kGridItem + 8;
 // Floats of staged weights per work item (a multiple of 4: the tile planes after them stay 16-byte aligned).
 template <int W, int FORM>
 __host__ __device__ constexpr int grid_wts_floats() {
-  return FORM == 3 ? 16 * kGridRows3 : (2 * W * kGridV + 3) / 4 * 4;
+  return FORM >= 3 ? 16 * kGridRows3 : (2 * W * kGridV + 3) / 4 * 4;
 }
 
 // Step 1 for one visibility j of a work item: row record r (fx, fy, w), its correlations
@@ -548,6 +548,22 @@ __device__ __forceinline__ void grid_stage_row(int j, float4 r, float4 b0, float
   x4[2 * j + 1] = make_float4(sc * (b0.z + b1.x), sc * (b0.w + b1.y), -sc * (b1.y - b0.w), sc * (b1.x - b0.z));
   if (FORM == 3) {
     // Weights arrive by bulk copies from the per-row table (k_row_weights).
+  } else if (FORM == 4) {
+    // The layout of FORM 3, evaluated here instead of copied from the table.
+    float wx[W], wy[W];
+    es_weights<W>(fx, beta, wx);
+    es_weights<W>(fy, beta, wy);
+    float t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = k < W ? wy[k] : 0.f;
+    float4* py = reinterpret_cast<float4*>(wts) + 2 * j;
+    py[0] = make_float4(t[0], t[1], t[2], t[3]);
+    py[1] = make_float4(t[4], t[5], t[6], t[7]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = k < W ? wx[k] : 0.f;
+    float4* px = reinterpret_cast<float4*>(wts + 8 * kGridRows3) + 2 * j;
+    px[0] = make_float4(t[0], t[1], t[2], t[3]);
+    px[1] = make_float4(t[4], t[5], t[6], t[7]);
   } else {
     float wx[W], wy[W];
     es_weights<W>(fx, beta, wx);
@@ -590,7 +606,7 @@ __device__ __forceinline__ void grid_chunks(const int32_t* __restrict__ chunks, 
   for (int c = warp; c < nc; c += nwarps) {
     const int pk = chunks[c];
     const int v0 = pk & 1023, cnt = (pk >> 10) & 63, ly = (pk >> 16) & 255, lx = (pk >> 24) & 255;
-    if constexpr (FORM == 3) {
+    if constexpr (FORM >= 3) {
       // Tensor cores: the chunk's W x W x 8 block is the product G = P^T Y over its rows,
       // P[v][(jx, c)] = w_x[v][jx] x_c[v] (64 rows (jx, c) in MT m-tiles of 16) and
       // Y[v][jy] = w_y[v][jy] (8 columns), k = 8 rows per mma.m16n8k8 (TF32). Each FP32
@@ -811,7 +827,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
     const int j = threadIdx.x + q * kGridThreads;
     if (j < nv) grid_stage_row<W, FORM>(j, r[q], b0[q], b1[q], use_scale ? cb[blk[q]] : 1.0f, beta, x4, wts);
   }
-  if (FORM == 3 && threadIdx.x < 8) {
+  if (FORM >= 3 && threadIdx.x < 8) {
     // Spare rows after the item: finite (zero) operands for the last k-step of its last chunk.
     const int j = nv + threadIdx.x;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -999,11 +1015,11 @@ cudaError_t configure_nufft_kernels() {
   const void* grids[] = {(const void*)k_grid<5, 0>, (const void*)k_grid<7, 0>, (const void*)k_grid<9, 0>,
                          (const void*)k_grid<5, 1>, (const void*)k_grid<7, 1>, (const void*)k_grid<9, 1>,
                          (const void*)k_grid<5, 2>, (const void*)k_grid<7, 2>, (const void*)k_grid<5, 3>,
-                         (const void*)k_grid<7, 3>};
+                         (const void*)k_grid<7, 3>, (const void*)k_grid<5, 4>, (const void*)k_grid<7, 4>};
   const size_t grid_bytes[] = {grid_smem<5, 0>(), grid_smem<7, 0>(), grid_smem<9, 0>(), grid_smem<5, 1>(),
                                grid_smem<7, 1>(), grid_smem<9, 1>(), grid_smem<5, 2>(), grid_smem<7, 2>(),
-                               grid_smem<5, 3>(), grid_smem<7, 3>()};
-  for (int i = 0; i < 10; ++i)
+                               grid_smem<5, 3>(), grid_smem<7, 3>(), grid_smem<5, 4>(), grid_smem<7, 4>()};
+  for (int i = 0; i < 12; ++i)
     if ((e = set_smem(grids[i], grid_bytes[i])) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
   const void* degrids[] = {(const void*)k_degrid<5, 0>, (const void*)k_degrid<7, 0>, (const void*)k_degrid<9, 0>,
@@ -1098,12 +1114,13 @@ static void launch_grid_form(Handle* h, const float2* in, int use_scale) {
 
 template <int W>
 static void launch_grid(Handle* h, const float2* in, int use_scale) {
-  // FORM 2 needs 4 W <= 32 lanes and FORM 3 8 taps per row: W = 9 runs FORM 0 for both.
+  // FORM 2 needs 4 W <= 32 lanes and FORMs 3-4 8 taps per row: W = 9 runs FORM 0 for them.
   constexpr bool narrow = W <= 8;
   switch (h->tune[PS_TUNE_GRID]) {
     case 1: launch_grid_form<W, 1>(h, in, use_scale); break;
     case 2: launch_grid_form<W, narrow ? 2 : 0>(h, in, use_scale); break;
     case 3: launch_grid_form<W, narrow ? 3 : 0>(h, in, use_scale); break;
+    case 4: launch_grid_form<W, narrow ? 4 : 0>(h, in, use_scale); break;
     default: launch_grid_form<W, 0>(h, in, use_scale); break;
   }
 }

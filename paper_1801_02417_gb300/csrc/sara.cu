@@ -468,6 +468,76 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
                approx_out, mode, scale, gamma, delta, err);
 }
 
+// Level-1 analysis with the input tile shared by NB bases: one CTA per (tile, group of NB
+// bases, map). The 2 TO + 14 rows the db8 filter needs cover every shorter filter (same
+// origin), so the map's tile is copied once and each basis filters it from shared memory.
+// The staged A and gamma W rows of basis i + 1 (dual mode) are copied into the second of
+// two staging sets while basis i is filtered.
+constexpr int kAnaMFloats = kA2In + 2 * kRSmax * kPlo + 4 * kStage;
+static size_t multi_analysis_smem() { return (size_t)kAnaMFloats * sizeof(float) + 32; }
+
+template <int NB>
+__global__ void __launch_bounds__(256, 2) k_ana_l1m(const float* __restrict__ X, int n, int last,
+                                                    float* __restrict__ coef, float* __restrict__ thr,
+                                                    float* __restrict__ approx_out, int mode, float scale,
+                                                    float gamma, float delta, int* err) {
+  extern __shared__ float4 smm[];
+  float* in_s = reinterpret_cast<float*>(smm);
+  float* lo_s = in_s + kA2In;
+  float* hi_s = lo_s + kRSmax * kPlo;
+  float* st = hi_s + kRSmax * kPlo;                                 // set s: A at st + 2 s kStage, gamma W after it
+  uint64_t* bar = reinterpret_cast<uint64_t*>(st + 4 * kStage);    // [0] input tile, [1 + s] stage set s
+  const int map = blockIdx.z, b0 = blockIdx.y * NB;
+  const int hm = n >> 1, tilesx = hm / kTO;
+  const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
+  const bool staged = mode == SARA_DUAL;
+  auto plane = [&](int bi) { return ((size_t)map * kBases + bi + 1) * (size_t)n * n; };
+  auto set_a = [&](int s) { return st + 2 * s * kStage; };
+  auto set_t = [&](int s) { return st + (2 * s + 1) * kStage; };
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) mbar_init(&bar[q], 1);
+  __syncthreads();
+  ana_issue_input(X + (size_t)map * n * n, n, oy0, ox0, kRSmax, in_s, &bar[0]);
+  if (staged) stage_epilogue(coef, thr, plane(b0), n, hm, oy0, ox0, set_a(0), set_t(0), &bar[1]);
+  const bool ok = mbar_wait(&bar[0], 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      (void)mbar_drain(&bar[0], 0);
+      if (staged) (void)mbar_drain(&bar[1], 0);
+    }
+    return;   // the CTA's tiles are left unchanged (the host reports PS_ETIMEOUT)
+  }
+  for (int i = 0; i < NB; ++i) {
+    const int bi = b0 + i, s = i & 1;
+    // Set s ^ 1 was last read by basis i - 1, which ended at a barrier: refill it for basis i + 1.
+    if (staged && i + 1 < NB)
+      stage_epilogue(coef, thr, plane(bi + 1), n, hm, oy0, ox0, set_a(s ^ 1), set_t(s ^ 1), &bar[1 + (s ^ 1)]);
+#define PS_MR(LFv) ana_rows<LFv>(in_s, lo_s, hi_s)
+    PS_SWITCH_LF(bi, PS_MR)
+#undef PS_MR
+    if (staged) {
+      const bool ok2 = mbar_wait(&bar[1 + s], (uint32_t)((i >> 1) & 1));
+      if (__syncthreads_or(!ok2)) {
+        if (threadIdx.x == 0) {
+          atomicExch(err, 1);
+          (void)mbar_drain(&bar[1 + s], (uint32_t)((i >> 1) & 1));
+          if (i + 1 < NB) (void)mbar_drain(&bar[1 + (s ^ 1)], (uint32_t)(((i + 1) >> 1) & 1));
+        }
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
+#define PS_MC(LFv)                                                                                          \
+  ana_cols<LFv>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, \
+                set_a(s), set_t(s))
+    PS_SWITCH_LF(bi, PS_MC)
+#undef PS_MC
+    __syncthreads();   // lo/hi and stage set s consumed before the next basis
+  }
+}
+
 // Persistent form of the tiled analysis levels: 2 CTAs per SM loop over the units
 // (tile, basis, map) of a level, tile fastest. A unit's input rows are copied while
 // the previous unit's columns are filtered, and its staged A and gamma W rows
@@ -912,6 +982,66 @@ __global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
   }
 }
 
+// Persistent form of the finest level: the CTAs (4 per SM) loop over the (tile, map) units,
+// and the single staging set runs on across units: the copies of the next unit's first
+// basis go out right after the y-pass of the current unit's last basis, so neither a
+// CTA's start nor the end of a unit exposes a copy's latency, and no wave runs part-full.
+__global__ void __launch_bounds__(256, 4)
+    k_syn2_fine_pers(const float* __restrict__ coef, const float* __restrict__ approx_in, int coarsest, int n,
+                     float* __restrict__ out, int* err) {
+  extern __shared__ float4 sm2[];
+  float* const s4 = reinterpret_cast<float*>(sm2);
+  float* loT = s4 + kC2Set;
+  float* hiT = loT + kLoSize;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hiT + kLoSize);
+  const int tilesx = n / kT2, units = tilesx * tilesx * 4;
+  const int hm = n >> 1;
+  auto issue = [&](int unit, int bi) {
+    const int map = unit / (tilesx * tilesx), t = unit % (tilesx * tilesx);
+    const int oy0 = (t / tilesx) * kT2, ox0 = (t % tilesx) * kT2;
+    const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
+    const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
+    syn2_issue(bi, cb, apx, n, hm, oy0, ox0, s4, bar);
+  };
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;            // uses of the barrier so far (each copy set completes one phase)
+  int unit = blockIdx.x;
+  if (unit < units) issue(unit, 0);
+  for (; unit < units; unit += gridDim.x) {
+    const int map = unit / (tilesx * tilesx), t = unit % (tilesx * tilesx);
+    const int oy0 = (t / tilesx) * kT2, ox0 = (t % tilesx) * kT2;
+    u64 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0ull;
+    for (int bi = 0; bi < kDb; ++bi, ++phase) {
+      const bool ok = mbar_wait(bar, phase & 1);
+      // Also orders the previous x-pass' reads of loT/hiT before this y-pass writes them.
+      if (__syncthreads_or(!ok)) {
+        syn2_abort(bar, phase & 1, nullptr, 0u, err);
+        return;
+      }
+      syn2_ypass_dispatch(bi, s4, loT, hiT);
+      __syncthreads();
+      // The staging set is free once every y-pass read of it has passed the barrier above.
+      if (bi + 1 < kDb) issue(unit, bi + 1);
+      else if (unit + (int)gridDim.x < units) issue(unit + gridDim.x, 0);
+      syn2_xpass_dispatch(bi, loT, hiT, acc);
+    }
+    const int rq = threadIdx.x & 15, cg = threadIdx.x >> 4;
+    const float k3 = 1.0f / 3.0f;
+    const float* cmap = coef + (size_t)map * kBases * n * n;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const size_t o = (size_t)(oy0 + 4 * rq + rr) * n + ox0 + 4 * cg;
+      const float4 d = *reinterpret_cast<const float4*>(cmap + o);
+      const float4 sv = syn2_row(acc, rr);
+      *reinterpret_cast<float4*>(out + (size_t)map * n * n + o) =
+          make_float4((d.x + sv.x) * k3, (d.y + sv.y) * k3, (d.z + sv.z) * k3, (d.w + sv.w) * k3);
+    }
+  }
+}
+
 // Coarser levels with output side m >= 64: one basis per CTA (grid.y), output to approximation scratch.
 __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ coef, const float* __restrict__ approx_in,
                                                     int coarsest, int m, int n, float* __restrict__ approx_out,
@@ -1138,7 +1268,17 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute((const void*)k_syn2_lv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syn2_smem(1));
   if (e != cudaSuccess) return e;
-  for (const void* f : {(const void*)k_syn2_fine<2>, (const void*)k_syn2_fine<1>, (const void*)k_syn2_lv}) {
+  e = cudaFuncSetAttribute((const void*)k_syn2_fine_pers, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syn2_smem(1));
+  if (e != cudaSuccess) return e;
+  for (const void* f : {(const void*)k_syn2_fine<2>, (const void*)k_syn2_fine<1>, (const void*)k_syn2_lv,
+                        (const void*)k_syn2_fine_pers}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  for (const void* f : {(const void*)k_ana_l1m<8>, (const void*)k_ana_l1m<4>}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)multi_analysis_smem());
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
@@ -1172,7 +1312,20 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
   for (int l = 1; l < lt; ++l) {
     const int m = n >> (l - 1), hm = m / 2;
     const dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
-    if (h->tune[PS_TUNE_ANALYSIS] == 1) {
+    if (l == 1 && h->tune[PS_TUNE_ANALYSIS] >= 2) {
+      const int nb = h->tune[PS_TUNE_ANALYSIS] == 2 ? 8 : 4;
+      const dim3 gm((hm / kTO) * (hm / kTO), kDb / nb, 4);
+      if (nb == 8)
+        k_ana_l1m<8><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode, scale,
+                                                                    gamma, delta, h->dev_flags);
+      else
+        k_ana_l1m<4><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode, scale,
+                                                                    gamma, delta, h->dev_flags);
+      if (fine_done) {
+        const cudaError_t e = cudaEventRecord(fine_done, h->stream);
+        if (e != cudaSuccess) return e;
+      }
+    } else if (h->tune[PS_TUNE_ANALYSIS] == 1) {
       const int units = (int)(grid.x * grid.y * grid.z);
       const int ctas = std::min(units, 2 * std::max(1, h->num_sms));
       const float* in = l == 1 ? X : buf[(l - 2) & 1];
@@ -1237,7 +1390,14 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
     }
     if (m >= kT2 && l == 1) {
       const dim3 grid((m / kT2) * (m / kT2), 1, 4);
-      if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err);
+      if (variant == 2) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int units = (int)(grid.x * grid.z);
+        k_syn2_fine_pers<<<std::min(units, 4 * std::max(1, sms)), 256, syn2_smem(1), stream>>>(coef, ain, l == L, n,
+                                                                                              out, err);
+      } else if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err);
       else k_syn2_fine<2><<<grid, 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err);
     } else if (m >= kT2) {
       k_syn2_lv<<<dim3((m / kT2) * (m / kT2), kDb, 4), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,

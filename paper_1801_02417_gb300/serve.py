@@ -423,14 +423,22 @@ def synthesize_channels(n: int, levels: int, M: int, nchan: int, seed: int, nblo
 
 
 SIZE_MIX = ((64, 0.4), (128, 0.3), (256, 0.2), (512, 0.1))
+# The served stream adds a share of large jobs to that mix: 1024^2 images with M uniform in
+# [200k, 2M] rows, 5 % of the requests.
+LARGE_JOBS = (1024, 0.05, (200_000, 2_000_000))
 
 
-def request_stream(rate: float, duration: float, seed: int, pool: list[Problem]) -> list[tuple[float, Problem]]:
-    """Poisson arrivals at `rate` per second over `duration` seconds, each a draw from `pool`."""
+def request_stream(rate: float, duration: float, seed: int, pool: list[Problem],
+                   large_pool: list[Problem] | None = None, large_share: float = 0.0) -> list[tuple[float, Problem]]:
+    """Poisson arrivals at `rate` per second over `duration` seconds, each a draw from `pool`,
+    or with probability `large_share` from `large_pool`."""
     rng = np.random.default_rng(seed)
     t, out = 0.0, []
     while True:
         t += rng.exponential(1.0 / rate)
         if t > duration:
             return out
-        out.append((t, pool[int(rng.integers(len(pool)))]))
+        if large_pool and rng.random() < large_share:
+            out.append((t, large_pool[int(rng.integers(len(large_pool)))]))
+        else:
+            out.append((t, pool[int(rng.integers(len(pool)))]))

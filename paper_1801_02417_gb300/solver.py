@@ -177,3 +177,37 @@ class PolarizedSARA:
             cycle()
             delta *= delta_decay
         return {"iterations": used, "S": self.get_stokes()}
+
+
+def solve_batched(solvers: list, schedules: list, mode: int = B.PS_POLARIZED) -> list:
+    """Algorithm 2 (NNLS start, reweighted cycles) for many independent problems at once.
+
+    Every cycle advances all problems together: one launch of a batch graph (ps_batch_*)
+    per iteration holds one iteration of every problem, each on its own stream, so the
+    kernels of different problems overlap on the device. The schedules must share their
+    iteration count and reweight count (the cycles run in lockstep); gamma and the delta
+    schedule are each problem's own. Returns the Stokes maps of every problem.
+    """
+    shapes = {(sch.iterations, sch.reweights) for sch in schedules}
+    if len(shapes) != 1 or len(schedules) != len(solvers):
+        raise ValueError("solve_batched: one schedule per solver, all with the same iterations and reweights")
+    iterations, reweights = shapes.pop()
+    per = iterations // (reweights + 1)
+    for s in solvers:
+        s.set_mode(B.PS_NNLS)
+    b = B.ps_batch_create([s.h for s in solvers])
+    try:
+        B.ps_batch_iterate(b, per)
+        deltas = [sch.delta_factor * B.ps_max_abs_analysis(s.h) for s, sch in zip(solvers, schedules)]
+        for s, sch in zip(solvers, schedules):
+            s.set_sara_weights(None, sch.gamma)
+            s.set_mode(mode)
+        for _ in range(reweights):
+            for s, d in zip(solvers, deltas):
+                s.reweight(d)
+            B.ps_batch_iterate(b, per)
+            deltas = [d * sch.delta_decay for d, sch in zip(deltas, schedules)]
+        B.ps_batch_synchronize(b)
+    finally:
+        B.ps_batch_destroy(b)
+    return [s.get_stokes() for s in solvers]

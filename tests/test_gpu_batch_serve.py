@@ -17,7 +17,7 @@ from oracle import primal_dual as opd
 from oracle import wavelets as wav
 from paper_1801_02417_gb300 import binding as B
 from paper_1801_02417_gb300.serve import Policy, Problem, Server, synthesize_problem
-from paper_1801_02417_gb300.solver import PolarizedSARA
+from paper_1801_02417_gb300.solver import PolarizedSARA, Schedule, solve_batched
 from problems import make_channel_problem, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +64,26 @@ def test_batch_graph_matches_individual_iterations(problems):
         B.ps_batch_destroy(b)
         for s in ss:
             s.close()
+
+
+def test_batched_algorithm2_matches_solo_solves(problems):
+    """Whole Algorithm 2 solves run in lockstep through one batch graph per iteration
+    (solver.solve_batched: reweights queued on each handle's stream between batch launches)
+    give each problem the maps of its solo solve."""
+    sch = [Schedule(150, 2, p.gamma) for p in problems]
+    solo = []
+    for p, sc in zip(problems, sch):
+        with _start(p) as s:
+            solo.append(s.solve(sc))
+    ss = [_start(p) for p in problems]
+    try:
+        got = solve_batched(ss, sch)
+    finally:
+        for s in ss:
+            s.close()
+    for g, r in zip(got, solo):
+        for k in range(4):
+            assert _rel(g[k], r[k]) <= TOL_FINAL, k
 
 
 def test_each_request_same_alone_and_in_the_mix(problems):

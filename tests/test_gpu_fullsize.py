@@ -93,7 +93,7 @@ def test_phi_adjoint_every_gridding_choice(big):
     saved = B.ps_get_tuning(s.h)
     maps = []
     try:
-        for choice in range(4):
+        for choice in range(5):
             B.ps_set_tuning(s.h, saved[:2] + [choice] + saved[3:])
             img = np.empty((4, WL.n, WL.n), np.float32)
             B.ps_apply_phi_adjoint(s.h, Y, img)
@@ -156,3 +156,36 @@ def test_one_iteration_per_pixel_step_at_sampled_pixels(big):
     assert _rel(got["Z"][:, pix[:, 0], pix[:, 1]], Z1) <= 2e-5
     assert _rel(got["C"][:, pix[:, 0], pix[:, 1]], C1) <= 2e-5
     assert _rel(got["D"][:, pix[:, 0], pix[:, 1]], D1) <= 2e-5
+
+
+def test_sara_every_launch_choice_full_maps(big):
+    """Every finest-level synthesis form (the persistent one loops over several (tile, map)
+    units per CTA only at this size) and every level-1 analysis form against the oracle's
+    transforms of one map, and all forms agree with each other over the four maps."""
+    s = big["s"]
+    rng = np.random.default_rng(17)
+    A = rng.normal(size=(4, 9, WL.n, WL.n)).astype(np.float32)
+    S = big["truth"]
+    ref_syn = wav.psi(A[1:2].astype(np.float64), WL.levels)[0]
+    ref_ana = wav.psi_adjoint(S[3:4].astype(np.float64), WL.levels)[0]
+    saved = B.ps_get_tuning(s.h)
+    outs, coefs = [], []
+    try:
+        for syn in range(3):
+            B.ps_set_tuning(s.h, [syn] + saved[1:])
+            back = np.empty((4, WL.n, WL.n), np.float32)
+            B.ps_apply_psi(s.h, A, back)
+            assert _rel(back[1], ref_syn) <= 1e-6, syn
+            outs.append(back)
+        for ana in range(4):
+            B.ps_set_tuning(s.h, saved[:3] + [ana])
+            C = np.empty((4, 9, WL.n, WL.n), np.float32)
+            B.ps_apply_psi_adjoint(s.h, S, C)
+            assert _rel(C[3], ref_ana) <= 1e-6, ana
+            coefs.append(C)
+    finally:
+        B.ps_set_tuning(s.h, saved)
+    for o in outs[1:]:
+        assert _rel(o, outs[0]) <= 1e-6
+    for c in coefs[1:]:
+        assert _rel(c, coefs[0]) <= 1e-6

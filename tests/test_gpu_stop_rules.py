@@ -71,8 +71,10 @@ def test_stop_rule_without_constraint_ignores_np():
     pb = make_problem(n, 900, levels, 1, seed=32)
     with _handle(pb, n, levels, mode=B.PS_NO_CONSTRAINT, np_tol=1e-9) as s:
         s.set_sara_weights(None, 0.0)
+        # |Q| > I = 0 everywhere, far above zeta (3 rms of the Stokes I residual image in units of
+        # the PSF peak, which Q does not enter since L L^H = 2 I): N_p = 100 %.
         bad = np.zeros((4, n, n), np.float32)
-        bad[1] = 1.0                                   # |Q| > I = 0 everywhere: N_p = 100 %
+        bad[1] = 1e4
         s.set_state({"S": bad})
         st = s.stats()
         assert st["violations"] == n * n
@@ -143,7 +145,11 @@ def test_nonfinite_state_is_reported(plane):
         s.set_state({"S": np.zeros((4, n, n), np.float32), "Z": np.zeros((2, n, n), np.float32),
                      "A": np.zeros((4, 9, n, n), np.float32), "B": np.zeros((900, 4), np.complex64),
                      "C": np.zeros((4, n, n), np.float32), "D": np.zeros((2, n, n), np.float32)})
+        # From the zero state the first iteration leaves S at zero (every dual is zero) and the
+        # second moves it: the relative change is +inf (a map that left zero), and finite after.
         s.pd_iterate(2)
+        assert np.all(np.isposinf(B.ps_get_rel_change(s.h)))
+        s.pd_iterate(1)
         assert np.all(np.isfinite(B.ps_get_rel_change(s.h)))
 
 
@@ -187,3 +193,11 @@ def test_bounded_wait_gives_up_then_recovers(tuning):
         ref = opd.pd_iteration(ref, prob, T, p, opd.POLARIZED)
     for k in "SZABCD":
         assert rel_err(got[k], ref[k]) <= 2e-5 * 2, k
+
+
+def test_fp32_peak_measurement_is_plausible():
+    """ps_fp32_peak (the compute ceiling reported beside the HBM roofline): between 10 and 500
+    TFLOP/s on one GPU of this class, for packed FP32x2 and scalar FMA chains."""
+    for packed in (True, False):
+        v = B.ps_fp32_peak(packed)
+        assert 1e13 < v < 5e14, (packed, v)
