@@ -82,7 +82,9 @@ typedef struct {
   int32_t literal_ball;  /* 0: l2-ball radius eps (Moreau reading of Alg. 1 step 8);
                             1: the printed radius eps / rho2 */
   int32_t kernel_width;  /* NUFFT interpolation width W: 5, 7 or 9; 0 => 7 */
-  int32_t reserved;      /* 0 */
+  int32_t stop_maps;     /* maps the relative-change rule of Eq. stop_crit takes: 3 = I, Q, U as printed
+                            (the paper's V is zero), 4 or 0 = all four (V included; a map that stays
+                            zero counts 0) */
   double tau, rho1, rho2, rho3;  /* step sizes; 0 => default of Section 4.3.3:
                                     rho1 = rho3 = 1, rho2 = 1/||phi||^2,
                                     tau = 0.99 / (sum of rho_i ||K_i||^2 in the mode) */
@@ -102,7 +104,8 @@ typedef struct {
 
 /* Criteria of the stopping rule of Section 5.5 (bits of ps_stats.stop_flags). */
 enum {
-  PS_STOP_REL = 1,     /* max_i ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| <= rel_tol (Eq. stop_crit) */
+  PS_STOP_REL = 1,     /* max_i ||S_i^(k+1) - S_i^(k)|| / ||S_i^(k)|| <= rel_tol over the first stop_maps
+                          maps (Eq. stop_crit) */
   PS_STOP_RESID = 2,   /* ||phi(S) - Y||_b <= (1 + resid_tol) eps_b for every block */
   PS_STOP_NP = 4       /* N_p = 100 violations / N <= np_tol */
 };

@@ -174,16 +174,16 @@ def violation_count(S: np.ndarray, zeta: float) -> int:
 
 def stop_rule(S_new: np.ndarray, S_old: np.ndarray, prob: Problem, rel_tol: float = 1e-5,
               resid_tol: float = 5e-3, np_tol: float = 0.5, zeta_sigma: float = 3.0,
-              constrained: bool = True) -> dict:
+              constrained: bool = True, maps: int = 4) -> dict:
     """The stopping rule of Section 5.5 after the iteration S_old -> S_new.
 
-    rel: max over the maps of the relative change (Eq. stop_crit) <= rel_tol; the paper
-    takes i = 1..3 because its V is zero, and all four maps are taken here (a map that
+    rel: max over the first `maps` maps of the relative change (Eq. stop_crit) <= rel_tol;
+    the paper takes i = 1..3 (I, Q, U: its V is zero); maps = 4 takes V as well (a map that
     stays zero contributes 0). resid: ||phi(S) - Y||_b <= (1 + vartheta) eps_b for every
     block. np: with the polarization constraint, N_p = 100 * (pixels above zeta) / N <= varrho
     (percent, Section 5.2). converged: all three.
     """
-    rel = bool(np.max(relative_change(S_new, S_old)) <= rel_tol)
+    rel = bool(np.max(relative_change(S_new, S_old)[:maps]) <= rel_tol)
     resid = bool(np.all(residual_norms(S_new, prob) <= (1.0 + resid_tol) * prob.eps))
     n_p = 100.0 * violation_count(S_new, zeta_threshold(S_new, prob, zeta_sigma)) / S_new[0].size
     np_ok = (not constrained) or n_p <= np_tol

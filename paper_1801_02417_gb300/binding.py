@@ -33,7 +33,7 @@ class PolsaraError(RuntimeError):
 class ps_config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("levels", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("literal_ball", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tau", ctypes.c_double), ("rho1", ctypes.c_double),
+                ("stop_maps", ctypes.c_int32), ("tau", ctypes.c_double), ("rho1", ctypes.c_double),
                 ("rho2", ctypes.c_double), ("rho3", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("noise_sigma", ctypes.c_double), ("rel_tol", ctypes.c_double),
                 ("resid_tol", ctypes.c_double), ("np_tol", ctypes.c_double), ("zeta_sigma", ctypes.c_double)]

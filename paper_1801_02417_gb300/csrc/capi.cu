@@ -378,6 +378,8 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
   if (W != 5 && W != 7 && W != 9) return fail(nullptr, PS_EINVAL, "ps_create: kernel_width must be 5, 7 or 9");
   if (cfg->tau < 0 || cfg->rho1 < 0 || cfg->rho2 < 0 || cfg->rho3 < 0)
     return fail(nullptr, PS_EINVAL, "ps_create: step sizes must be >= 0");
+  if (cfg->stop_maps != 0 && cfg->stop_maps != 3 && cfg->stop_maps != 4)
+    return fail(nullptr, PS_EINVAL, "ps_create: stop_maps must be 0, 3 or 4");
   if (!(cfg->alpha == 0.0 || cfg->alpha == 2.0))
     return fail(nullptr, PS_EINVAL, "ps_create: alpha (NUFFT oversampling) must be 0 or 2");
   for (double v : {cfg->gamma, cfg->noise_sigma, cfg->rel_tol, cfg->resid_tol, cfg->np_tol, cfg->zeta_sigma})
@@ -393,6 +395,7 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
   // Defaults of Section 5.5 (rel_tol = epsilon, resid_tol = vartheta, np_tol = varrho in
   // percent) and Section 5.2 (zeta = 3 rms), and the oversampling 2.
   h->cfg.alpha = 2.0;
+  if (h->cfg.stop_maps == 0) h->cfg.stop_maps = 4;
   if (!(h->cfg.rel_tol > 0)) h->cfg.rel_tol = 1e-5;
   if (!(h->cfg.resid_tol > 0)) h->cfg.resid_tol = 5e-3;
   if (!(h->cfg.np_tol > 0)) h->cfg.np_tol = 0.5;
@@ -1146,7 +1149,7 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
   // Stopping rule of Section 5.5: every criterion that applies in the mode.
   int flags = 0;
   double rc = 0.0;
-  for (int c = 0; c < 4; ++c) rc = std::max(rc, out->rel_change[c]);
+  for (int c = 0; c < h->cfg.stop_maps; ++c) rc = std::max(rc, out->rel_change[c]);
   if (rc <= h->cfg.rel_tol) flags |= PS_STOP_REL;
   bool fit = true;
   if (!ps::tv_mode(h->mode))

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ps {
@@ -44,6 +45,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// 2D tensor-map copy (TMA) of one box into shared memory (128-byte aligned destination), completing
+// on `bar`. The map lives in kernel-parameter space (a __grid_constant__ argument). x is the
+// innermost coordinate in elements (x * 4 bytes a multiple of 16 for float data); parts of the
+// box outside the tensor are filled with zeros and still count toward the transaction bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Poll budget of the bounded waits. c_wait_polls (one copy per translation unit,
 // set by set_wait_polls_here) bounds the first wait on a barrier phase; a CTA
 // whose wait gave up drains its copies still in flight with the full budget

@@ -13,9 +13,12 @@
 //
 // Synthesis Psi runs one launch per level from coarse to fine; the finest level
 // sums the eight bases and the Dirac part in registers and writes Psi A once.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -325,6 +328,20 @@ __device__ __forceinline__ void ana_cols(const float* __restrict__ lo_s, const f
   }
 }
 
+// 2D tensor maps (TMA) of the arrays whose tiles the tiled SARA kernels stage, one box
+// each, with the box's row pitch equal to the shared-memory pitch of the staged tile:
+//   in    analysis input planes, width m, box kA2Pitch x kRSmax (the whole input tile)
+//   coef  analysis: coefficients, width n, box kTO x kTO (one subband tile of A)
+//   thr   analysis: thresholds gamma W, same box (one subband tile of gamma W)
+//   scoef synthesis: coefficients, width n, box kC2Pitch x kC2Rows (one subband tile)
+//   apx   synthesis: approximations of the level, width hm, same box
+// A use_* flag is 0 when its map was not made (then the per-row bulk copies run).
+// Tiles whose rows or columns wrap around the periodic edges always take the per-row copies.
+struct SaraTma {
+  CUtensorMap in, coef, thr, scoef, apx;
+  int use_in, use_stage, use_scoef, use_apx;
+};
+
 // Input tile of one analysis CTA: RS rows from row 2 oy0 and the 80 columns from
 // column 2 ox0 (both modulo m), one bulk copy per row, two where the row wraps
 // around the periodic right edge (then the first piece is 64 columns).
@@ -344,12 +361,31 @@ __device__ __forceinline__ void ana_issue_input(const float* __restrict__ src, i
   }
 }
 
+// The input tile by one tensor-map copy when it does not wrap (kRSmax rows of kA2Pitch
+// columns; the rows past RS and columns past kA2Cols are not read), else by rows.
+// `in_row0` is the row of the plane's first row in the input map.
+__device__ __forceinline__ void ana_issue_input_t(const SaraTma& tm, int in_row0, const float* __restrict__ src,
+                                                  int m, int oy0, int ox0, int RS, float* __restrict__ in_s,
+                                                  uint64_t* bar) {
+  if (tm.use_in && 2 * ox0 + kA2Cols <= m && 2 * oy0 + kRSmax <= m) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, (uint32_t)(kRSmax * kA2Pitch * sizeof(float)));
+      fence_proxy_async();
+      tma_load_2d(in_s, &tm.in, 2 * ox0, in_row0 + 2 * oy0, bar);
+    }
+  } else {
+    ana_issue_input(src, m, oy0, ox0, RS, in_s, bar);
+  }
+}
+
 // Shared-memory layout of the fast analysis kernels (floats): input tile, row-filtered
 // low/high tiles, the staged A and gamma W rows of the three detail subbands, and two
 // mbarriers (input tile, staged epilogue operands).
 constexpr int kStage = 3 * kTO * kTO;
-constexpr int kAnaFloats = kA2In + 2 * kRSmax * kPlo + 2 * kStage;
-static_assert(kA2In % 4 == 0 && (kRSmax * kPlo) % 4 == 0 && kStage % 4 == 0, "16-byte aligned stage buffers");
+// Staged epilogue operands start on a 128-byte boundary (tensor-map copy destinations).
+constexpr int kAnaPre = (kA2In + 2 * kRSmax * kPlo + 31) / 32 * 32;
+constexpr int kAnaFloats = kAnaPre + 2 * kStage;
+static_assert(kA2In % 4 == 0 && (kRSmax * kPlo) % 4 == 0 && kStage % 32 == 0, "aligned stage buffers");
 
 // The first 3 * 32 * 2 threads each start one bulk copy of this tile's A and gamma W
 // detail rows (3 subbands x 32 rows x 128 B) so they arrive while the rows are
@@ -371,6 +407,27 @@ __device__ __forceinline__ void stage_epilogue(const float* coef, const float* t
   }
 }
 
+// The same operands as six tensor-map copies (three subband tiles of A and of gamma W) by
+// one thread, when the maps were made; `prow` is the row of the basis plane in the maps.
+__device__ __forceinline__ void stage_epilogue_t(const SaraTma& tm, const float* coef, const float* thr, size_t base,
+                                                 int prow, int n, int hm, int oy0, int ox0, float* st_a, float* st_t,
+                                                 uint64_t* bar) {
+  if (!tm.use_stage) {
+    stage_epilogue(coef, thr, base, n, hm, oy0, ox0, st_a, st_t, bar);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, 2u * kStage * sizeof(float));
+    fence_proxy_async();   // the persistent and multi-basis forms refill buffers their threads have read
+    const int xs[3] = {hm + ox0, ox0, hm + ox0}, ys[3] = {prow + oy0, prow + hm + oy0, prow + hm + oy0};
+#pragma unroll
+    for (int sb = 0; sb < 3; ++sb) {
+      tma_load_2d(st_a + sb * kTO * kTO, &tm.coef, xs[sb], ys[sb], bar);
+      tma_load_2d(st_t + sb * kTO * kTO, &tm.thr, xs[sb], ys[sb], bar);
+    }
+  }
+}
+
 struct AnaSmem {
   float *in_s, *lo_s, *hi_s, *st_a, *st_t;
   uint64_t* bar;   // [0] input tile, [1] staged epilogue operands
@@ -380,7 +437,7 @@ __device__ __forceinline__ AnaSmem ana_smem(float4* sma) {
   a.in_s = reinterpret_cast<float*>(sma);
   a.lo_s = a.in_s + kA2In;
   a.hi_s = a.lo_s + kRSmax * kPlo;
-  a.st_a = a.hi_s + kRSmax * kPlo;
+  a.st_a = a.in_s + kAnaPre;
   a.st_t = a.st_a + kStage;
   a.bar = reinterpret_cast<uint64_t*>(a.st_t + kStage);
   return a;
@@ -399,13 +456,14 @@ __device__ __forceinline__ void ana_abort(const AnaSmem& S, int staged, int* err
 // One basis of one tile: input copies (issued first), staged epilogue operands (dual
 // mode), rows, columns + epilogue.
 template <int LF>
-__device__ __forceinline__ void ana_basis(const float* src, int m, const AnaSmem& S, int bi, int map, int n, int hm,
-                                          int oy0, int ox0, int last, float* coef, float* thr, float* approx_out,
-                                          int mode, float scale, float gamma, float delta, int* err) {
-  ana_issue_input(src, m, oy0, ox0, 2 * kTO + LF - 2, S.in_s, &S.bar[0]);
+__device__ __forceinline__ void ana_basis(const SaraTma& tm, int in_row0, const float* src, int m, const AnaSmem& S,
+                                          int bi, int map, int n, int hm, int oy0, int ox0, int last, float* coef,
+                                          float* thr, float* approx_out, int mode, float scale, float gamma,
+                                          float delta, int* err) {
+  ana_issue_input_t(tm, in_row0, src, m, oy0, ox0, 2 * kTO + LF - 2, S.in_s, &S.bar[0]);
   if (mode == SARA_DUAL)
-    stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, S.st_a, S.st_t,
-                   &S.bar[1]);
+    stage_epilogue_t(tm, coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, (map * kBases + bi + 1) * n, n,
+                     hm, oy0, ox0, S.st_a, S.st_t, &S.bar[1]);
   const bool ok = mbar_wait(&S.bar[0], 0);
   if (__syncthreads_or(!ok)) {
     ana_abort(S, mode == SARA_DUAL, err);
@@ -422,11 +480,13 @@ __device__ __forceinline__ void ana_basis(const float* src, int m, const AnaSmem
                S.st_a, S.st_t);
 }
 
-__device__ __forceinline__ void ana_dispatch(int bi, const float* src, int m, const AnaSmem& S, int map, int n, int hm,
-                                             int oy0, int ox0, int last, float* coef, float* thr, float* approx_out,
-                                             int mode, float scale, float gamma, float delta, int* err) {
-#define PS_ANA(LFv) \
-  ana_basis<LFv>(src, m, S, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, err)
+__device__ __forceinline__ void ana_dispatch(const SaraTma& tm, int in_row0, int bi, const float* src, int m,
+                                             const AnaSmem& S, int map, int n, int hm, int oy0, int ox0, int last,
+                                             float* coef, float* thr, float* approx_out, int mode, float scale,
+                                             float gamma, float delta, int* err) {
+#define PS_ANA(LFv)                                                                                              \
+  ana_basis<LFv>(tm, in_row0, src, m, S, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, \
+                 delta, err)
   PS_SWITCH_LF(bi, PS_ANA)
 #undef PS_ANA
 }
@@ -434,8 +494,9 @@ __device__ __forceinline__ void ana_dispatch(int bi, const float* src, int m, co
 // Level-1 analysis: input is the map itself; one basis per CTA (grid.y).
 __global__ void __launch_bounds__(256, 3) k_ana_l1(const float* __restrict__ X, int n, int last, float* __restrict__ coef,
                                                    float* __restrict__ thr, float* __restrict__ approx_out, int mode,
-                                                   float scale, float gamma, float delta, int* err) {
-  extern __shared__ float4 sma[];
+                                                   float scale, float gamma, float delta, int* err,
+                                                   const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 sma[];
   const AnaSmem S = ana_smem(sma);
   const int bi = blockIdx.y, map = blockIdx.z;
   const int hm = n >> 1, tilesx = hm / kTO;
@@ -445,16 +506,16 @@ __global__ void __launch_bounds__(256, 3) k_ana_l1(const float* __restrict__ X, 
     mbar_init(&S.bar[1], 1);
   }
   __syncthreads();
-  ana_dispatch(bi, X + (size_t)map * n * n, n, S, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale,
-               gamma, delta, err);
+  ana_dispatch(tm, map * n, bi, X + (size_t)map * n * n, n, S, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode,
+               scale, gamma, delta, err);
 }
 
 // Levels >= 2 with half size >= 32: one basis per CTA (grid.y).
 __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ approx_in, int m, int n, int last,
                                                    float* __restrict__ coef, float* __restrict__ thr,
                                                    float* __restrict__ approx_out, int mode, float scale, float gamma,
-                                                   float delta, int* err) {
-  extern __shared__ float4 sma[];
+                                                   float delta, int* err, const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 sma[];
   const AnaSmem S = ana_smem(sma);
   const int bi = blockIdx.y, map = blockIdx.z;
   const int hm = m >> 1, tilesx = hm / kTO;
@@ -464,8 +525,8 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
     mbar_init(&S.bar[1], 1);
   }
   __syncthreads();
-  ana_dispatch(bi, approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, S, map, n, hm, oy0, ox0, last, coef, thr,
-               approx_out, mode, scale, gamma, delta, err);
+  ana_dispatch(tm, (map * kDb + bi) * m, bi, approx_in + ((size_t)map * kDb + bi) * (size_t)m * m, m, S, map, n, hm,
+               oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, err);
 }
 
 // Level-1 analysis with the input tile shared by NB bases: one CTA per (tile, group of NB
@@ -473,32 +534,34 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
 // origin), so the map's tile is copied once and each basis filters it from shared memory.
 // The staged A and gamma W rows of basis i + 1 (dual mode) are copied into the second of
 // two staging sets while basis i is filtered.
-constexpr int kAnaMFloats = kA2In + 2 * kRSmax * kPlo + 4 * kStage;
+constexpr int kAnaMFloats = kAnaPre + 4 * kStage;
 static size_t multi_analysis_smem() { return (size_t)kAnaMFloats * sizeof(float) + 32; }
 
 template <int NB>
 __global__ void __launch_bounds__(256, 2) k_ana_l1m(const float* __restrict__ X, int n, int last,
                                                     float* __restrict__ coef, float* __restrict__ thr,
                                                     float* __restrict__ approx_out, int mode, float scale,
-                                                    float gamma, float delta, int* err) {
-  extern __shared__ float4 smm[];
+                                                    float gamma, float delta, int* err,
+                                                    const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 smm[];
   float* in_s = reinterpret_cast<float*>(smm);
   float* lo_s = in_s + kA2In;
   float* hi_s = lo_s + kRSmax * kPlo;
-  float* st = hi_s + kRSmax * kPlo;                                 // set s: A at st + 2 s kStage, gamma W after it
+  float* st = in_s + kAnaPre;                                       // set s: A at st + 2 s kStage, gamma W after it
   uint64_t* bar = reinterpret_cast<uint64_t*>(st + 4 * kStage);    // [0] input tile, [1 + s] stage set s
   const int map = blockIdx.z, b0 = blockIdx.y * NB;
   const int hm = n >> 1, tilesx = hm / kTO;
   const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
   const bool staged = mode == SARA_DUAL;
   auto plane = [&](int bi) { return ((size_t)map * kBases + bi + 1) * (size_t)n * n; };
+  auto prow = [&](int bi) { return (map * kBases + bi + 1) * n; };
   auto set_a = [&](int s) { return st + 2 * s * kStage; };
   auto set_t = [&](int s) { return st + (2 * s + 1) * kStage; };
   if (threadIdx.x == 0)
     for (int q = 0; q < 3; ++q) mbar_init(&bar[q], 1);
   __syncthreads();
-  ana_issue_input(X + (size_t)map * n * n, n, oy0, ox0, kRSmax, in_s, &bar[0]);
-  if (staged) stage_epilogue(coef, thr, plane(b0), n, hm, oy0, ox0, set_a(0), set_t(0), &bar[1]);
+  ana_issue_input_t(tm, map * n, X + (size_t)map * n * n, n, oy0, ox0, kRSmax, in_s, &bar[0]);
+  if (staged) stage_epilogue_t(tm, coef, thr, plane(b0), prow(b0), n, hm, oy0, ox0, set_a(0), set_t(0), &bar[1]);
   const bool ok = mbar_wait(&bar[0], 0);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {
@@ -512,7 +575,8 @@ __global__ void __launch_bounds__(256, 2) k_ana_l1m(const float* __restrict__ X,
     const int bi = b0 + i, s = i & 1;
     // Set s ^ 1 was last read by basis i - 1, which ended at a barrier: refill it for basis i + 1.
     if (staged && i + 1 < NB)
-      stage_epilogue(coef, thr, plane(bi + 1), n, hm, oy0, ox0, set_a(s ^ 1), set_t(s ^ 1), &bar[1 + (s ^ 1)]);
+      stage_epilogue_t(tm, coef, thr, plane(bi + 1), prow(bi + 1), n, hm, oy0, ox0, set_a(s ^ 1), set_t(s ^ 1),
+                       &bar[1 + (s ^ 1)]);
 #define PS_MR(LFv) ana_rows<LFv>(in_s, lo_s, hi_s)
     PS_SWITCH_LF(bi, PS_MR)
 #undef PS_MR
@@ -543,18 +607,19 @@ __global__ void __launch_bounds__(256, 2) k_ana_l1m(const float* __restrict__ X,
 // the previous unit's columns are filtered, and its staged A and gamma W rows
 // (double-buffered) while the whole previous unit runs, so the copy latency that the
 // one-unit-per-CTA form exposes once per CTA is hidden behind compute.
-constexpr int kAnaPFloats = kA2In + 2 * kRSmax * kPlo + 4 * kStage;
+constexpr int kAnaPFloats = kAnaPre + 4 * kStage;
 static size_t pers_analysis_smem() { return (size_t)kAnaPFloats * sizeof(float) + 32; }
 
 __global__ void __launch_bounds__(256, 2) k_ana_pers(const float* __restrict__ in, size_t in_map, size_t in_basis, int m,
                                                      int n, int last, float* __restrict__ coef,
                                                      float* __restrict__ thr, float* __restrict__ approx_out,
-                                                     int mode, float scale, float gamma, float delta, int* err) {
-  extern __shared__ float4 smp[];
+                                                     int mode, float scale, float gamma, float delta, int* err,
+                                                     const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 smp[];
   float* in_s = reinterpret_cast<float*>(smp);
   float* lo_s = in_s + kA2In;
   float* hi_s = lo_s + kRSmax * kPlo;
-  float* st = hi_s + kRSmax * kPlo;                                  // set s: A at st + 2 s kStage, gamma W after it
+  float* st = in_s + kAnaPre;                                        // set s: A at st + 2 s kStage, gamma W after it
   uint64_t* bar = reinterpret_cast<uint64_t*>(st + 4 * kStage);     // [0] input rows, [1 + s] stage set s
   const int hm = m >> 1, tilesx = hm / kTO, tiles = tilesx * tilesx;
   const int units = tiles * kDb * 4;
@@ -573,12 +638,13 @@ __global__ void __launch_bounds__(256, 2) k_ana_pers(const float* __restrict__ i
   auto issue = [&](int u, int s) {
     int bi, map, oy0, ox0;
     decode(u, bi, map, oy0, ox0);
-    ana_issue_input(in + (size_t)map * in_map + (size_t)bi * in_basis, m, oy0, ox0, 2 * kTO + 2 * (bi + 1) - 2, in_s,
-                    &bar[0]);
+    const size_t in_off = (size_t)map * in_map + (size_t)bi * in_basis;
+    ana_issue_input_t(tm, (int)(in_off / (size_t)m), in + in_off, m, oy0, ox0, 2 * kTO + 2 * (bi + 1) - 2, in_s,
+                      &bar[0]);
     ++issued_in;
     if (staged) {
-      stage_epilogue(coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, n, hm, oy0, ox0, st + 2 * s * kStage,
-                     st + (2 * s + 1) * kStage, &bar[1 + s]);
+      stage_epilogue_t(tm, coef, thr, ((size_t)map * kBases + bi + 1) * (size_t)n * n, (map * kBases + bi + 1) * n, n,
+                       hm, oy0, ox0, st + 2 * s * kStage, st + (2 * s + 1) * kStage, &bar[1 + s]);
       ++issued_st[s];
     }
   };
@@ -780,11 +846,11 @@ constexpr int kT2 = 64;                                  // output tile side
 constexpr int kC2Rows = kT2 / 2 + kMaxTaps / 2 - 1;      // 39 coefficient rows (db8 halo)
 constexpr int kC2Cols = kT2 / 2 + 8;                     // 40 staged columns: [ox0/2 - 8, ox0/2 + 32)
 constexpr int kC2Pitch = 52;                             // staged row pitch (2 x 52 = 8 mod 32 banks)
-constexpr int kC2Sub = kC2Rows * kC2Pitch;               // one subband tile
+constexpr int kC2Sub = (kC2Rows * kC2Pitch + 31) / 32 * 32;   // one subband tile, 128-byte aligned
 constexpr int kC2Set = 4 * kC2Sub;                       // LL, LH, HL, HH
 constexpr int kLoPitch = kT2 + 4;                        // column-major intermediates: [column][row]
 constexpr int kLoSize = kC2Cols * kLoPitch;
-static_assert(kC2Sub % 4 == 0 && kLoSize % 4 == 0, "16-byte aligned synthesis buffers");
+static_assert(kC2Sub % 32 == 0 && kLoSize % 4 == 0, "aligned synthesis buffers");
 
 // Issue the bulk copies of basis `half` (db(half+1)) for the tile at (oy0, ox0):
 // subband sb row r <- coefficient row (oy0/2 - half + r) mod hm, columns
@@ -811,6 +877,30 @@ __device__ __forceinline__ void syn2_issue(int half, const float* __restrict__ c
       bulk_g2s(dst, row + hm - 8, 8 * sizeof(float), bar);
       bulk_g2s(dst + 8, row, (kC2Cols - 8) * sizeof(float), bar);
     }
+  }
+}
+
+// The four subband tiles by four tensor-map copies from one thread when the tile does not
+// wrap (ox0, oy0 > 0) and the maps were made, else by rows. Each box is kC2Rows x kC2Pitch
+// (rows past CI and columns past kC2Cols are not read). `prow` is the row of the basis plane
+// in the coefficient map, `aprow` the row of the (map, basis) approximation in the
+// approximation map (apx non-null).
+__device__ __forceinline__ void syn2_issue_t(const SaraTma& tm, int prow, int aprow, int half,
+                                             const float* __restrict__ cb, const float* __restrict__ apx, int n, int hm,
+                                             int oy0, int ox0, float* __restrict__ s4, uint64_t* bar) {
+  if (!(tm.use_scoef && ox0 > 0 && oy0 > 0 && (apx == nullptr || tm.use_apx))) {
+    syn2_issue(half, cb, apx, n, hm, oy0, ox0, s4, bar);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    const int ky0 = oy0 / 2 - half, kxa = ox0 / 2 - 8;
+    mbar_expect_tx(bar, (uint32_t)(4 * kC2Rows * kC2Pitch * sizeof(float)));
+    fence_proxy_async();
+    if (apx) tma_load_2d(s4, &tm.apx, kxa, aprow + ky0, bar);               // LL from the approximations
+    else tma_load_2d(s4, &tm.scoef, kxa, prow + ky0, bar);                  // LL (coarsest level)
+    tma_load_2d(s4 + kC2Sub, &tm.scoef, kxa, prow + hm + ky0, bar);         // LH (x-low, y-high)
+    tma_load_2d(s4 + 2 * kC2Sub, &tm.scoef, hm + kxa, prow + ky0, bar);     // HL (x-high, y-low)
+    tma_load_2d(s4 + 3 * kC2Sub, &tm.scoef, hm + kxa, prow + hm + ky0, bar);  // HH
   }
 }
 
@@ -927,8 +1017,8 @@ __device__ __forceinline__ void syn2_abort(uint64_t* b0, uint32_t p0, uint64_t* 
 template <int NBUF>
 __global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
     k_syn2_fine(const float* __restrict__ coef, const float* __restrict__ approx_in, int coarsest, int n,
-                float* __restrict__ out, int* err) {
-  extern __shared__ float4 sm2[];
+                float* __restrict__ out, int* err, const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 sm2[];
   float* const s4 = reinterpret_cast<float*>(sm2);   // staging set(s): basis b in set b % NBUF
   float* loT = s4 + NBUF * kC2Set;
   float* hiT = loT + kLoSize;
@@ -942,20 +1032,23 @@ __global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
     return coarsest ? (const float*)nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
   };
   auto set = [&](int bi) { return s4 + (bi % NBUF) * kC2Set; };
+  auto issue = [&](int bi) {
+    syn2_issue_t(tm, (map * kBases + bi + 1) * n, (map * kDb + bi) * hm, bi, cbp(bi), apxp(bi), n, hm, oy0, ox0, set(bi),
+                 &bar[bi % NBUF]);
+  };
   // Barrier of basis bi and the parity of its phase (each barrier completes once per use).
   auto bar_of = [&](int bi) { return &bar[bi % NBUF]; };
   auto par_of = [&](int bi) { return (uint32_t)((bi / NBUF) & 1); };
   if (threadIdx.x == 0)
     for (int q = 0; q < NBUF; ++q) mbar_init(&bar[q], 1);
   __syncthreads();
-  syn2_issue(0, cbp(0), apxp(0), n, hm, oy0, ox0, set(0), bar_of(0));
+  issue(0);
   u64 acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0ull;
   for (int bi = 0; bi < kDb; ++bi) {
     // NBUF = 2: set (bi+1)&1 last fed the y-pass of basis bi-1, which ended at a barrier.
-    if (NBUF == 2 && bi + 1 < kDb) syn2_issue(bi + 1, cbp(bi + 1), apxp(bi + 1), n, hm, oy0, ox0, set(bi + 1),
-                                              bar_of(bi + 1));
+    if (NBUF == 2 && bi + 1 < kDb) issue(bi + 1);
     const bool ok = mbar_wait(bar_of(bi), par_of(bi));
     // Also orders the previous x-pass' reads of loT/hiT before this y-pass writes them.
     if (__syncthreads_or(!ok)) {
@@ -966,8 +1059,7 @@ __global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
     syn2_ypass_dispatch(bi, set(bi), loT, hiT);
     __syncthreads();
     // NBUF = 1: the set is free once every y-pass read of it has passed the barrier above.
-    if (NBUF == 1 && bi + 1 < kDb) syn2_issue(bi + 1, cbp(bi + 1), apxp(bi + 1), n, hm, oy0, ox0, set(bi + 1),
-                                              bar_of(bi + 1));
+    if (NBUF == 1 && bi + 1 < kDb) issue(bi + 1);
     syn2_xpass_dispatch(bi, loT, hiT, acc);
   }
   const int rq = threadIdx.x & 15, cg = threadIdx.x >> 4;
@@ -988,8 +1080,8 @@ __global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
 // CTA's start nor the end of a unit exposes a copy's latency, and no wave runs part-full.
 __global__ void __launch_bounds__(256, 4)
     k_syn2_fine_pers(const float* __restrict__ coef, const float* __restrict__ approx_in, int coarsest, int n,
-                     float* __restrict__ out, int* err) {
-  extern __shared__ float4 sm2[];
+                     float* __restrict__ out, int* err, const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 sm2[];
   float* const s4 = reinterpret_cast<float*>(sm2);
   float* loT = s4 + kC2Set;
   float* hiT = loT + kLoSize;
@@ -1001,7 +1093,7 @@ __global__ void __launch_bounds__(256, 4)
     const int oy0 = (t / tilesx) * kT2, ox0 = (t % tilesx) * kT2;
     const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
     const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
-    syn2_issue(bi, cb, apx, n, hm, oy0, ox0, s4, bar);
+    syn2_issue_t(tm, (map * kBases + bi + 1) * n, (map * kDb + bi) * hm, bi, cb, apx, n, hm, oy0, ox0, s4, bar);
   };
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
@@ -1045,8 +1137,8 @@ __global__ void __launch_bounds__(256, 4)
 // Coarser levels with output side m >= 64: one basis per CTA (grid.y), output to approximation scratch.
 __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ coef, const float* __restrict__ approx_in,
                                                     int coarsest, int m, int n, float* __restrict__ approx_out,
-                                                    int* err) {
-  extern __shared__ float4 sm2[];
+                                                    int* err, const __grid_constant__ SaraTma tm) {
+  extern __shared__ __align__(128) float4 sm2[];
   float* s4 = reinterpret_cast<float*>(sm2);
   float* loT = s4 + kC2Set;
   float* hiT = loT + kLoSize;
@@ -1058,7 +1150,7 @@ __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ co
   const float* apx = coarsest ? nullptr : approx_in + ((size_t)map * kDb + bi) * (size_t)hm * hm;
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
-  syn2_issue(bi, cb, apx, n, hm, oy0, ox0, s4, bar);
+  syn2_issue_t(tm, (map * kBases + bi + 1) * n, (map * kDb + bi) * hm, bi, cb, apx, n, hm, oy0, ox0, s4, bar);
   const bool ok = mbar_wait(bar, 0);
   if (__syncthreads_or(!ok)) {
     syn2_abort(bar, 0, nullptr, 0, err);
@@ -1248,6 +1340,65 @@ static size_t syn_tail_smem(int mmax) {
   return (size_t)(mmax * mmax + mmax * mmax / 4 + mmax * mmax + 3 * (mmax / 2) * (mmax / 2)) * sizeof(float);
 }
 
+// ---- tensor maps (host side). cuTensorMapEncodeTiled comes from the driver through the
+// runtime's entry-point query, so the library links against the runtime alone; without it
+// (or when an encode fails) the kernels take the per-row bulk copies.
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+static std::once_flag g_encode_once;
+
+static bool tensor_maps_available() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    else
+      cudaGetLastError();
+  });
+  return g_encode_tiled != nullptr;
+}
+
+// Map of a row-major float array of `height` rows of `width` floats, box bw x bh (zero fill
+// outside). Returns 1 when made. The base must be 16-byte aligned and width * 4 a multiple of
+// 16 (every array here: n, m, hm >= 16).
+static int make_map(CUtensorMap* map, const float* base, uint64_t width, uint64_t height, uint32_t bw, uint32_t bh) {
+  std::memset(map, 0, sizeof(*map));
+  if (!base || !tensor_maps_available() || ((uintptr_t)base & 15u) || (width * 4) % 16 != 0 || bw > 256 || bh > 256 ||
+      bw > width || bh > height)
+    return 0;
+  const cuuint64_t dims[2] = {width, height};
+  const cuuint64_t strides[1] = {width * sizeof(float)};
+  const cuuint32_t box[2] = {bw, bh};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 1 : 0;
+}
+
+// Maps of one tiled analysis level: input planes of side m (`planes` of them), and the
+// coefficient and threshold arrays (36 n x n) for the staged epilogue operands.
+static SaraTma analysis_maps(const float* in, int m, int planes, const float* coef, const float* thr, int n, int mode) {
+  SaraTma t;
+  std::memset(&t, 0, sizeof(t));
+  t.use_in = make_map(&t.in, in, (uint64_t)m, (uint64_t)planes * m, kA2Pitch, kRSmax);
+  if (mode == SARA_DUAL)
+    t.use_stage = make_map(&t.coef, coef, (uint64_t)n, 36ull * n, kTO, kTO) &
+                  make_map(&t.thr, thr, (uint64_t)n, 36ull * n, kTO, kTO);
+  return t;
+}
+
+// Maps of one tiled synthesis level of output side m: coefficients and, below the coarsest
+// level, the 32 (map, basis) approximations of side m / 2.
+static SaraTma synthesis_maps(const float* coef, const float* approx_in, int m, int n) {
+  SaraTma t;
+  std::memset(&t, 0, sizeof(t));
+  t.use_scoef = make_map(&t.scoef, coef, (uint64_t)n, 36ull * n, kC2Pitch, kC2Rows);
+  if (approx_in) t.use_apx = make_map(&t.apx, approx_in, (uint64_t)(m / 2), 32ull * (m / 2), kC2Pitch, kC2Rows);
+  return t;
+}
+
 cudaError_t configure_nufft_kernels();
 
 cudaError_t configure_kernels() {
@@ -1315,12 +1466,13 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
     if (l == 1 && h->tune[PS_TUNE_ANALYSIS] >= 2) {
       const int nb = h->tune[PS_TUNE_ANALYSIS] == 2 ? 8 : 4;
       const dim3 gm((hm / kTO) * (hm / kTO), kDb / nb, 4);
+      const SaraTma tm = analysis_maps(X, n, 4, coef, thr, n, mode);
       if (nb == 8)
         k_ana_l1m<8><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode, scale,
-                                                                    gamma, delta, h->dev_flags);
+                                                                    gamma, delta, h->dev_flags, tm);
       else
         k_ana_l1m<4><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode, scale,
-                                                                    gamma, delta, h->dev_flags);
+                                                                    gamma, delta, h->dev_flags, tm);
       if (fine_done) {
         const cudaError_t e = cudaEventRecord(fine_done, h->stream);
         if (e != cudaSuccess) return e;
@@ -1330,24 +1482,27 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
       const int ctas = std::min(units, 2 * std::max(1, h->num_sms));
       const float* in = l == 1 ? X : buf[(l - 2) & 1];
       const size_t in_map = l == 1 ? (size_t)n * n : (size_t)kDb * m * m, in_basis = l == 1 ? 0 : (size_t)m * m;
+      const SaraTma tm = analysis_maps(in, m, l == 1 ? 4 : 32, coef, thr, n, mode);
       k_ana_pers<<<ctas, 256, pers_analysis_smem(), h->stream>>>(in, in_map, in_basis, m, n, l == L, coef, thr,
                                                                  buf[(l - 1) & 1], mode, scale, gamma, delta,
-                                                                 h->dev_flags);
+                                                                 h->dev_flags, tm);
       if (l == 1 && fine_done) {
         const cudaError_t e = cudaEventRecord(fine_done, h->stream);
         if (e != cudaSuccess) return e;
       }
     } else if (l == 1) {
+      const SaraTma tm = analysis_maps(X, n, 4, coef, thr, n, mode);
       k_ana_l1<<<grid, 256, fast_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[(l - 1) & 1], mode, scale,
-                                                              gamma, delta, h->dev_flags);
+                                                              gamma, delta, h->dev_flags, tm);
       if (fine_done) {
         const cudaError_t e = cudaEventRecord(fine_done, h->stream);
         if (e != cudaSuccess) return e;
       }
     } else {
+      const SaraTma tm = analysis_maps(buf[(l - 2) & 1], m, 32, coef, thr, n, mode);
       k_ana_lv<<<grid, 256, fast_analysis_smem(), h->stream>>>(buf[(l - 2) & 1], m, n, l == L, coef, thr,
                                                               buf[(l - 1) & 1], mode, scale, gamma, delta,
-                                                              h->dev_flags);
+                                                              h->dev_flags, tm);
     }
   }
   if (lt <= L) {
@@ -1388,6 +1543,7 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
       const cudaError_t e = cudaEventRecord(fine_start, stream);
       if (e != cudaSuccess) return e;
     }
+    const SaraTma tm = m >= kT2 ? synthesis_maps(coef, ain, m, n) : SaraTma{};
     if (m >= kT2 && l == 1) {
       const dim3 grid((m / kT2) * (m / kT2), 1, 4);
       if (variant == 2) {
@@ -1396,12 +1552,12 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int units = (int)(grid.x * grid.z);
         k_syn2_fine_pers<<<std::min(units, 4 * std::max(1, sms)), 256, syn2_smem(1), stream>>>(coef, ain, l == L, n,
-                                                                                              out, err);
-      } else if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err);
-      else k_syn2_fine<2><<<grid, 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err);
+                                                                                              out, err, tm);
+      } else if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err, tm);
+      else k_syn2_fine<2><<<grid, 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err, tm);
     } else if (m >= kT2) {
       k_syn2_lv<<<dim3((m / kT2) * (m / kT2), kDb, 4), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
-                                                                                     err);
+                                                                                     err, tm);
     } else if (m >= kTI && l == 1) {
       k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, stream>>>(coef, ain, l == L, n, out);
     } else {

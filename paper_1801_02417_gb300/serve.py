@@ -67,6 +67,7 @@ class Result:
 class Policy:
     rel_tol: float = 1e-4          # Eq. stop_crit tolerance per cycle
     rule: str = "paper"            # "paper": every criterion of Section 5.5; "rel": the relative change only
+    maps: int = 4                  # maps of Eq. stop_crit: 3 = I, Q, U as printed, 4 = V included
     max_iter: int = 2000           # per request
     reweights: int = 5             # reweighted cycles after the NNLS cycle
     check_every: int = 20          # iterations between stop-rule checks
@@ -98,7 +99,7 @@ class _Active:
         if self.policy.rule == "paper":
             met = B.ps_compute_stats(self.s.h, 0.0, self.s.nblocks)["converged"]
         else:
-            met = float(np.max(B.ps_get_rel_change(self.s.h))) <= self.policy.rel_tol
+            met = float(np.max(B.ps_get_rel_change(self.s.h)[:self.policy.maps])) <= self.policy.rel_tol
         cycle_done = met or self.in_cycle >= self.per_cycle
         if self.used >= self.policy.max_iter:
             return True
@@ -156,7 +157,7 @@ class Server:
         self._id_lock = threading.Lock()
 
     def _prepare(self, prob: Problem) -> PolarizedSARA:
-        s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS, rel_tol=self.policy.rel_tol)
+        s = PolarizedSARA(prob.n, prob.levels, mode=B.PS_NNLS, rel_tol=self.policy.rel_tol, stop_maps=self.policy.maps)
         try:
             s.set_measurements(prob.uv, prob.vis, prob.weights, prob.offsets, prob.eps)
             if self.autotune:

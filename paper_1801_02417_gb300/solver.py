@@ -33,10 +33,11 @@ class PolarizedSARA:
     def __init__(self, n: int, levels: int, mode: int = B.PS_POLARIZED, kernel_width: int = 7,
                  literal_ball: bool = False, tau: float = 0.0, rho1: float = 0.0, rho2: float = 0.0,
                  rho3: float = 0.0, stream=None, gamma: float = 0.0, noise_sigma: float = 0.0,
-                 rel_tol: float = 0.0, resid_tol: float = 0.0, np_tol: float = 0.0, zeta_sigma: float = 0.0):
+                 rel_tol: float = 0.0, resid_tol: float = 0.0, np_tol: float = 0.0, zeta_sigma: float = 0.0,
+                 stop_maps: int = 0):
         """Zero for a parameter takes the library default (include/polsara.h, ps_config)."""
         cfg = B.ps_config(n=n, levels=levels, mode=mode, literal_ball=int(literal_ball),
-                          kernel_width=kernel_width, reserved=0, tau=tau, rho1=rho1, rho2=rho2, rho3=rho3,
+                          kernel_width=kernel_width, stop_maps=stop_maps, tau=tau, rho1=rho1, rho2=rho2, rho3=rho3,
                           alpha=0.0, gamma=gamma, noise_sigma=noise_sigma, rel_tol=rel_tol,
                           resid_tol=resid_tol, np_tol=np_tol, zeta_sigma=zeta_sigma)
         self.n, self.levels = n, levels
@@ -145,11 +146,13 @@ class PolarizedSARA:
         rel_tol, resid_tol, np_tol): the relative change of Eq. stop_crit, the data fit
         ||phi(S) - Y||_b <= (1 + vartheta) eps_b and, with the constraint, N_p <= varrho.
         rule "rel": the relative change alone (cheaper: no residual evaluation).
-        The relative change covers all four maps (a map that stays zero does not count).
+        The relative change covers the handle's stop_maps maps (all four by default; a map that
+        stays zero counts 0).
         gamma 0 takes the handle's gamma."""
         used = 0
         per_cap = max(check_every, max_iter // (reweights + 1))
-        rel_tol = B.ps_get_config(self.h).rel_tol
+        cfg = B.ps_get_config(self.h)
+        rel_tol, maps = cfg.rel_tol, cfg.stop_maps
 
         def cycle():
             nonlocal used
@@ -163,7 +166,7 @@ class PolarizedSARA:
                         break
                 else:
                     self.pd_iterate(step)
-                    if float(np.max(B.ps_get_rel_change(self.h))) <= rel_tol:
+                    if float(np.max(B.ps_get_rel_change(self.h)[:maps])) <= rel_tol:
                         break
         self.set_mode(B.PS_NNLS)
         cycle()

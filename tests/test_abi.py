@@ -51,7 +51,7 @@ def test_estimate_bytes_and_invalid_sizes(lib):
 
 
 def test_create_rejects_bad_config_without_touching_a_device(lib):
-    cfg = binding.ps_config(n=100, levels=2, mode=0, literal_ball=0, kernel_width=7, reserved=0,
+    cfg = binding.ps_config(n=100, levels=2, mode=0, literal_ball=0, kernel_width=7, stop_maps=0,
                             tau=0, rho1=0, rho2=0, rho3=0)
     with pytest.raises(binding.PolsaraError) as e:
         binding.ps_create(cfg)
@@ -60,3 +60,18 @@ def test_create_rejects_bad_config_without_touching_a_device(lib):
     with pytest.raises(binding.PolsaraError) as e:
         binding.ps_create(cfg)
     assert e.value.status == binding.PS_EINVAL
+
+
+def test_create_validates_the_problem_and_stopping_fields_without_a_device(lib):
+    """The ps_config fields of the problem statement and of the stopping rule (Section 5.5) are
+    checked before any device call: oversampling other than 2, a negative gamma, sigma or
+    tolerance, and a map count of the relative-change rule other than 3 or 4 are refused."""
+    for field, bad in (("alpha", 3.0), ("gamma", -1.0), ("noise_sigma", -0.5), ("rel_tol", -1e-5),
+                       ("resid_tol", float("nan")), ("np_tol", -0.5), ("zeta_sigma", float("inf")),
+                       ("stop_maps", 2)):
+        cfg = binding.ps_config(n=64, levels=2, mode=0, kernel_width=7)
+        setattr(cfg, field, bad)
+        with pytest.raises(binding.PolsaraError) as e:
+            binding.ps_create(cfg)
+        assert e.value.status == binding.PS_EINVAL, field
+        assert "ps_create" in binding.ps_last_error(None)

@@ -33,11 +33,12 @@ def _handle(pb, n, levels, **kw):
     return s
 
 
-@pytest.mark.parametrize("tols", [dict(), dict(rel_tol=1.0, resid_tol=100.0, np_tol=100.0)])
+@pytest.mark.parametrize("tols", [dict(), dict(rel_tol=1.0, resid_tol=100.0, np_tol=100.0),
+                                  dict(rel_tol=1.0, resid_tol=100.0, np_tol=100.0, stop_maps=3)])
 def test_rel_change_and_stop_flags_match_oracle(tols):
-    """Eq. stop_crit per map (V included) and the PS_STOP_* flags of Section 5.5 against the
-    oracle's stop_rule on the same FP32 states: default tolerances (nothing but N_p met after
-    20 iterations from zero) and loose ones (all met, converged)."""
+    """Eq. stop_crit per map (V included, or I, Q, U as printed) and the PS_STOP_* flags of
+    Section 5.5 against the oracle's stop_rule on the same FP32 states: default tolerances
+    (nothing but N_p met after 20 iterations from zero) and loose ones (all met, converged)."""
     n, levels = 32, 3
     pb = make_problem(n, 1500, levels, 4, seed=31)
     prob = pb["prob"]
@@ -53,13 +54,15 @@ def test_rel_change_and_stop_flags_match_oracle(tols):
     assert np.all(np.isfinite(ref_rc)) and np.all(ref_rc > 0)
     assert np.allclose(st["rel_change"], ref_rc, rtol=1e-5)
     assert np.allclose(rc, ref_rc, rtol=1e-5)
-    ref = opd.stop_rule(S_new, S_old, prob, cfg.rel_tol, cfg.resid_tol, cfg.np_tol, cfg.zeta_sigma, True)
+    ref = opd.stop_rule(S_new, S_old, prob, cfg.rel_tol, cfg.resid_tol, cfg.np_tol, cfg.zeta_sigma, True,
+                        maps=cfg.stop_maps)
+    assert cfg.stop_maps == tols.get("stop_maps", 4)
     flags = {"rel": B.PS_STOP_REL, "resid": B.PS_STOP_RESID, "np": B.PS_STOP_NP}
     for k, bit in flags.items():
         assert bool(st["stop_flags"] & bit) == ref[k], (k, st, ref)
     assert st["converged"] == ref["converged"]
     if not tols:
-        assert (cfg.rel_tol, cfg.resid_tol, cfg.np_tol, cfg.zeta_sigma) == (1e-5, 5e-3, 0.5, 3.0)
+        assert (cfg.rel_tol, cfg.resid_tol, cfg.np_tol, cfg.zeta_sigma, cfg.stop_maps) == (1e-5, 5e-3, 0.5, 3.0, 4)
         assert not st["converged"]
     else:
         assert st["converged"]

@@ -256,6 +256,11 @@ def test_relative_change_and_stop_rule():
     assert st["rel"] and st["resid"] and st["np"] and st["converged"] and st["N_p"] == 0.0
     st = pd.stop_rule(Strue * (1 + 1e-4), Strue, prob, rel_tol=1e-5)
     assert not st["rel"] and not st["converged"]
+    # Eq. stop_crit as printed (I, Q, U) ignores a change confined to V.
+    Sv = Strue.copy()
+    Sv[3] *= 1.01
+    assert pd.stop_rule(Sv, Strue, prob, rel_tol=1e-5, maps=3)["rel"]
+    assert not pd.stop_rule(Sv, Strue, prob, rel_tol=1e-5, maps=4)["rel"]
     # Far from the data: the fit criterion fails.
     assert not pd.stop_rule(0.5 * Strue, 0.5 * Strue, prob)["resid"]
     # Q made larger than I on 2% of the pixels (beyond zeta): N_p = 2 > 0.5 fails with the constraint only.
