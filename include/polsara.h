@@ -371,7 +371,8 @@ enum {
                              2 level 1 with one CTA per (tile, map): the map's input tile copied once for
                                the 8 bases, each basis' staged A and gamma W in flight during the previous
                                basis (levels >= 2 as 0),
-                             3 as 2 with one CTA per (tile, 4 bases, map) */
+                             3 as 2 with one CTA per (tile, 4 bases, map),
+                             4 as 3 with 512 threads per CTA (two columns per thread) */
   PS_TUNE_COUNT = 4
 };
 

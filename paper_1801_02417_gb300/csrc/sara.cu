@@ -510,7 +510,8 @@ __global__ void __launch_bounds__(256, 3) k_ana_l1(const float* __restrict__ X, 
                scale, gamma, delta, err);
 }
 
-// Levels >= 2 with half size >= 32: one basis per CTA (grid.y).
+// Levels >= 2 with half size >= 32: one basis per CTA (grid.y). (A basis-slowest grid, which
+// keeps the co-resident CTAs on one filter's code, measured 5 us slower at 1024^2.)
 __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ approx_in, int m, int n, int last,
                                                    float* __restrict__ coef, float* __restrict__ thr,
                                                    float* __restrict__ approx_out, int mode, float scale, float gamma,
@@ -529,6 +530,66 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
                oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, err);
 }
 
+// Columns + epilogue for one basis with two columns per thread (the 512-thread form): each
+// thread owns two consecutive columns of one output row (one packed pair per subband).
+template <int LF>
+__device__ __forceinline__ void ana_cols2(const float* __restrict__ lo_s, const float* __restrict__ hi_s, int bi,
+                                          int map, int n, int hm, int oy0, int ox0, int last, float* __restrict__ coef,
+                                          float* __restrict__ thr, float* __restrict__ approx_out, int mode,
+                                          float scale, float gamma, float delta, const float* __restrict__ st_a,
+                                          const float* __restrict__ st_t) {
+  constexpr int b = LF / 2 - 1;
+  const size_t base = ((size_t)map * kBases + (bi + 1)) * (size_t)n * n;
+  for (int u = threadIdx.x; u < kTO * kTO / 2; u += blockDim.x) {
+    const int kx0 = (u % (kTO / 2)) * 2, ky = u / (kTO / 2);
+    const int Y = oy0 + ky, X = ox0 + kx0;
+    const size_t idx[4] = {base + (size_t)Y * n + (hm + X), base + (size_t)(hm + Y) * n + X,
+                           base + (size_t)(hm + Y) * n + (hm + X), base + (size_t)Y * n + X};   // HL, LH, HH, LL
+    u64 ll = 0ull, lh = 0ull, hl = 0ull, hh = 0ull;
+#pragma unroll
+    for (int j = 0; j < LF; ++j) {
+      const u64 a = *reinterpret_cast<const u64*>(lo_s + (2 * ky + j) * kPlo + kx0);
+      const u64 c = *reinterpret_cast<const u64*>(hi_s + (2 * ky + j) * kPlo + kx0);
+      const u64 ph = cdup(c_hd[b][j]), pg = cdup(c_gd[b][j]);
+      ll = ffma2(ph, a, ll);
+      lh = ffma2(pg, a, lh);
+      hl = ffma2(ph, c, hl);
+      hh = ffma2(pg, c, hh);
+    }
+    const u64 v[4] = {hl, lh, hh, ll};
+    const int nsb = last ? 4 : 3;
+    for (int sb = 0; sb < nsb; ++sb) {
+      float v0, v1;
+      f2unpack(v[sb], v0, v1);
+      float2* dst = reinterpret_cast<float2*>(coef + idx[sb]);
+      if (mode == SARA_DUAL) {
+        float2 a2, t2;
+        if (sb < 3) {
+          a2 = *reinterpret_cast<const float2*>(st_a + sb * kTO * kTO + ky * kTO + kx0);
+          t2 = *reinterpret_cast<const float2*>(st_t + sb * kTO * kTO + ky * kTO + kx0);
+        } else {
+          a2 = *reinterpret_cast<const float2*>(coef + idx[sb]);
+          t2 = *reinterpret_cast<const float2*>(thr + idx[sb]);
+        }
+        *dst = make_float2(fminf(fmaxf(fmaf(scale, v0, a2.x), -t2.x), t2.x),
+                           fminf(fmaxf(fmaf(scale, v1, a2.y), -t2.y), t2.y));
+      } else if (mode == SARA_APPLY) {
+        *dst = make_float2(scale * v0, scale * v1);
+      } else {
+        const float gd = gamma * delta;
+        *reinterpret_cast<float2*>(thr + idx[sb]) =
+            make_float2(gd / (delta + fabsf(scale * v0)), gd / (delta + fabsf(scale * v1)));
+      }
+    }
+    if (!last) {
+      float a0, a1;
+      f2unpack(ll, a0, a1);
+      *reinterpret_cast<float2*>(approx_out + ((size_t)map * kDb + bi) * (size_t)hm * hm + (size_t)Y * hm + X) =
+          make_float2(a0, a1);
+    }
+  }
+}
+
 // Level-1 analysis with the input tile shared by NB bases: one CTA per (tile, group of NB
 // bases, map). The 2 TO + 14 rows the db8 filter needs cover every shorter filter (same
 // origin), so the map's tile is copied once and each basis filters it from shared memory.
@@ -537,8 +598,8 @@ __global__ void __launch_bounds__(256, 3) k_ana_lv(const float* __restrict__ app
 constexpr int kAnaMFloats = kAnaPre + 4 * kStage;
 static size_t multi_analysis_smem() { return (size_t)kAnaMFloats * sizeof(float) + 32; }
 
-template <int NB>
-__global__ void __launch_bounds__(256, 2) k_ana_l1m(const float* __restrict__ X, int n, int last,
+template <int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS, 2) k_ana_l1m(const float* __restrict__ X, int n, int last,
                                                     float* __restrict__ coef, float* __restrict__ thr,
                                                     float* __restrict__ approx_out, int mode, float scale,
                                                     float gamma, float delta, int* err,
@@ -593,9 +654,13 @@ __global__ void __launch_bounds__(256, 2) k_ana_l1m(const float* __restrict__ X,
     } else {
       __syncthreads();
     }
-#define PS_MC(LFv)                                                                                          \
-  ana_cols<LFv>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, \
-                set_a(s), set_t(s))
+#define PS_MC(LFv)                                                                                           \
+  if (THREADS == 512)                                                                                        \
+    ana_cols2<LFv>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta, \
+                   set_a(s), set_t(s));                                                                      \
+  else                                                                                                       \
+    ana_cols<LFv>(lo_s, hi_s, bi, map, n, hm, oy0, ox0, last, coef, thr, approx_out, mode, scale, gamma, delta,  \
+                  set_a(s), set_t(s))
     PS_SWITCH_LF(bi, PS_MC)
 #undef PS_MC
     __syncthreads();   // lo/hi and stage set s consumed before the next basis
@@ -1134,7 +1199,8 @@ __global__ void __launch_bounds__(256, 4)
   }
 }
 
-// Coarser levels with output side m >= 64: one basis per CTA (grid.y), output to approximation scratch.
+// Coarser levels with output side m >= 64: one basis per CTA (grid.z, basis slowest), output to
+// approximation scratch.
 __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ coef, const float* __restrict__ approx_in,
                                                     int coarsest, int m, int n, float* __restrict__ approx_out,
                                                     int* err, const __grid_constant__ SaraTma tm) {
@@ -1143,7 +1209,7 @@ __global__ void __launch_bounds__(256, 3) k_syn2_lv(const float* __restrict__ co
   float* loT = s4 + kC2Set;
   float* hiT = loT + kLoSize;
   uint64_t* bar = reinterpret_cast<uint64_t*>(hiT + kLoSize);
-  const int bi = blockIdx.y, map = blockIdx.z, tilesx = m / kT2;
+  const int bi = blockIdx.z, map = blockIdx.y, tilesx = m / kT2;   // basis slowest, as k_ana_lv
   const int oy0 = (blockIdx.x / tilesx) * kT2, ox0 = (blockIdx.x % tilesx) * kT2;
   const int hm = m >> 1;
   const float* cb = coef + ((size_t)map * kBases + bi + 1) * (size_t)n * n;
@@ -1427,7 +1493,8 @@ cudaError_t configure_kernels() {
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
-  for (const void* f : {(const void*)k_ana_l1m<8>, (const void*)k_ana_l1m<4>}) {
+  for (const void* f : {(const void*)k_ana_l1m<8, 256>, (const void*)k_ana_l1m<4, 256>,
+                        (const void*)k_ana_l1m<4, 512>}) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)multi_analysis_smem());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -1464,15 +1531,18 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
     const int m = n >> (l - 1), hm = m / 2;
     const dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
     if (l == 1 && h->tune[PS_TUNE_ANALYSIS] >= 2) {
-      const int nb = h->tune[PS_TUNE_ANALYSIS] == 2 ? 8 : 4;
+      const int choice = h->tune[PS_TUNE_ANALYSIS], nb = choice == 2 ? 8 : 4;
       const dim3 gm((hm / kTO) * (hm / kTO), kDb / nb, 4);
       const SaraTma tm = analysis_maps(X, n, 4, coef, thr, n, mode);
-      if (nb == 8)
-        k_ana_l1m<8><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode, scale,
-                                                                    gamma, delta, h->dev_flags, tm);
+      if (choice == 2)
+        k_ana_l1m<8, 256><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
+                                                                         scale, gamma, delta, h->dev_flags, tm);
+      else if (choice == 3)
+        k_ana_l1m<4, 256><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
+                                                                         scale, gamma, delta, h->dev_flags, tm);
       else
-        k_ana_l1m<4><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode, scale,
-                                                                    gamma, delta, h->dev_flags, tm);
+        k_ana_l1m<4, 512><<<gm, 512, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
+                                                                         scale, gamma, delta, h->dev_flags, tm);
       if (fine_done) {
         const cudaError_t e = cudaEventRecord(fine_done, h->stream);
         if (e != cudaSuccess) return e;
@@ -1556,7 +1626,7 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
       } else if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err, tm);
       else k_syn2_fine<2><<<grid, 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err, tm);
     } else if (m >= kT2) {
-      k_syn2_lv<<<dim3((m / kT2) * (m / kT2), kDb, 4), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
+      k_syn2_lv<<<dim3((m / kT2) * (m / kT2), 4, kDb), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
                                                                                      err, tm);
     } else if (m >= kTI && l == 1) {
       k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, stream>>>(coef, ain, l == L, n, out);
