@@ -462,6 +462,7 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
     h->err = "ps_create: device allocation failed";
     return bail(PS_ENOMEM);
   }
+  h->approx2 = h->approx + 8 * N;
   if (reset_state(h) != PS_OK) return bail(PS_ECUDA);
   // Thresholds default to 1 (gamma = 1, W = 1).
   std::vector<float> ones(36 * N, 1.0f);
@@ -482,6 +483,10 @@ void ps_destroy(ps_handle* h) {
   drop_graph(h);
   free_vis(h);
   const size_t N = h->N;
+  if (h->in_slab) {   // these arrays belong to a batch's class slabs
+    h->S = h->Z = h->C = h->D = h->Xb = h->PsiA = h->Adj = h->A = h->T = h->approx = h->approx2 = nullptr;
+    h->red = nullptr;
+  }
   dfree(h, h->S, 4 * N);
   dfree(h, h->Z, 2 * N);
   dfree(h, h->C, 4 * N);
@@ -1447,11 +1452,31 @@ ps_status ps_wavelet_filters(double* out) {
 }
 
 }  // extern "C"
+// Batches. Handles of one size class (same n and levels) keep their per-pixel state and SARA
+// coefficients in class-wide slabs, problem after problem, so that the per-pixel sweep and
+// the SARA transforms of the whole class run as single launches over 4 P maps (the kernels
+// index maps across the consecutive problems); each problem's NUFFT chain stays on its own
+// stream. The slabs are filled from the handles' own arrays when the batch is made and
+// copied back when it is destroyed.
+struct BatchClass {
+  std::vector<Handle*> hs;
+  size_t N = 0;
+  int red_cap = 0;
+  float *S = nullptr, *Z = nullptr, *C = nullptr, *D = nullptr, *Xb = nullptr, *PsiA = nullptr, *Adj = nullptr;
+  float *A = nullptr, *T = nullptr, *ap0 = nullptr, *ap1 = nullptr;
+  double* red = nullptr;
+  cudaStream_t s_main = nullptr, s_sara = nullptr;
+  cudaEvent_t ev_primal = nullptr, ev_sara = nullptr;
+  bool fused = false;   // the last graph ran this class through the class-wide launches
+};
+
 struct ps_batch {
   std::vector<Handle*> hs;
   std::vector<uint64_t> versions;
   std::vector<cudaEvent_t> join;
   std::vector<cudaEvent_t> pre;    // each handle's own pending work, ordered before the batch's launches
+  std::vector<BatchClass> classes;
+  int64_t slab_bytes = 0;
   cudaEvent_t fork = nullptr;
   cudaEvent_t done = nullptr;      // the batch's launches, ordered before each handle's later work
   cudaStream_t stream = nullptr;
@@ -1464,10 +1489,150 @@ static ps_status batch_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? PS_ENOMEM : PS_ECUDA;
 }
 
+// The slab arrays of a class, in the order of the Handle fields they replace, with their
+// per-problem sizes in floats (red: doubles).
+struct SlabField {
+  float* Handle::*hp;
+  float* BatchClass::*cp;
+  size_t per_N;   // floats per problem = per_N * N
+};
+static const SlabField kSlabFields[] = {
+    {&Handle::S, &BatchClass::S, 4},    {&Handle::Z, &BatchClass::Z, 2},       {&Handle::C, &BatchClass::C, 4},
+    {&Handle::D, &BatchClass::D, 2},    {&Handle::Xb, &BatchClass::Xb, 4},     {&Handle::PsiA, &BatchClass::PsiA, 4},
+    {&Handle::Adj, &BatchClass::Adj, 4}, {&Handle::A, &BatchClass::A, 36},     {&Handle::T, &BatchClass::T, 36},
+    {&Handle::approx, &BatchClass::ap0, 8}, {&Handle::approx2, &BatchClass::ap1, 8}};
+
+static void free_class_slabs(BatchClass& c) {
+  for (const SlabField& f : kSlabFields)
+    if (c.*(f.cp)) {
+      cudaFree(c.*(f.cp));
+      c.*(f.cp) = nullptr;
+    }
+  if (c.red) cudaFree(c.red);
+  c.red = nullptr;
+  if (c.s_main) cudaStreamDestroy(c.s_main);
+  if (c.s_sara) cudaStreamDestroy(c.s_sara);
+  if (c.ev_primal) cudaEventDestroy(c.ev_primal);
+  if (c.ev_sara) cudaEventDestroy(c.ev_sara);
+  c.s_main = c.s_sara = nullptr;
+  c.ev_primal = c.ev_sara = nullptr;
+}
+
+// Moves every handle of the class into freshly allocated slabs (device-to-device copies of its
+// arrays, then its own arrays freed). On failure nothing has moved.
+static cudaError_t move_class_into_slabs(BatchClass& c, int64_t* bytes) {
+  const size_t P = c.hs.size(), N = c.N;
+  cudaError_t e = cudaSuccess;
+  for (const SlabField& f : kSlabFields)
+    if (e == cudaSuccess) e = cudaMalloc((void**)&(c.*(f.cp)), P * f.per_N * N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c.red, P * (size_t)c.red_cap * sizeof(double));
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.s_main, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c.s_sara, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_primal, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_sara, cudaEventDisableTiming);
+  for (size_t p = 0; p < P && e == cudaSuccess; ++p) {
+    Handle* h = c.hs[p];
+    for (const SlabField& f : kSlabFields)
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.*(f.cp) + p * f.per_N * N, h->*(f.hp), f.per_N * N * sizeof(float),
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c.red + p * c.red_cap, h->red, (size_t)c.red_cap * sizeof(double), cudaMemcpyDeviceToDevice,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_class_slabs(c);
+    return e;
+  }
+  for (size_t p = 0; p < P; ++p) {
+    Handle* h = c.hs[p];
+    cudaFree(h->approx);   // approx2 lies in the same allocation
+    h->approx2 = nullptr;
+    for (const SlabField& f : kSlabFields) {
+      if (f.hp != &Handle::approx && f.hp != &Handle::approx2) cudaFree(h->*(f.hp));
+      h->*(f.hp) = c.*(f.cp) + p * f.per_N * N;
+    }
+    cudaFree(h->red);
+    h->red = c.red + p * c.red_cap;
+    const int64_t moved = (int64_t)(112 * N * sizeof(float) + (size_t)c.red_cap * sizeof(double));
+    h->bytes -= moved;
+    *bytes += moved;
+    h->in_slab = true;
+    h->graph_mode = -1;   // the handle's own graph holds the old addresses
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    ++h->version;
+  }
+  return cudaSuccess;
+}
+
+// Copies every handle of the class back into arrays of its own and frees the slabs. A handle
+// whose allocation fails stays in the slabs (which are then kept).
+static void move_class_out_of_slabs(BatchClass& c, int64_t* bytes) {
+  const size_t N = c.N;
+  bool all_out = true;
+  for (size_t p = 0; p < c.hs.size(); ++p) {
+    Handle* h = c.hs[p];
+    if (!h->in_slab) continue;
+    cudaStreamSynchronize(h->stream);
+    float* own[sizeof(kSlabFields) / sizeof(kSlabFields[0])] = {};
+    double* red = nullptr;
+    float* ap = nullptr;
+    cudaError_t e = cudaMalloc((void**)&ap, 16 * N * sizeof(float));
+    size_t k = 0;
+    for (const SlabField& f : kSlabFields) {
+      if (f.hp == &Handle::approx) own[k] = ap;
+      else if (f.hp == &Handle::approx2) own[k] = ap ? ap + 8 * N : nullptr;
+      else if (e == cudaSuccess) e = cudaMalloc((void**)&own[k], f.per_N * N * sizeof(float));
+      ++k;
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&red, (size_t)c.red_cap * sizeof(double));
+    k = 0;
+    for (const SlabField& f : kSlabFields) {
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(own[k], h->*(f.hp), f.per_N * N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream);
+      ++k;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(red, h->red, (size_t)c.red_cap * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      k = 0;
+      for (const SlabField& f : kSlabFields) {
+        if (f.hp != &Handle::approx && f.hp != &Handle::approx2 && own[k]) cudaFree(own[k]);
+        ++k;
+      }
+      if (ap) cudaFree(ap);
+      if (red) cudaFree(red);
+      all_out = false;
+      continue;
+    }
+    k = 0;
+    for (const SlabField& f : kSlabFields) h->*(f.hp) = own[k++];
+    h->red = red;
+    const int64_t moved = (int64_t)(112 * N * sizeof(float) + (size_t)c.red_cap * sizeof(double));
+    h->bytes += moved;
+    *bytes -= moved;
+    h->in_slab = false;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_mode = -1;
+    ++h->version;
+  }
+  if (all_out) free_class_slabs(c);
+}
+
 extern "C" void ps_batch_destroy(ps_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (BatchClass& c : b->classes)
+    if (c.S) move_class_out_of_slabs(c, &b->slab_bytes);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
   for (cudaEvent_t e : b->pre) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -1489,6 +1654,11 @@ extern "C" ps_status ps_batch_create(ps_handle* const* handles, int32_t count, v
       ps_batch_destroy(b);
       ps::set_global_error("batch_create: every handle needs ps_set_measurements first");
       return PS_ESTATE;
+    }
+    if (h->in_slab) {
+      ps_batch_destroy(b);
+      ps::set_global_error("batch_create: a handle belongs to another batch");
+      return PS_EINVAL;
     }
     for (Handle* o : b->hs)
       if (o == h || o->stream == h->stream) {
@@ -1521,12 +1691,47 @@ extern "C" ps_status ps_batch_create(ps_handle* const* handles, int32_t count, v
       ps_batch_destroy(b);
       return batch_fail(e, "batch_create: event");
     }
+  // Size classes (n, levels) in order of first appearance; classes of two or more handles get slabs.
+  for (Handle* h : b->hs) {
+    BatchClass* c = nullptr;
+    for (BatchClass& x : b->classes)
+      if (x.hs[0]->n == h->n && x.hs[0]->L == h->L) c = &x;
+    if (!c) {
+      b->classes.emplace_back();
+      c = &b->classes.back();
+      c->N = h->N;
+      c->red_cap = h->red_cap;
+    }
+    c->hs.push_back(h);
+  }
+  for (BatchClass& c : b->classes) {
+    if (c.hs.size() < 2) continue;
+    if ((e = move_class_into_slabs(c, &b->slab_bytes)) != cudaSuccess) {
+      ps_batch_destroy(b);
+      return batch_fail(e, "batch_create: class slabs");
+    }
+  }
   *out = b;
   return PS_OK;
 }
 
-// Capture one iteration of every handle: fork from the batch stream, one_iteration on
-// each handle's stream, join back.
+// Whether a class can take the class-wide launches in this graph: two or more handles, all in
+// the same SARA mode with the same step sizes, each with measurements. The class-wide SARA
+// launches take the first handle's SARA launch choices (they depend on the image size only);
+// each NUFFT chain keeps its handle's own.
+static bool class_fusable(const BatchClass& c) {
+  if (c.hs.size() < 2 || !c.S) return false;
+  const Handle* a = c.hs[0];
+  if (ps::tv_mode(a->mode)) return false;
+  for (const Handle* h : c.hs)
+    if (h->mode != a->mode || h->tau != a->tau || h->rho1 != a->rho1 || h->rho3 != a->rho3 || h->M == 0 || !h->aux)
+      return false;
+  return true;
+}
+
+// Capture one iteration of every handle: fork from the batch stream; per fusable class the
+// class-wide per-pixel sweep, then its SARA chain beside the problems' NUFFT chains; every
+// other handle's iteration on its own stream; join back.
 static ps_status batch_build(ps_batch* b) {
   for (Handle* h : b->hs) {
     if (!h->derived_valid) {
@@ -1547,12 +1752,50 @@ static ps_status batch_build(ps_batch* b) {
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return batch_fail(e, "batch: begin capture");
   cudaError_t err = cudaEventRecord(b->fork, b->stream);
-  for (size_t i = 0; i < b->hs.size() && err == cudaSuccess; ++i) {
-    Handle* h = b->hs[i];
-    err = cudaStreamWaitEvent(h->stream, b->fork, 0);
-    if (err == cudaSuccess) err = one_iteration(h);
-    if (err == cudaSuccess) err = cudaEventRecord(b->join[i], h->stream);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  auto index_of = [&](const Handle* h) {
+    for (size_t i = 0; i < b->hs.size(); ++i)
+      if (b->hs[i] == h) return i;
+    return (size_t)0;
+  };
+  for (BatchClass& c : b->classes) {
+    c.fused = class_fusable(c);
+    if (!c.fused) {
+      for (Handle* h : c.hs) {
+        const size_t i = index_of(h);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(h->stream, b->fork, 0);
+        if (err == cudaSuccess) err = one_iteration(h);
+        if (err == cudaSuccess) err = cudaEventRecord(b->join[i], h->stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+      }
+      continue;
+    }
+    // A view of the class as one problem of 4 P maps over the slabs.
+    Handle v = *c.hs[0];
+    const int P = (int)c.hs.size();
+    v.S = c.S, v.Z = c.Z, v.C = c.C, v.D = c.D, v.Xb = c.Xb, v.PsiA = c.PsiA, v.Adj = c.Adj;
+    v.A = c.A, v.T = c.T, v.approx = c.ap0, v.approx2 = c.ap1, v.red = c.red;
+    v.nmaps = 4 * P;
+    v.problems = P;
+    v.stream = c.s_main;
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(c.s_main, b->fork, 0);
+    if (err == cudaSuccess) err = ps::primal_sweep(&v);
+    if (err == cudaSuccess) err = cudaEventRecord(c.ev_primal, c.s_main);
+    if (v.mode != PS_NNLS) {
+      v.stream = c.s_sara;
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(c.s_sara, c.ev_primal, 0);
+      if (err == cudaSuccess) err = sara_chain(&v);
+      if (err == cudaSuccess) err = cudaEventRecord(c.ev_sara, c.s_sara);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, c.ev_sara, 0);
+    } else if (err == cudaSuccess) {
+      err = cudaStreamWaitEvent(b->stream, c.ev_primal, 0);
+    }
+    for (Handle* h : c.hs) {
+      const size_t i = index_of(h);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(h->stream, c.ev_primal, 0);
+      if (err == cudaSuccess) err = nufft_chain(h, nullptr);
+      if (err == cudaSuccess) err = cudaEventRecord(b->join[i], h->stream);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
   }
   e = cudaStreamEndCapture(b->stream, &graph);
   if (err != cudaSuccess || e != cudaSuccess) {

@@ -68,7 +68,11 @@ struct Handle {
   float *Adj = nullptr;       // phi^dagger B
   float *tmp4 = nullptr;      // 4N scratch for operators
   float *A = nullptr, *T = nullptr;   // 36N coefficients and thresholds gamma W
-  float *approx = nullptr;    // 2 ping-pong buffers of 32 * (N/4) approximations
+  float *approx = nullptr;    // ping-pong buffers of 32 * (N/4) approximations: approx and approx2
+  float *approx2 = nullptr;
+  int nmaps = 4;              // maps the SARA and primal launches cover (4 P for a batch's size class)
+  int problems = 1;           // problems of a batched primal launch (the per-problem arrays are consecutive)
+  bool in_slab = false;       // state arrays are slices of a batch's class slabs (not freed by ps_destroy)
   double *red = nullptr;      // reduction partials
   int red_cap = 0;
   double *red_host = nullptr; // pinned

@@ -66,13 +66,28 @@ __device__ __forceinline__ void setc(float4& v, int k, float x) {
   else v.w = x;
 }
 
-// One thread = four consecutive pixels (float4 on every plane).
+// One thread = four consecutive pixels (float4 on every plane). grid.y indexes the problems
+// of a batch's size class, whose arrays follow one another (S, C, Xb, PsiA, Adj: 4 N floats
+// each; Z, D: 2 N; A, T: 4 cstride; partials: part_stride doubles); one problem: grid.y = 1.
 __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
     int N, int mode, float tau, float rho1, float rho3, float* __restrict__ S, float* __restrict__ Z,
     float* __restrict__ C, float* __restrict__ D, const float* __restrict__ PsiA, const float* __restrict__ Adj,
     float* __restrict__ Xb, float* __restrict__ A, const float* __restrict__ T, size_t cstride,
-    double* __restrict__ part) {
+    double* __restrict__ part, size_t part_stride) {
   __shared__ double sh[kSweepThreads / 32][8];
+  if (blockIdx.y) {
+    const size_t p = blockIdx.y, n4 = 4 * (size_t)N, n2 = 2 * (size_t)N;
+    S += p * n4;
+    C += p * n4;
+    Xb += p * n4;
+    PsiA += p * n4;
+    Adj += p * n4;
+    Z += p * n2;
+    D += p * n2;
+    A += p * 4 * cstride;
+    T += p * 4 * cstride;
+    part += p * part_stride;
+  }
   float dss[4] = {0.f, 0.f, 0.f, 0.f}, ss[4] = {0.f, 0.f, 0.f, 0.f};
   const int i = 4 * (blockIdx.x * kSweepThreads + threadIdx.x);
   const float inv_r3 = 1.0f / rho3;
@@ -199,10 +214,10 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_primal(
 int sweep_blocks(int N) { return (N + kSweepThreads * kSweepPix - 1) / (kSweepThreads * kSweepPix); }
 
 cudaError_t primal_sweep(Handle* h) {
-  const int nb = sweep_blocks(h->N);
-  k_primal<<<nb, kSweepThreads, 0, h->stream>>>(h->N, h->mode, (float)h->tau, (float)h->rho1, (float)h->rho3, h->S,
-                                                h->Z, h->C, h->D, h->PsiA, h->Adj, h->Xb, h->A, h->T,
-                                                (size_t)kBases * h->N, h->red);
+  const dim3 grid(sweep_blocks(h->N), h->problems);
+  k_primal<<<grid, kSweepThreads, 0, h->stream>>>(h->N, h->mode, (float)h->tau, (float)h->rho1, (float)h->rho3, h->S,
+                                                  h->Z, h->C, h->D, h->PsiA, h->Adj, h->Xb, h->A, h->T,
+                                                  (size_t)kBases * h->N, h->red, (size_t)h->red_cap);
   return cudaGetLastError();
 }
 
@@ -220,7 +235,7 @@ __global__ void k_dirac(int N, const float* __restrict__ X, float* __restrict__ 
 
 cudaError_t dirac_apply(Handle* h, const float* X, float* coef, float* thr, int mode, float scale, float gamma,
                         float delta) {
-  dim3 grid((h->N + 255) / 256, 4);
+  dim3 grid((h->N + 255) / 256, h->nmaps);
   k_dirac<<<grid, 256, 0, h->stream>>>(h->N, X, coef, thr, (size_t)kBases * h->N, mode, scale, gamma, delta);
   return cudaGetLastError();
 }

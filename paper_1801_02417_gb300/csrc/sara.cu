@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(256, 2) k_ana_pers(const float* __restrict__ i
                                                      int n, int last, float* __restrict__ coef,
                                                      float* __restrict__ thr, float* __restrict__ approx_out,
                                                      int mode, float scale, float gamma, float delta, int* err,
-                                                     const __grid_constant__ SaraTma tm) {
+                                                     int nmaps, const __grid_constant__ SaraTma tm) {
   extern __shared__ __align__(128) float4 smp[];
   float* in_s = reinterpret_cast<float*>(smp);
   float* lo_s = in_s + kA2In;
@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(256, 2) k_ana_pers(const float* __restrict__ i
   float* st = in_s + kAnaPre;                                        // set s: A at st + 2 s kStage, gamma W after it
   uint64_t* bar = reinterpret_cast<uint64_t*>(st + 4 * kStage);     // [0] input rows, [1 + s] stage set s
   const int hm = m >> 1, tilesx = hm / kTO, tiles = tilesx * tilesx;
-  const int units = tiles * kDb * 4;
+  const int units = tiles * kDb * nmaps;
   const bool staged = mode == SARA_DUAL;
   if (threadIdx.x == 0)
     for (int q = 0; q < 3; ++q) mbar_init(&bar[q], 1);
@@ -1145,13 +1145,13 @@ __global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
 // CTA's start nor the end of a unit exposes a copy's latency, and no wave runs part-full.
 __global__ void __launch_bounds__(256, 4)
     k_syn2_fine_pers(const float* __restrict__ coef, const float* __restrict__ approx_in, int coarsest, int n,
-                     float* __restrict__ out, int* err, const __grid_constant__ SaraTma tm) {
+                     float* __restrict__ out, int* err, int nmaps, const __grid_constant__ SaraTma tm) {
   extern __shared__ __align__(128) float4 sm2[];
   float* const s4 = reinterpret_cast<float*>(sm2);
   float* loT = s4 + kC2Set;
   float* hiT = loT + kLoSize;
   uint64_t* bar = reinterpret_cast<uint64_t*>(hiT + kLoSize);
-  const int tilesx = n / kT2, units = tilesx * tilesx * 4;
+  const int tilesx = n / kT2, units = tilesx * tilesx * nmaps;
   const int hm = n >> 1;
   auto issue = [&](int unit, int bi) {
     const int map = unit / (tilesx * tilesx), t = unit % (tilesx * tilesx);
@@ -1445,23 +1445,25 @@ static int make_map(CUtensorMap* map, const float* base, uint64_t width, uint64_
 
 // Maps of one tiled analysis level: input planes of side m (`planes` of them), and the
 // coefficient and threshold arrays (36 n x n) for the staged epilogue operands.
-static SaraTma analysis_maps(const float* in, int m, int planes, const float* coef, const float* thr, int n, int mode) {
+static SaraTma analysis_maps(const float* in, int m, int planes, const float* coef, const float* thr, int n, int nmaps,
+                             int mode) {
   SaraTma t;
   std::memset(&t, 0, sizeof(t));
   t.use_in = make_map(&t.in, in, (uint64_t)m, (uint64_t)planes * m, kA2Pitch, kRSmax);
   if (mode == SARA_DUAL)
-    t.use_stage = make_map(&t.coef, coef, (uint64_t)n, 36ull * n, kTO, kTO) &
-                  make_map(&t.thr, thr, (uint64_t)n, 36ull * n, kTO, kTO);
+    t.use_stage = make_map(&t.coef, coef, (uint64_t)n, (uint64_t)kBases * nmaps * n, kTO, kTO) &
+                  make_map(&t.thr, thr, (uint64_t)n, (uint64_t)kBases * nmaps * n, kTO, kTO);
   return t;
 }
 
 // Maps of one tiled synthesis level of output side m: coefficients and, below the coarsest
 // level, the 32 (map, basis) approximations of side m / 2.
-static SaraTma synthesis_maps(const float* coef, const float* approx_in, int m, int n) {
+static SaraTma synthesis_maps(const float* coef, const float* approx_in, int m, int n, int nmaps) {
   SaraTma t;
   std::memset(&t, 0, sizeof(t));
-  t.use_scoef = make_map(&t.scoef, coef, (uint64_t)n, 36ull * n, kC2Pitch, kC2Rows);
-  if (approx_in) t.use_apx = make_map(&t.apx, approx_in, (uint64_t)(m / 2), 32ull * (m / 2), kC2Pitch, kC2Rows);
+  t.use_scoef = make_map(&t.scoef, coef, (uint64_t)n, (uint64_t)kBases * nmaps * n, kC2Pitch, kC2Rows);
+  if (approx_in)
+    t.use_apx = make_map(&t.apx, approx_in, (uint64_t)(m / 2), (uint64_t)kDb * nmaps * (m / 2), kC2Pitch, kC2Rows);
   return t;
 }
 
@@ -1518,8 +1520,8 @@ cudaError_t configure_kernels() {
 cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, int mode, float scale, float gamma,
                           float delta, cudaEvent_t fine_done) {
   const int n = h->n, L = h->L;
-  const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
-  float* buf[2] = {h->approx, h->approx + quarter};
+  const int nmaps = h->nmaps;
+  float* buf[2] = {h->approx, h->approx2};
   int lt = L + 1;                                   // first level of the fused tail
   for (int l = 1; l <= L; ++l)
     if ((n >> (l - 1)) <= kTail) {
@@ -1529,11 +1531,11 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
   // Levels with input side > kTail: tiled, one launch per level (half side >= 128).
   for (int l = 1; l < lt; ++l) {
     const int m = n >> (l - 1), hm = m / 2;
-    const dim3 grid((hm / kTO) * (hm / kTO), kDb, 4);
+    const dim3 grid((hm / kTO) * (hm / kTO), kDb, nmaps);
     if (l == 1 && h->tune[PS_TUNE_ANALYSIS] >= 2) {
       const int choice = h->tune[PS_TUNE_ANALYSIS], nb = choice == 2 ? 8 : 4;
-      const dim3 gm((hm / kTO) * (hm / kTO), kDb / nb, 4);
-      const SaraTma tm = analysis_maps(X, n, 4, coef, thr, n, mode);
+      const dim3 gm((hm / kTO) * (hm / kTO), kDb / nb, nmaps);
+      const SaraTma tm = analysis_maps(X, n, nmaps, coef, thr, n, nmaps, mode);
       if (choice == 2)
         k_ana_l1m<8, 256><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
                                                                          scale, gamma, delta, h->dev_flags, tm);
@@ -1552,16 +1554,16 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
       const int ctas = std::min(units, 2 * std::max(1, h->num_sms));
       const float* in = l == 1 ? X : buf[(l - 2) & 1];
       const size_t in_map = l == 1 ? (size_t)n * n : (size_t)kDb * m * m, in_basis = l == 1 ? 0 : (size_t)m * m;
-      const SaraTma tm = analysis_maps(in, m, l == 1 ? 4 : 32, coef, thr, n, mode);
+      const SaraTma tm = analysis_maps(in, m, l == 1 ? nmaps : kDb * nmaps, coef, thr, n, nmaps, mode);
       k_ana_pers<<<ctas, 256, pers_analysis_smem(), h->stream>>>(in, in_map, in_basis, m, n, l == L, coef, thr,
                                                                  buf[(l - 1) & 1], mode, scale, gamma, delta,
-                                                                 h->dev_flags, tm);
+                                                                 h->dev_flags, nmaps, tm);
       if (l == 1 && fine_done) {
         const cudaError_t e = cudaEventRecord(fine_done, h->stream);
         if (e != cudaSuccess) return e;
       }
     } else if (l == 1) {
-      const SaraTma tm = analysis_maps(X, n, 4, coef, thr, n, mode);
+      const SaraTma tm = analysis_maps(X, n, nmaps, coef, thr, n, nmaps, mode);
       k_ana_l1<<<grid, 256, fast_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[(l - 1) & 1], mode, scale,
                                                               gamma, delta, h->dev_flags, tm);
       if (fine_done) {
@@ -1569,7 +1571,7 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
         if (e != cudaSuccess) return e;
       }
     } else {
-      const SaraTma tm = analysis_maps(buf[(l - 2) & 1], m, 32, coef, thr, n, mode);
+      const SaraTma tm = analysis_maps(buf[(l - 2) & 1], m, kDb * nmaps, coef, thr, n, nmaps, mode);
       k_ana_lv<<<grid, 256, fast_analysis_smem(), h->stream>>>(buf[(l - 2) & 1], m, n, l == L, coef, thr,
                                                               buf[(l - 1) & 1], mode, scale, gamma, delta,
                                                               h->dev_flags, tm);
@@ -1577,7 +1579,7 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
   }
   if (lt <= L) {
     const float* in = lt == 1 ? X : buf[(lt - 2) & 1];
-    k_ana_tail<<<dim3(kDb, 4), kTailThreads, ana_tail_smem(n >> (lt - 1)), h->stream>>>(in, lt, L, n, coef, thr,
+    k_ana_tail<<<dim3(kDb, nmaps), kTailThreads, ana_tail_smem(n >> (lt - 1)), h->stream>>>(in, lt, L, n, coef, thr,
                                                                                          mode, scale, gamma, delta);
     if (lt == 1 && fine_done) {
       const cudaError_t e = cudaEventRecord(fine_done, h->stream);
@@ -1590,10 +1592,10 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
 // Psi A on `stream` with `approx` as the per-level approximation scratch
 // (2 x 32 x (n/2)^2 floats); `err` (may be null) receives the bounded-wait flag;
 // `variant` is the PS_TUNE_SYNTHESIS choice of the finest level.
-static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx,
-                                    int* err, int variant, cudaEvent_t fine_start = nullptr) {
-  const size_t quarter = (size_t)kDb * 4 * (n / 2) * (n / 2);
-  float* buf[2] = {approx, approx + quarter};
+static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const float* coef, float* out, float* approx0,
+                                    float* approx1, int nmaps, int* err, int variant,
+                                    cudaEvent_t fine_start = nullptr) {
+  float* buf[2] = {approx0, approx1};
   int lt = 0;                                       // lowest level of the fused tail (>= 2), 0: none
   for (int l = 2; l <= L; ++l)
     if ((n >> (l - 1)) <= kTailSyn) {
@@ -1601,7 +1603,7 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
       break;
     }
   if (lt)
-    k_syn_tail<<<dim3(kDb, 4), kTailThreads, syn_tail_smem(n >> (lt - 1)), stream>>>(coef, L, lt, n,
+    k_syn_tail<<<dim3(kDb, nmaps), kTailThreads, syn_tail_smem(n >> (lt - 1)), stream>>>(coef, L, lt, n,
                                                                                       buf[(lt - 1) & 1]);
   for (int l = lt ? lt - 1 : L; l >= 1; --l) {
     const int m = n >> (l - 1);
@@ -1613,25 +1615,25 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
       const cudaError_t e = cudaEventRecord(fine_start, stream);
       if (e != cudaSuccess) return e;
     }
-    const SaraTma tm = m >= kT2 ? synthesis_maps(coef, ain, m, n) : SaraTma{};
+    const SaraTma tm = m >= kT2 ? synthesis_maps(coef, ain, m, n, nmaps) : SaraTma{};
     if (m >= kT2 && l == 1) {
-      const dim3 grid((m / kT2) * (m / kT2), 1, 4);
+      const dim3 grid((m / kT2) * (m / kT2), 1, nmaps);
       if (variant == 2) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int units = (int)(grid.x * grid.z);
         k_syn2_fine_pers<<<std::min(units, 4 * std::max(1, sms)), 256, syn2_smem(1), stream>>>(coef, ain, l == L, n,
-                                                                                              out, err, tm);
+                                                                                              out, err, nmaps, tm);
       } else if (variant == 1) k_syn2_fine<1><<<grid, 256, syn2_smem(1), stream>>>(coef, ain, l == L, n, out, err, tm);
       else k_syn2_fine<2><<<grid, 256, syn2_smem(2), stream>>>(coef, ain, l == L, n, out, err, tm);
     } else if (m >= kT2) {
-      k_syn2_lv<<<dim3((m / kT2) * (m / kT2), 4, kDb), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
+      k_syn2_lv<<<dim3((m / kT2) * (m / kT2), nmaps, kDb), 256, syn2_smem(1), stream>>>(coef, ain, l == L, m, n, aout,
                                                                                      err, tm);
     } else if (m >= kTI && l == 1) {
-      k_syn_fine<<<dim3(tiles, 1, 4), 256, 0, stream>>>(coef, ain, l == L, n, out);
+      k_syn_fine<<<dim3(tiles, 1, nmaps), 256, 0, stream>>>(coef, ain, l == L, n, out);
     } else {
-      dim3 grid(tiles, l == 1 ? 1 : kDb, 4);
+      dim3 grid(tiles, l == 1 ? 1 : kDb, nmaps);
       k_synthesis<<<grid, 256, synthesis_smem(TI), stream>>>(coef, ain, l == L, m, TI, n, l == 1, aout, out);
     }
   }
@@ -1639,7 +1641,8 @@ static cudaError_t synthesis_levels(cudaStream_t stream, int n, int L, const flo
 }
 
 cudaError_t sara_synthesis(Handle* h, const float* coef, float* out, cudaEvent_t fine_start) {
-  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->dev_flags, h->tune[PS_TUNE_SYNTHESIS],
+  return synthesis_levels(h->stream, h->n, h->L, coef, out, h->approx, h->approx2, h->nmaps, h->dev_flags,
+                          h->tune[PS_TUNE_SYNTHESIS],
                           fine_start);
 }
 
@@ -1728,7 +1731,9 @@ extern "C" ps_status ps_apply_psi_static(const float* A, float* S, int32_t n, in
     flag = g_static_err_ptr[dev];
   }
   e = cudaMemsetAsync(flag, 0, sizeof(int), (cudaStream_t)cuda_stream);
-  if (e == cudaSuccess) e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, flag, 0);
+  if (e == cudaSuccess)
+    e = synthesis_levels((cudaStream_t)cuda_stream, n, levels, A, S, scratch, scratch + kStaticScratchFloats / 2, 4, flag,
+                         0);
   if (e != cudaSuccess) {
     set_global_error(std::string("apply_psi_static: launch: ") + cudaGetErrorString(e));
     return PS_ECUDA;

@@ -66,10 +66,62 @@ def test_batch_graph_matches_individual_iterations(problems):
             s.close()
 
 
-def test_batched_algorithm2_matches_solo_solves(problems):
+@pytest.fixture(scope="module")
+def class_problems():
+    """Two size classes of several problems each (the batch keeps each class's state in shared
+    slabs and runs its per-pixel sweep and SARA transforms as class-wide launches), plus a
+    single problem of a third class."""
+    specs = [(64, 3, 2500, 11, 1), (64, 3, 4000, 12, 2), (64, 3, 1800, 13, 1), (128, 3, 9000, 14, 2),
+             (128, 3, 15000, 15, 4), (32, 2, 900, 16, 1)]
+    return [synthesize_problem(n, L, M, seed, nb) for (n, L, M, seed, nb) in specs]
+
+
+def test_class_fused_batch_matches_individual_iterations(class_problems):
+    """Iterations of a batch whose size classes run as class-wide launches (and after the batch
+    is destroyed, each handle's own arrays again) against the same iterations one handle at a
+    time; a handle switched to another mode takes its class out of the fused launches (still
+    correct)."""
+    probs = class_problems
+    solo = []
+    for i, p in enumerate(probs):
+        with _start(p) as s:
+            s.pd_iterate(30)
+            if i == 1:
+                s.set_mode(B.PS_SOC)
+            s.pd_iterate(20)
+            s.set_mode(B.PS_POLARIZED)
+            s.pd_iterate(10)
+            solo.append(s.get_stokes())
+    ss = [_start(p) for p in probs]
+    b = B.ps_batch_create([s.h for s in ss])
+    try:
+        B.ps_batch_iterate(b, 30)
+        ss[1].set_mode(B.PS_SOC)              # class (64, 3) no longer uniform: per-handle iterations
+        B.ps_batch_iterate(b, 20)
+        ss[1].set_mode(B.PS_POLARIZED)        # uniform again: class-wide launches
+        B.ps_batch_iterate(b, 10)
+        B.ps_batch_synchronize(b)
+        for s, ref in zip(ss, solo):
+            assert _rel(s.get_stokes(), ref) <= TOL
+        dev = [B.ps_device_bytes(s.h) for s in ss]
+    finally:
+        B.ps_batch_destroy(b)
+    try:
+        # Back in arrays of their own (the slab bytes return to the handles), still iterating.
+        for s, d in zip(ss, dev):
+            assert B.ps_device_bytes(s.h) >= d
+            s.pd_iterate(2)
+            assert np.all(np.isfinite(s.get_stokes()))
+    finally:
+        for s in ss:
+            s.close()
+
+
+def test_batched_algorithm2_matches_solo_solves(class_problems):
     """Whole Algorithm 2 solves run in lockstep through one batch graph per iteration
-    (solver.solve_batched: reweights queued on each handle's stream between batch launches)
-    give each problem the maps of its solo solve."""
+    (solver.solve_batched: reweights queued on each handle's stream between batch launches,
+    size classes in class-wide launches) give each problem the maps of its solo solve."""
+    problems = class_problems
     sch = [Schedule(150, 2, p.gamma) for p in problems]
     solo = []
     for p, sc in zip(problems, sch):
