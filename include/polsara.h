@@ -352,7 +352,7 @@ void ps_batch_destroy(ps_batch* b);
  * fastest depends on the image size and on how the visibilities fill the uv plane,
  * so it is measured on the handle's own problem). Values index the candidates: */
 enum {
-  PS_TUNE_SYNTHESIS = 0,  /* finest synthesis level: 0 double-buffered subband staging (2 CTAs/SM),
+  PS_TUNE_SYNTHESIS = 0,  /* finest synthesis level: 0 double-buffered subband staging (3 CTAs/SM),
                              1 single-buffered, refilled during the x-pass (4 CTAs/SM),
                              2 as 1 in persistent CTAs looping over (tile, map) units, the staging
                                running on from one unit into the next */

@@ -108,6 +108,30 @@ def phi_adjoint_at(B: np.ndarray, uv: np.ndarray, w: np.ndarray, n: int, pixels:
     return out
 
 
+def phi_adjoint_grid(B: np.ndarray, uv: np.ndarray, w: np.ndarray, n: int, ys, xs) -> np.ndarray:
+    """phi^dagger(B) at every pixel (y, x) of the product of the image rows `ys` and columns `xs`:
+    (4, len(ys), len(xs)).
+
+    The same sum as phi_adjoint_at, Re sum_m exp(+i (omega_u,m x + omega_v,m y)) w_m [B L^H]_{m,s},
+    with the phase split into its y and x factors so that the pixels of the product grid come
+    out of one matrix product over the rows m (checks along tile and window boundaries of
+    large maps).
+    """
+    X = (B @ np.conj(L_MIX).T) * w[:, None]                    # (M, 4)
+    cy = np.asarray(ys, dtype=np.float64) - n / 2
+    cx = np.asarray(xs, dtype=np.float64) - n / 2
+    out = np.zeros((4, len(cy), len(cx)))
+    M = uv.shape[0]
+    ch = 1 << 16
+    for m0 in range(0, M, ch):
+        m1 = min(M, m0 + ch)
+        ex = np.exp(1j * np.outer(uv[m0:m1, 0], cx))            # (m, len(xs))
+        ey = np.exp(1j * np.outer(uv[m0:m1, 1], cy))            # (m, len(ys))
+        for s in range(4):
+            out[s] += np.real((ey * X[m0:m1, s][:, None]).T @ ex)
+    return out
+
+
 def phi_dense(uv: np.ndarray, w: np.ndarray, n: int) -> np.ndarray:
     """Dense real matrix of phi acting on vec(S) (4N reals) -> real/imag parts of vec(Y) (8M).
 

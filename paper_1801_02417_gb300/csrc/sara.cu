@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(256, 3) k_syn_fine(const float* __restrict__ c
 constexpr int kT2 = 64;                                  // output tile side
 constexpr int kC2Rows = kT2 / 2 + kMaxTaps / 2 - 1;      // 39 coefficient rows (db8 halo)
 constexpr int kC2Cols = kT2 / 2 + 8;                     // 40 staged columns: [ox0/2 - 8, ox0/2 + 32)
-constexpr int kC2Pitch = 52;                             // staged row pitch (2 x 52 = 8 mod 32 banks)
+constexpr int kC2Pitch = 40;                             // staged row pitch: the 40 staged columns
 constexpr int kC2Sub = (kC2Rows * kC2Pitch + 31) / 32 * 32;   // one subband tile, 128-byte aligned
 constexpr int kC2Set = 4 * kC2Sub;                       // LL, LH, HL, HH
 constexpr int kLoPitch = kT2 + 4;                        // column-major intermediates: [column][row]
@@ -1076,11 +1076,11 @@ __device__ __forceinline__ void syn2_abort(uint64_t* b0, uint32_t p0, uint64_t* 
 }
 
 // Finest level (m = n >= 64): the eight bases plus the Dirac part summed in registers -> Psi A.
-// NBUF = 2: two staging sets, basis b+1 copied while basis b is filtered (2 CTAs per SM).
+// NBUF = 2: two staging sets, basis b+1 copied while basis b is filtered (3 CTAs per SM).
 // NBUF = 1: one staging set, refilled with basis b+1 as soon as the y-pass of basis b
 // has read it, so the copy overlaps the x-pass (4 CTAs per SM hide the rest).
 template <int NBUF>
-__global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 2)
+__global__ void __launch_bounds__(256, NBUF == 1 ? 4 : 3)
     k_syn2_fine(const float* __restrict__ coef, const float* __restrict__ approx_in, int coarsest, int n,
                 float* __restrict__ out, int* err, const __grid_constant__ SaraTma tm) {
   extern __shared__ __align__(128) float4 sm2[];

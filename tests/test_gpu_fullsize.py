@@ -189,3 +189,71 @@ def test_sara_every_launch_choice_full_maps(big):
         assert _rel(o, outs[0]) <= 1e-6
     for c in coefs[1:]:
         assert _rel(c, coefs[0]) <= 1e-6
+
+
+# Rows and columns on the image edges, the centre and the boundaries of the 32- and 64-wide
+# SARA tiles and of the FFT halves, plus seeded interior ones.
+_EDGE_LINES = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 255, 256, 257, 511, 512, 513, 767, 768, 1021, 1022, 1023]
+
+
+def test_phi_adjoint_on_boundary_grid_with_elementwise_bound(big):
+    """phi^dagger of the 2M rows on the 1,600 pixels where 40 rows cross 40 columns chosen on tile,
+    centre and edge boundaries (and at random): relative l2 within 1e-5 and every element within
+    1e-5 of the largest value, so no boundary error hides in a global norm."""
+    s, uv, w, Y = big["s"], big["uv"], big["w"], big["Y"]
+    img = np.empty((4, WL.n, WL.n), np.float32)
+    B.ps_apply_phi_adjoint(s.h, Y, img)
+    rng = np.random.default_rng(19)
+    lines = sorted(set(_EDGE_LINES) | set(rng.integers(0, WL.n, 18).tolist()))
+    ys, xs = lines[:40], lines[-40:]
+    ref = meas.phi_adjoint_grid(Y.astype(np.complex128), uv, w.astype(np.float64), WL.n, ys, xs)
+    got = img[:, ys][:, :, xs].astype(np.float64)
+    assert _rel(got, ref) <= 1e-5
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def test_one_iteration_duals_at_full_size():
+    """One iteration at 1024^2 / 2M rows from a random state: the l1 dual A (every coefficient,
+    steps 5-6: clamp(A + rho1 Psi^dagger X^bar, +-gamma W) with the oracle's Psi^dagger of the
+    GPU's X^bar = 2 S' - S) and the data dual B of one block made of 256 rows (steps 7-8: the
+    oracle's direct DFT of X^bar on those rows, the block's ball factor, B = c_b (B~/rho2 - Y)),
+    within the one-iteration bound 2e-5."""
+    from paper_1801_02417_gb300 import _build
+    _build.build_library()
+    n, M = WL.n, WL.M
+    uv = inputs.uv_coverage(WL)
+    w = inputs.visibility_weights(M, WL.seed, 0.2).astype(np.float32)
+    rng = np.random.default_rng(23)
+    Y = (0.05 * (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4)))).astype(np.complex64)
+    off = np.concatenate([[0, 256], inputs.block_offsets(M - 256, 31)[1:] + 256]).astype(np.int64)
+    eps = np.full(32, 30.0)
+    eps[0] = 0.5
+    st = {"S": (0.1 * rng.normal(size=(4, n, n))).astype(np.float32),
+          "Z": (0.1 * rng.normal(size=(2, n, n))).astype(np.float32),
+          "A": (0.01 * rng.normal(size=(4, 9, n, n))).astype(np.float32),
+          "C": (0.1 * rng.normal(size=(4, n, n))).astype(np.float32),
+          "D": (0.1 * rng.normal(size=(2, n, n))).astype(np.float32)}
+    W = rng.uniform(0.2, 1.0, size=(4, 9, n, n)).astype(np.float32)
+    gamma = 0.01
+    with PolarizedSARA(n, WL.levels) as s:
+        s.set_measurements(uv, Y, w, off, eps)
+        par = s.params()
+        # B on the scale of rho2 phi(X^bar) (per row ~ 0.1 sqrt(N) = 100), so that both terms of
+        # B~ = B + rho2 phi(X^bar) count in the comparison.
+        st["B"] = (par["rho2"] * 50.0 * (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4)))).astype(np.complex64)
+        s.set_sara_weights(W, gamma)
+        s.set_state(st)
+        s.pd_iterate(1)
+        got = s.get_state()
+    Xb = 2.0 * got["S"].astype(np.float64) - st["S"].astype(np.float64)
+    T = gamma * W.astype(np.float64)
+    A_ref = np.clip(st["A"] + par["rho1"] * wav.psi_adjoint(Xb, WL.levels), -T, T)
+    assert _rel(got["A"], A_ref) <= 2e-5
+    rows = np.arange(256)
+    w64 = w.astype(np.float64)
+    Bt = st["B"][rows].astype(np.complex128) + par["rho2"] * meas.phi(Xb, uv[rows], w64[rows])
+    R = Bt / par["rho2"] - Y[rows].astype(np.complex128)
+    r = np.linalg.norm(R)
+    c_b = par["rho2"] * (1.0 - min(1.0, eps[0] / r))
+    assert c_b > 0                                   # the ball constraint is active for this block
+    assert _rel(got["B"][rows], c_b * R) <= 2e-5

@@ -121,3 +121,17 @@ def test_pixel_sampled_adjoint_matches_full_adjoint():
     pix = np.array([[0, 0], [3, 7], [9, 9], [5, 5]])
     got = meas.phi_adjoint_at(B, uv, w, 10, pix)
     assert np.allclose(got, full[:, pix[:, 0], pix[:, 1]], atol=1e-12)
+
+
+def test_phi_adjoint_grid_equals_the_full_adjoint():
+    """The product-grid evaluation of phi^dagger (one matrix product per map) against the full
+    adjoint on the same data."""
+    rng = np.random.default_rng(21)
+    n, M = 16, 300
+    uv = rng.uniform(-2.5, 2.5, size=(M, 2))
+    w = rng.uniform(0.5, 1.5, size=M)
+    B = rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))
+    full = meas.phi_adjoint(B, uv, w, n)
+    ys, xs = [0, 7, 15], [1, 8, 9, 15]
+    got = meas.phi_adjoint_grid(B, uv, w, n, ys, xs)
+    assert np.allclose(got, full[:, ys][:, :, xs], rtol=1e-12, atol=1e-10)
