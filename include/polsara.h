@@ -357,7 +357,9 @@ enum {
                              2 as 1 in persistent CTAs looping over (tile, map) units, the staging
                                running on from one unit into the next */
   PS_TUNE_DEGRID = 1,     /* 0 one row per thread over a work item,
-                             1 one same-cell chunk per warp (broadcast stencil reads) */
+                             1 one same-cell chunk per warp (broadcast stencil reads),
+                             2 as 0 with registers capped for 6 CTAs per SM (W = 7; other widths
+                               run 0) */
   PS_TUNE_GRID = 2,       /* 0 one warp per same-cell chunk (2 kernel cells per lane),
                              1 half-warps on alternate rows of a chunk (4 cells per lane),
                              2 lanes own (stencil row, channel pair) (W <= 8; W = 9 runs 0),

@@ -332,6 +332,14 @@ __device__ __forceinline__ void degrid_finish(int m, bool active, float w, float
   }
 }
 
+// Ask L1 for the row's inputs of degrid_finish (R, Y: one 32-byte sector each) before the
+// interpolation, so that their latency overlaps it instead of following it.
+__device__ __forceinline__ void degrid_prefetch(int m, int mode, const float2* R, const float2* Yv) {
+  if (mode == DEG_APPLY) return;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(Yv + 4 * (size_t)m));
+  if (mode == DEG_DUAL) asm volatile("prefetch.global.L1 [%0];" ::"l"(R + 4 * (size_t)m));
+}
+
 // One row of a degridding work item on the CUDA cores: the 2 W^2 taps read from the
 // staged spectrum cells, then degrid_finish (warp-collective, like it).
 template <int W>
@@ -347,6 +355,7 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
   float4 sp = make_float4(0.f, 0.f, 0.f, 0.f), sn = sp;
   float w = 0.f;
   if (active) {
+    degrid_prefetch(m, mode, R, Yv);
     float fx, fy;
     int cx, cy;
     unpack_rec(rec[m], fx, fy, w, cx, cy);
@@ -397,9 +406,10 @@ __device__ __forceinline__ void degrid_row(int m, bool active, const GridItem& i
 // atomics beyond) and one global FP64 atomic per block and CTA (block_sum, cleared
 // by the caller).
 // FORM 0: one row per thread over the item; 1: one same-cell chunk per warp (broadcast
-// stencil reads).
+// stencil reads); 2: as 0 with registers capped for 6 CTAs per SM at W = 7 (40 instead of
+// 51, so more rows are in flight per SM; other widths would spill under a cap and run as 0).
 template <int W, int FORM>
-__global__ void __launch_bounds__(256) k_degrid(
+__global__ void __launch_bounds__(256, (FORM == 2 && W == 7) ? 6 : 0) k_degrid(
     const GridItem* __restrict__ items, const int32_t* __restrict__ chunks, const float4* __restrict__ rec, const float4* __restrict__ G, int Wd,
     int off, int full, int K, float beta, int mode, float2* __restrict__ R, const float2* __restrict__ Yv,
     const float* __restrict__ cb, float inv_rho2, const uint16_t* __restrict__ vblk, int nblocks,
@@ -1023,9 +1033,10 @@ cudaError_t configure_nufft_kernels() {
     if ((e = set_smem(grids[i], grid_bytes[i])) != cudaSuccess) return e;
   // Per-block FP64 accumulators of the degridding kernels (up to 2047 blocks).
   const void* degrids[] = {(const void*)k_degrid<5, 0>, (const void*)k_degrid<7, 0>, (const void*)k_degrid<9, 0>,
-                           (const void*)k_degrid<5, 1>, (const void*)k_degrid<7, 1>, (const void*)k_degrid<9, 1>};
+                           (const void*)k_degrid<5, 1>, (const void*)k_degrid<7, 1>, (const void*)k_degrid<9, 1>,
+                           (const void*)k_degrid<5, 2>, (const void*)k_degrid<7, 2>, (const void*)k_degrid<9, 2>};
   const size_t degrid_smem[] = {degrid_smem_tiles<5>(), degrid_smem_tiles<7>(), degrid_smem_tiles<9>()};
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 9; ++i)
     if ((e = set_smem(degrids[i], degrid_smem[i % 3] + 2048 * sizeof(double))) != cudaSuccess) return e;
   return set_smem((const void*)k_adj_cols, sm2);
 }
@@ -1043,7 +1054,8 @@ static void launch_degrid(Handle* h, int mode, float2* out) {
   const GridGeom& g = h->g;
   const int nbins = h->nblocks <= kWarpBins ? kWarpBins * 8 : h->nblocks;   // 8 warps of 256 threads
   const size_t sm = degrid_smem_tiles<W>() + (size_t)nbins * sizeof(double);
-  auto kern = h->tune[PS_TUNE_DEGRID] == 1 ? k_degrid<W, 1> : k_degrid<W, 0>;
+  const int form = h->tune[PS_TUNE_DEGRID];
+  auto kern = form == 1 ? k_degrid<W, 1> : (form == 2 ? k_degrid<W, 2> : k_degrid<W, 0>);
   kern<<<h->nitems, 256, sm, h->stream>>>(h->items, h->gchunks, h->rec, h->G, g.Wd, g.off, g.full, g.K, g.beta, mode,
                                           h->R, h->Y, h->cb, (float)(1.0 / h->rho2), h->vblk, h->nblocks,
                                           h->block_sum, out);

@@ -72,7 +72,7 @@ def test_phi_every_degridding_choice(big):
     saved = B.ps_get_tuning(s.h)
     outs = []
     try:
-        for choice in range(2):
+        for choice in range(3):
             B.ps_set_tuning(s.h, saved[:1] + [choice] + saved[2:])
             out = np.empty((WL.M, 4), np.complex64)
             B.ps_apply_phi(s.h, big["truth"], out)
