@@ -340,6 +340,47 @@ def default_gamma(s, dirty: np.ndarray, factor: float = 1e-3) -> float:
     return factor * float(np.max(np.abs(s.psi_adjoint(dirty)))) / on
 
 
+def small_configs(iters: int = 500) -> dict:
+    """Iteration rate of the small workloads (64^2 / 2,000 rows and 256^2 / 50,000 rows) on
+    the same launch path (autotuned choices, multi-iteration graphs), timed with CUDA events on
+    the handle's stream; at these sizes an iteration is a chain of short kernels, so the rate
+    measures launch and dependency latency more than bandwidth."""
+    import torch
+    from paper_1801_02417_gb300 import binding as B
+    from paper_1801_02417_gb300.solver import PolarizedSARA
+    out = {}
+    stream = torch.cuda.Stream()
+    for name in ("img64_m2k", "img256_m50k"):
+        wl = inputs.WORKLOADS[name]
+        uv, w, truth, off = make_inputs(wl)
+        with PolarizedSARA(wl.n, wl.levels, stream=stream.cuda_stream) as s:
+            s.set_measurements(uv, np.zeros((wl.M, 4), np.complex64), w, off, np.ones(wl.nblocks))
+            clean = np.empty((wl.M, 4), np.complex64)
+            B.ps_apply_phi(s.h, truth, clean)
+            sigma = inputs.sigma_for_snr(clean, wl.snr_db)
+            Y = (clean + inputs.complex_noise(wl.M, sigma, wl.seed)).astype(np.complex64)
+            eps = np.array([chi2_epsilon(int(off[b + 1] - off[b]), sigma) for b in range(wl.nblocks)])
+            s.set_measurements(uv, Y, w, off, eps)
+            s.set_sara_weights(None, 0.0)
+            s.set_mode(B.PS_POLARIZED)
+            picks = B.ps_autotune(s.h, reps=5)
+            s.pd_iterate(16)
+            s.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s.pd_iterate(iters)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1) / iters
+            stages = B.ps_profile_stages(s.h, 50)
+            out[name] = {"iters_per_s": 1000.0 / ms, "us_per_iter": 1000.0 * ms, "iterations_timed": iters,
+                         "kernels_per_iteration": B.ps_kernels_per_iteration(s.h),
+                         "stages_us_sum": 1000.0 * sum(stages.values()),
+                         "tuning": {k: v[0] for k, v in picks.items() if not k.startswith("reserved")}}
+    return out
+
+
 def np_comparison(wl_name: str = "img256_m50k", iterations: int = 0, reweights: int = -1) -> dict:
     """Section 5.2 protocol on synthetic data: the same schedule (NNLS start, reweighted cycles;
     the workload's own budget unless given) with and without the polarization constraint;
@@ -666,8 +707,9 @@ def run_own(args) -> None:
                        "constraint by the epigraph split) on the same measurements"}
         s.set_mode(B.PS_POLARIZED)
 
-    batched = served = np_cmp = hyper = None
+    batched = served = np_cmp = hyper = small = None
     if rank == 0 and world == 1 and not args.no_serve and not args.kernels_only:
+        small = small_configs()
         np_cmp = np_comparison()
         s.close()
         pool = draw_requests(args.batch, seed=wl.seed + 50)
@@ -730,6 +772,7 @@ def run_own(args) -> None:
             "served": served,
             "hyperspectral": hyper,
             "np_comparison": np_cmp,
+            "small_configs": small,
         }
         print(json.dumps(line), flush=True)
     if s is not None:

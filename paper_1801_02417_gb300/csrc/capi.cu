@@ -152,7 +152,8 @@ static void free_vis(Handle* h) {
 
 static void drop_graph(Handle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
-  h->graph = nullptr;
+  if (h->graph_multi) cudaGraphExecDestroy(h->graph_multi);
+  h->graph = h->graph_multi = nullptr;
   h->graph_mode = -1;
 }
 
@@ -332,19 +333,34 @@ static cudaError_t one_iteration(Handle* h, cudaEvent_t* ev = nullptr) {
   return cudaStreamWaitEvent(h->stream, h->ev_join, 0);
 }
 
-static ps_status build_graph(Handle* h) {
-  drop_graph(h);
+// Graph of `iters` iterations back to back (their launches in order on the handle's streams).
+static ps_status capture_iterations(Handle* h, int iters, cudaGraphExec_t* exec) {
   cudaGraph_t graph = nullptr;
   CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = one_iteration(h);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < iters && e == cudaSuccess; ++i) e = one_iteration(h);
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return fail(h, PS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(&h->graph, graph, cudaGraphInstantiateFlagUseNodePriority);
+  e = cudaGraphInstantiate(exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(h, PS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return PS_OK;
+}
+
+// The one-iteration graph, and the kGraphIters-iteration one that ps_pd_iterate launches for
+// runs of that many iterations: one launch instead of kGraphIters, which matters where an
+// iteration is a few microseconds of work (small images).
+static ps_status build_graph(Handle* h) {
+  drop_graph(h);
+  ps_status st = capture_iterations(h, 1, &h->graph);
+  if (st == PS_OK) st = capture_iterations(h, ps::kGraphIters, &h->graph_multi);
+  if (st != PS_OK) {
+    drop_graph(h);
+    return st;
+  }
   h->graph_mode = h->mode;
   return PS_OK;
 }
@@ -975,7 +991,9 @@ ps_status ps_pd_iterate(ps_handle* h, int32_t n_iter, ps_stats* stats) {
       ps_status st = build_graph(h);
       if (st != PS_OK) return st;
     }
-    for (int i = 0; i < n_iter; ++i) CK(h, cudaGraphLaunch(h->graph, h->stream));
+    int i = 0;
+    for (; i + ps::kGraphIters <= n_iter; i += ps::kGraphIters) CK(h, cudaGraphLaunch(h->graph_multi, h->stream));
+    for (; i < n_iter; ++i) CK(h, cudaGraphLaunch(h->graph, h->stream));
     h->iterations += n_iter;
   }
   return stats ? ps_compute_stats(h, 0.0, stats) : PS_OK;
@@ -1562,9 +1580,7 @@ static cudaError_t move_class_into_slabs(BatchClass& c, int64_t* bytes) {
     h->bytes -= moved;
     *bytes += moved;
     h->in_slab = true;
-    h->graph_mode = -1;   // the handle's own graph holds the old addresses
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
+    drop_graph(h);   // the handle's own graphs hold the old addresses
     ++h->version;
   }
   return cudaSuccess;
@@ -1619,9 +1635,7 @@ static void move_class_out_of_slabs(BatchClass& c, int64_t* bytes) {
     h->bytes += moved;
     *bytes -= moved;
     h->in_slab = false;
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-    h->graph_mode = -1;
+    drop_graph(h);
     ++h->version;
   }
   if (all_out) free_class_slabs(c);

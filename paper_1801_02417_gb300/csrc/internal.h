@@ -19,6 +19,7 @@ constexpr int kChunk = 1024;     // visibilities per reduction chunk
 constexpr int kGridItem = 512;   // visibilities per gridding work item
 constexpr int kBinChunk = 32;    // visibilities per same-cell accumulation chunk
 constexpr int kWarpBins = 64;    // l2 blocks up to which degridding keeps per-warp FP64 block sums
+constexpr int kGraphIters = 8;   // iterations per launch of the multi-iteration graph
 
 // Analysis / synthesis kernel modes.
 enum { SARA_DUAL = 0, SARA_APPLY = 1, SARA_REWEIGHT = 2 };
@@ -114,6 +115,7 @@ struct Handle {
 
   // CUDA graph of one iteration.
   cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_multi = nullptr;   // kGraphIters iterations back to back (same mode as graph)
   int graph_mode = -1;
   uint64_t version = 1;       // bumped when mode, state or measurements change (batch graphs rebuild)
 };
