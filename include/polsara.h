@@ -382,9 +382,9 @@ enum {
  * slot on the handle's data (reps launches each, CUDA events on the handle's
  * stream, after one untimed launch) and keep the fastest. The state of the
  * iteration is unchanged (the timed launches run the analysis dual update on scratch
- * coefficients, recompute Psi A of the current A in place, interpolate the current
- * spectrum into scratch and grid the current dual into the gridding accumulator, an
- * intermediate; phi^dagger B is kept). Uses (and on first use allocates) the handle's
+ * coefficients, recompute Psi A of the current A in place, run the degridding dual update
+ * on a scratch copy of the data dual and grid the current dual into the gridding
+ * accumulator, an intermediate; phi^dagger B is kept). Uses (and on first use allocates) the handle's
  * 36N operator scratch. choices (nullable) receives the
  * PS_TUNE_COUNT picks; ms (nullable) receives, per slot, the time of the pick in
  * milliseconds. Synchronises the stream. PS_ESTATE before measurements. */

@@ -1371,10 +1371,16 @@ ps_status ps_autotune(ps_handle* h, int32_t reps, int32_t* choices, double* ms) 
   // Synthesis: Psi A of the current coefficients, written where it already is.
   ps_status st = pick(PS_TUNE_SYNTHESIS, [&] { return ps::sara_synthesis(h, h->A, h->PsiA); });
   if (st != PS_OK) return st;
-  // Degridding: the spectrum of the current S interpolated into scratch.
+  // Degridding as the iteration runs it (the dual update of steps 7-8 with its block sums),
+  // from the spectrum of the current S, on a scratch copy of the dual: the candidates read and
+  // write the visibility rows as in the iteration, and the state's dual is untouched.
   if (h->M > 0) {
     CK(h, ps::nufft_forward_grid(h, h->S));
-    st = pick(PS_TUNE_DEGRID, [&] { return ps::nufft_degrid(h, ps::DEG_APPLY, h->vtmp); });
+    CK(h, cudaMemcpyAsync(h->vtmp, h->R, 4 * (size_t)h->M * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+    float2* const R_state = h->R;
+    h->R = h->vtmp;
+    st = pick(PS_TUNE_DEGRID, [&] { return ps::nufft_degrid(h, ps::DEG_DUAL, nullptr); });
+    h->R = R_state;
     if (st != PS_OK) return st;
     // Gridding: the current dual into the accumulator (an intermediate; phi^dagger B is kept).
     st = pick(PS_TUNE_GRID, [&] { return ps::nufft_grid(h, h->R, 1); });
