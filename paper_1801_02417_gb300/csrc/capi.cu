@@ -137,6 +137,8 @@ static void free_vis(Handle* h) {
   dfree(h, h->block_sum, (size_t)h->nblocks);
   dfree(h, h->items, (size_t)h->nitems);
   dfree(h, h->gchunks, (size_t)h->ngchunks);
+  dfree(h, h->items_g, (size_t)h->nitems_g);
+  dfree(h, h->gchunks_g, (size_t)h->ngchunks_g);
   dfree(h, h->vblk, M);
   dfree(h, h->wrow, 16 * M);
   const size_t Wd = h->g.Wd;
@@ -146,7 +148,7 @@ static void free_vis(Handle* h) {
   dfree(h, h->T2, (size_t)h->n * Wd);
   dfree(h, h->tw, (size_t)h->g.K);
   dfree(h, h->corr, (size_t)h->n);
-  h->M = h->nblocks = h->nitems = h->ngchunks = 0;
+  h->M = h->nblocks = h->nitems = h->ngchunks = h->nitems_g = h->ngchunks_g = 0;
   h->g = ps::GridGeom{};
 }
 
@@ -374,7 +376,7 @@ int64_t ps_estimate_bytes(int32_t n, int32_t levels, int64_t M) {
   if (n < 16 || n > 2048 || !is_pow2(n) || levels < 1 || (n % (1 << levels)) != 0 || M < 0) return 0;
   const int64_t N = (int64_t)n * n, K = 2 * (int64_t)n;
   const int64_t img = (28 + 72 + 16) * N * 4 + (8 * (int64_t)sweep_blocks_host((int)N) + 1024) * 8;
-  const int64_t vis = M * (3 * 32 + 16 + 4 + 64) + (M / ps::kChunk + 64) * 24;
+  const int64_t vis = M * (3 * 32 + 16 + 4 + 64) + (M / ps::kChunk + 64) * 24 + M / 2;   // + item and chunk lists
   const int64_t grid = 2 * (int64_t)n * K * 16 + 48 * K * K + K * 12 + (int64_t)n * 4;
   return img + vis + grid;
 }
@@ -719,15 +721,14 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
     part_psf[t] = acc;
   });
   h->psf_peak = std::accumulate(part_psf.begin(), part_psf.end(), 0.0);
-  // Work items (<= kGridItem rows of one tile) and same-cell chunks (<= kBinChunk rows).
-  std::vector<ps::GridItem> items;
-  std::vector<int32_t> gchunks;
-  {
+  // Work items (<= cap rows of one tile) and same-cell chunks (<= kBinChunk rows): kGridItem
+  // rows per degridding item, kGridItemG per gridding item.
+  auto make_items = [&](int cap, std::vector<ps::GridItem>& items, std::vector<int32_t>& gchunks) {
     int j0 = 0;
     while (j0 < M) {
       const int64_t tile = skey[j0] / (TS * TS);
       int j1 = j0;
-      while (j1 < M && j1 - j0 < ps::kGridItem && skey[j1] / (TS * TS) == tile) ++j1;
+      while (j1 < M && j1 - j0 < cap && skey[j1] / (TS * TS) == tile) ++j1;
       ps::GridItem it{};
       it.ty = (int32_t)(tile / g.tilesX);
       it.tx = (int32_t)(tile % g.tilesX);
@@ -747,11 +748,17 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
       items.push_back(it);
       j0 = j1;
     }
-  }
+  };
+  std::vector<ps::GridItem> items, items_g;
+  std::vector<int32_t> gchunks, gchunks_g;
+  make_items(ps::kGridItem, items, gchunks);
+  make_items(ps::kGridItemG, items_g, gchunks_g);
   h->M = M;
   h->nblocks = M > 0 ? nblocks : 0;
   h->nitems = (int)items.size();
   h->ngchunks = (int)gchunks.size();
+  h->nitems_g = (int)items_g.size();
+  h->ngchunks_g = (int)gchunks_g.size();
   if (M > 0) h->eps_host.assign(eps, eps + h->nblocks);
   else h->eps_host.clear();
 
@@ -763,7 +770,9 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
             dalloc(h, &h->cb, (size_t)h->nblocks) == cudaSuccess &&
             dalloc(h, &h->block_sum, (size_t)h->nblocks) == cudaSuccess &&
             dalloc(h, &h->items, items.size()) == cudaSuccess &&
-            dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess && dalloc(h, &h->vblk, (size_t)M) == cudaSuccess &&
+            dalloc(h, &h->gchunks, gchunks.size()) == cudaSuccess &&
+            dalloc(h, &h->items_g, items_g.size()) == cudaSuccess &&
+            dalloc(h, &h->gchunks_g, gchunks_g.size()) == cudaSuccess && dalloc(h, &h->vblk, (size_t)M) == cudaSuccess &&
             dalloc(h, &h->T1, (size_t)h->n * Wd) == cudaSuccess && dalloc(h, &h->G, Wd * Wd) == cudaSuccess &&
             dalloc(h, &h->Acc, 2 * Wd * Wd) == cudaSuccess && dalloc(h, &h->T2, (size_t)h->n * Wd) == cudaSuccess &&
             dalloc(h, &h->tw, (size_t)g.K) == cudaSuccess && dalloc(h, &h->corr, (size_t)h->n) == cudaSuccess &&
@@ -794,6 +803,10 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
     CK(h, cudaMemcpyAsync(h->eps, eps, h->nblocks * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->items, items.data(), items.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->gchunks, gchunks.data(), gchunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->items_g, items_g.data(), items_g.size() * sizeof(ps::GridItem), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaMemcpyAsync(h->gchunks_g, gchunks_g.data(), gchunks_g.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                          h->stream));
     CK(h, cudaMemcpyAsync(h->vblk, vblk.data(), vblk.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
     CK(h, ps::nufft_row_weights(h));
     // Measurements into sorted order.

@@ -16,7 +16,8 @@ constexpr int kDb = 8;           // Daubechies bases
 constexpr int kMaxTaps = 16;     // db8 filter length
 constexpr int kGridTile = 16;    // gridding tile side (cells)
 constexpr int kChunk = 1024;     // visibilities per reduction chunk
-constexpr int kGridItem = 512;   // visibilities per gridding work item
+constexpr int kGridItem = 512;   // visibilities per degridding work item
+constexpr int kGridItemG = 384;  // visibilities per gridding work item (smaller: 4 CTAs per SM)
 constexpr int kBinChunk = 32;    // visibilities per same-cell accumulation chunk
 constexpr int kWarpBins = 64;    // l2 blocks up to which degridding keeps per-warp FP64 block sums
 constexpr int kGraphIters = 8;   // iterations per launch of the multi-iteration graph
@@ -90,8 +91,11 @@ struct Handle {
   float *cb = nullptr;        // per block scale c_b (device)
   double *block_sum = nullptr;     // nblocks FP64 sums filled by the degridding kernel
   int nitems = 0, ngchunks = 0;
-  GridItem *items = nullptr;       // gridding work items
-  int32_t *gchunks = nullptr;      // packed (start, count, ly, lx) of same-cell chunks
+  GridItem *items = nullptr;       // degridding work items (<= kGridItem rows)
+  int32_t *gchunks = nullptr;      // packed (start, count, ly, lx) of their same-cell chunks
+  int nitems_g = 0, ngchunks_g = 0;
+  GridItem *items_g = nullptr;     // gridding work items (<= kGridItemG rows) and their chunks
+  int32_t *gchunks_g = nullptr;
   uint16_t *vblk = nullptr;        // l2 block of each stored row
   float *wrow = nullptr;           // W <= 8: kernel weights of each stored row, 8 y-taps (M x 8)
                                    // then 8 x-taps (M x 8), zero past W

@@ -496,7 +496,7 @@ __global__ void k_block_scale(const double* __restrict__ block_sum, const double
 
 // Gridding (adjoint of the interpolation), Alg. 1 step 3's phi^dagger.
 // Rows are stored sorted by tap-centre cell. One CTA owns a work item:
-// up to kGridItem visibilities whose centres lie in one kGridTile^2 tile.
+// up to kGridItemG visibilities whose centres lie in one kGridTile^2 tile.
 //  1. Each thread stages one visibility in shared memory: the conj(L)-mixed
 //     values x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL)
 //     scaled by c_b w_m (two float4), and its W x and W y kernel weights (planes
@@ -512,7 +512,7 @@ __global__ void k_block_scale(const double* __restrict__ block_sum, const double
 // Stride of the staged per-row weight planes: tap j of row v sits in bank (2 j + v) mod 32, so
 // the lanes of a warp (one row, or two rows v, v+1 in the half-warp form) reading their
 // cells' taps never share a bank.
-constexpr int kGridV = kGridItem + 2;
+constexpr int kGridV = kGridItemG + 2;
 
 // Work split of a same-cell chunk (one warp per chunk in every form):
 // FORM 0: lane l owns kernel cells l, l + 32, all 8 channels.
@@ -533,9 +533,9 @@ __host__ __device__ constexpr int grid_plane() {
   return (kGridTile + W - 1) * (kGridTile + W - 1) + 1;
 }
 
-// FORM 3 keeps 8 y-weights and 8 x-weights per row for kGridItem rows plus 8 spare
+// FORM 3 keeps 8 y-weights and 8 x-weights per row for kGridItemG rows plus 8 spare
 // rows (its last k-step of a chunk may read, and then discard, up to 7 rows past it).
-constexpr int kGridRows3 = kGridItem + 8;
+constexpr int kGridRows3 = kGridItemG + 8;
 // Floats of staged weights per work item (a multiple of 4: the tile planes after them stay 16-byte aligned).
 template <int W, int FORM>
 __host__ __device__ constexpr int grid_wts_floats() {
@@ -806,8 +806,8 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
   constexpr int NP = grid_plane<W>();
   __shared__ uint64_t wbar;                      // FORM 3: completion of the weight copies
   extern __shared__ float4 smg[];
-  float4* x4 = smg;                              // kGridItem x 2: mixed, scaled channels of each row
-  float* wts = reinterpret_cast<float*>(smg + 2 * kGridItem);   // weights (layout by FORM)
+  float4* x4 = smg;                              // kGridItemG x 2: mixed, scaled channels of each row
+  float* wts = reinterpret_cast<float*>(smg + 2 * kGridItemG);  // weights (layout by FORM)
   float* acc = wts + grid_wts_floats<W, FORM>(); // 8 planes of NP floats
   const GridItem it = items[blockIdx.x];
   for (int i = threadIdx.x; i < 8 * NP; i += blockDim.x) acc[i] = 0.f;
@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
   }
   const float4* v4 = reinterpret_cast<const float4*>(vin);
   // Every global load of this thread's rows is issued before the first is used.
-  constexpr int RPT = (kGridItem + kGridThreads - 1) / kGridThreads;   // rows per thread
+  constexpr int RPT = (kGridItemG + kGridThreads - 1) / kGridThreads;   // rows per thread
   float4 r[RPT], b0[RPT], b1[RPT];
   int blk[RPT];
 #pragma unroll
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
     // Spare rows after the item: finite (zero) operands for the last k-step of its last chunk.
     const int j = nv + threadIdx.x;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j < kGridItem) x4[2 * j] = x4[2 * j + 1] = z;
+    if (j < kGridItemG) x4[2 * j] = x4[2 * j + 1] = z;
     float4* yb = reinterpret_cast<float4*>(wts) + 2 * j;
     float4* xb = reinterpret_cast<float4*>(wts + 8 * kGridRows3) + 2 * j;
     yb[0] = yb[1] = xb[0] = xb[1] = z;
@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(
 
 template <int W, int FORM>
 static constexpr size_t grid_smem() {
-  return (size_t)2 * kGridItem * sizeof(float4) +
+  return (size_t)2 * kGridItemG * sizeof(float4) +
          (size_t)(grid_wts_floats<W, FORM>() + 8 * grid_plane<W>()) * sizeof(float);
 }
 
@@ -1119,8 +1119,8 @@ cudaError_t nufft_row_weights(Handle* h) {
 template <int W, int FORM>
 static void launch_grid_form(Handle* h, const float2* in, int use_scale) {
   const GridGeom& g = h->g;
-  k_grid<W, FORM><<<h->nitems, kGridThreads, grid_smem<W, FORM>(), h->stream>>>(
-      h->items, h->gchunks, h->vblk, h->rec, in, h->cb, use_scale, g.Wd, g.full, g.K, g.beta, h->wrow, h->M, h->Acc,
+  k_grid<W, FORM><<<h->nitems_g, kGridThreads, grid_smem<W, FORM>(), h->stream>>>(
+      h->items_g, h->gchunks_g, h->vblk, h->rec, in, h->cb, use_scale, g.Wd, g.full, g.K, g.beta, h->wrow, h->M, h->Acc,
       h->dev_flags);
 }
 
@@ -1140,7 +1140,7 @@ static void launch_grid(Handle* h, const float2* in, int use_scale) {
 cudaError_t nufft_grid(Handle* h, const float2* in, int use_scale) {
   const GridGeom& g = h->g;
   cudaError_t e = cudaMemsetAsync(h->Acc, 0, (size_t)g.Wd * g.Wd * 2 * sizeof(float4), h->stream);
-  if (e != cudaSuccess || h->nitems == 0) return e;
+  if (e != cudaSuccess || h->nitems_g == 0) return e;
   switch (g.W) {
     case 5: launch_grid<5>(h, in, use_scale); break;
     case 9: launch_grid<9>(h, in, use_scale); break;
