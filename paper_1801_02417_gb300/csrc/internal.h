@@ -16,8 +16,9 @@ constexpr int kDb = 8;           // Daubechies bases
 constexpr int kMaxTaps = 16;     // db8 filter length
 constexpr int kGridTile = 16;    // gridding tile side (cells)
 constexpr int kChunk = 1024;     // visibilities per reduction chunk
-constexpr int kGridItem = 512;   // visibilities per degridding work item
+constexpr int kGridItem = 768;   // visibilities per degridding work item
 constexpr int kGridItemG = 384;  // visibilities per gridding work item (smaller: 4 CTAs per SM)
+static_assert(kGridItem <= 1024 && kGridItemG <= 1024, "a chunk's start is a 10-bit offset in its item");
 constexpr int kBinChunk = 32;    // visibilities per same-cell accumulation chunk
 constexpr int kWarpBins = 64;    // l2 blocks up to which degridding keeps per-warp FP64 block sums
 constexpr int kGraphIters = 8;   // iterations per launch of the multi-iteration graph
