@@ -329,6 +329,20 @@ ps_status ps_set_visibilities(ps_handle* h, const float* vis, int32_t device_ptr
  * Synchronises the handle's stream. */
 ps_status ps_get_rel_change(ps_handle* h, double* out4);
 
+/* The same relative change (Eq. stop_crit) without stalling the device, for solve loops that
+ * test the stopping rule after every iteration: ps_rel_change_request enqueues on the handle's
+ * stream the FP64 sums of the last iteration's partials and their copy (with the device error
+ * flags) into host memory the library owns, and returns at once; ps_rel_change_result waits
+ * for that copy only, not for work queued after it, and writes the four values as
+ * ps_get_rel_change would have at the request (PS_ENONFINITE, PS_ETIMEOUT likewise). A loop
+ * that requests after iteration k, launches iteration k + 1 and then reads the result keeps
+ * the GPU busy while the host decides, and stops one iteration late. One request at a time:
+ * a second request replaces the first, and a synchronous read (ps_get_rel_change,
+ * ps_compute_stats, ps_pd_iterate with statistics) consumes it. ps_rel_change_result without a
+ * pending request returns PS_ESTATE. */
+ps_status ps_rel_change_request(ps_handle* h);
+ps_status ps_rel_change_result(ps_handle* h, double* out4);
+
 /* max_j |[Psi^dagger S]_j| over all four maps (FP32 values, exact maximum): the scale
  * from which reweighting schedules pick delta (Eq. weights). Synchronises. */
 ps_status ps_max_abs_analysis(ps_handle* h, double* out);

@@ -86,6 +86,8 @@ _SIGS = {
     "ps_fp32_peak": (_I32, [_I32, ctypes.POINTER(_F64)]),
     "ps_set_visibilities": (_I32, [_H, _P, _I32]),
     "ps_get_rel_change": (_I32, [_H, _P]),
+    "ps_rel_change_request": (_I32, [_H]),
+    "ps_rel_change_result": (_I32, [_H, _P]),
     "ps_max_abs_analysis": (_I32, [_H, ctypes.POINTER(_F64)]),
     "ps_batch_create": (_I32, [_P, _I32, _P, ctypes.POINTER(_H)]),
     "ps_batch_iterate": (_I32, [_H, _I32]),
@@ -357,6 +359,16 @@ def ps_set_visibilities(h, vis) -> None:
 def ps_get_rel_change(h) -> np.ndarray:
     out = np.zeros(4, dtype=np.float64)
     _check(h, lib().ps_get_rel_change(h, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def ps_rel_change_request(h) -> None:
+    _check(h, lib().ps_rel_change_request(h))
+
+
+def ps_rel_change_result(h) -> np.ndarray:
+    out = np.zeros(4, dtype=np.float64)
+    _check(h, lib().ps_rel_change_result(h, ctypes.c_void_p(out.ctypes.data)))
     return out
 
 

@@ -444,7 +444,8 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->relc_ev, cudaEventDisableTiming) != cudaSuccess) {
     h->err = "ps_create: auxiliary stream/events";
     return bail(PS_ECUDA);
   }
@@ -474,7 +475,9 @@ ps_status ps_create(const ps_config* cfg, void* cuda_stream, ps_handle** out) {
             dalloc(h, &h->A, 36 * N) == cudaSuccess && dalloc(h, &h->T, 36 * N) == cudaSuccess &&
             dalloc(h, &h->approx, 16 * N) == cudaSuccess && dalloc(h, &h->red, (size_t)h->red_cap) == cudaSuccess &&
             dalloc(h, &h->dev_flags, 4) == cudaSuccess &&
-            cudaMallocHost((void**)&h->red_host, 1024 * sizeof(double)) == cudaSuccess;
+            cudaMallocHost((void**)&h->red_host, 1024 * sizeof(double)) == cudaSuccess &&
+            cudaHostAlloc((void**)&h->relc_host, 16 * sizeof(double), cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer((void**)&h->relc_dev, h->relc_host, 0) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     h->err = "ps_create: device allocation failed";
@@ -520,6 +523,8 @@ void ps_destroy(ps_handle* h) {
   dfree(h, h->red, (size_t)h->red_cap);
   dfree(h, h->dev_flags, 4);
   if (h->red_host) cudaFreeHost(h->red_host);
+  if (h->relc_host) cudaFreeHost(h->relc_host);
+  if (h->relc_ev) cudaEventDestroy(h->relc_ev);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -1114,15 +1119,27 @@ ps_status ps_get_params(ps_handle* h, double* tau, double* rho1, double* rho2, d
 
 // Relative change per map (Eq. stop_crit) from the FP64 partials k_primal wrote: 0/0 = 0
 // (a map that stayed zero), x/0 = +inf. Non-finite sums mean a NaN or infinity in S.
-static ps_status rel_change_from_partials(Handle* h, const std::vector<double>& part, double out4[4]) {
-  const int nb = sweep_blocks_host(h->N);
+// Enqueues on the handle's stream: one small kernel that sums the last iteration's
+// relative-change partials (FP64) and writes the 8 sums and the device flags straight into the
+// mapped host buffer relc_host (no copy), and the event that marks them written.
+static ps_status relc_enqueue(Handle* h) {
+  CK(h, ps::relc_sums(h, sweep_blocks_host(h->N), h->relc_dev));
+  CK(h, cudaEventRecord(h->relc_ev, h->stream));
+  h->relc_pending = true;
+  return PS_OK;
+}
+
+// The relative change from the landed sums (and the flags copied with them).
+static ps_status relc_finish(Handle* h, double* out4) {
+  h->relc_pending = false;
+  const int* f = reinterpret_cast<const int*>(h->relc_host + 8);
+  if (f[0]) {
+    CK(h, cudaMemsetAsync(h->dev_flags, 0, 4 * sizeof(int), h->stream));
+    return fail(h, PS_ETIMEOUT, "a bounded device wait (bulk-copy barrier) gave up; results of that launch are invalid");
+  }
   bool finite = true;
   for (int c = 0; c < 4; ++c) {
-    double num = 0, den = 0;
-    for (int b = 0; b < nb; ++b) {
-      num += part[8 * (size_t)b + c];
-      den += part[8 * (size_t)b + 4 + c];
-    }
+    const double num = h->relc_host[c], den = h->relc_host[4 + c];
     finite = finite && std::isfinite(num) && std::isfinite(den);
     out4[c] = den > 0 ? std::sqrt(num / den) : (num > 0 ? INFINITY : 0.0);
   }
@@ -1141,15 +1158,14 @@ ps_status ps_compute_stats(ps_handle* h, double zeta_sigma, ps_stats* out) {
   if (!(zeta_sigma > 0)) zeta_sigma = h->cfg.zeta_sigma;
   const size_t N = h->N;
   double* dres = h->red + (size_t)h->red_cap - 600;
-  // Relative change of the last iteration (partials written by k_primal).
-  const int nb = sweep_blocks_host((int)N);
-  std::vector<double> part(8 * (size_t)nb);
-  CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(h, cudaStreamSynchronize(h->stream));
+  // Relative change of the last iteration (from the partials written by k_primal).
   out->stop_flags = 0;
   out->converged = 0;
   {
-    ps_status st = rel_change_from_partials(h, part, out->rel_change);
+    ps_status st = relc_enqueue(h);
+    if (st != PS_OK) return st;
+    CK(h, cudaStreamSynchronize(h->stream));
+    st = relc_finish(h, out->rel_change);
     if (st != PS_OK) return st;
   }
   // Residual Y - phi(S) per block, and the residual image.
@@ -1448,13 +1464,22 @@ ps_status ps_set_visibilities(ps_handle* h, const float* vis, int32_t device_ptr
 
 ps_status ps_get_rel_change(ps_handle* h, double* out4) {
   if (!h || !out4) return h ? fail(h, PS_EINVAL, "get_rel_change: null output") : PS_EINVAL;
-  const int nb = sweep_blocks_host(h->N);
-  std::vector<double> part(8 * (size_t)nb);
-  CK(h, cudaMemcpyAsync(part.data(), h->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(h, cudaStreamSynchronize(h->stream));
-  ps_status st = check_flags(h);
+  ps_status st = relc_enqueue(h);
   if (st != PS_OK) return st;
-  return rel_change_from_partials(h, part, out4);
+  CK(h, cudaStreamSynchronize(h->stream));
+  return relc_finish(h, out4);
+}
+
+ps_status ps_rel_change_request(ps_handle* h) {
+  if (!h) return PS_EINVAL;
+  return relc_enqueue(h);
+}
+
+ps_status ps_rel_change_result(ps_handle* h, double* out4) {
+  if (!h || !out4) return h ? fail(h, PS_EINVAL, "rel_change_result: null output") : PS_EINVAL;
+  if (!h->relc_pending) return fail(h, PS_ESTATE, "rel_change_result: no ps_rel_change_request pending");
+  CK(h, cudaEventSynchronize(h->relc_ev));
+  return relc_finish(h, out4);
 }
 
 ps_status ps_max_abs_analysis(ps_handle* h, double* out) {

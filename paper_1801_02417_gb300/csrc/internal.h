@@ -79,6 +79,10 @@ struct Handle {
   double *red = nullptr;      // reduction partials
   int red_cap = 0;
   double *red_host = nullptr; // pinned
+  double *relc_host = nullptr; // pinned, mapped: relative-change sums (8) and the device flags of the last request
+  double *relc_dev = nullptr;  // the device's address of relc_host
+  cudaEvent_t relc_ev = nullptr;
+  bool relc_pending = false;
   int *dev_flags = nullptr;   // device error flags: [0] a bounded wait gave up
 
   // Visibility-domain state, rows stored in tap-centre-cell order (tile-major).
@@ -165,6 +169,7 @@ cudaError_t primal_sweep(Handle* h);
 cudaError_t dirac_apply(Handle* h, const float* X, float* coef, float* thr, int mode,
                         float scale, float gamma, float delta);
 cudaError_t reduce_dot(Handle* h, const float* a, const float* b, size_t len, double* dev_out);
+cudaError_t relc_sums(Handle* h, int nb, double* out);   // 8 column sums of k_primal's partials + the flags
 cudaError_t violation_count(Handle* h, const float* S, double zeta, double* dev_out);
 cudaError_t weighted_l1(Handle* h, const float* coef, const float* thr, double* dev_out);
 cudaError_t max_abs(Handle* h, const float* c, size_t len, double* dev_out);

@@ -271,6 +271,35 @@ __global__ void k_sum_partials(const double* __restrict__ part, int np, double* 
   }
 }
 
+// Column sums of the per-CTA relative-change partials that k_primal writes (8 per CTA: the
+// squared changes of the four maps, then their squared norms), in FP64 and a fixed order,
+// written with the device error flags (as ints after the 8 sums) straight into `out`, which
+// may be mapped host memory.
+__global__ void k_relc_sums(const double* __restrict__ part, int nb, const int* __restrict__ flags,
+                            double* __restrict__ out) {
+  __shared__ double sh[8][8];   // [warp][column]
+  const int c = threadIdx.x & 7;
+  double s = 0.0;
+  for (int b = threadIdx.x >> 3; b < nb; b += blockDim.x >> 3) s += part[8 * (size_t)b + c];
+  s += __shfl_xor_sync(0xffffffffu, s, 8);    // lanes c, c + 8, c + 16, c + 24 hold column c
+  s += __shfl_xor_sync(0xffffffffu, s, 16);
+  if ((threadIdx.x & 31) < 8) sh[threadIdx.x >> 5][c] = s;
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][threadIdx.x];
+    out[threadIdx.x] = t;
+  } else if (threadIdx.x < 12) {
+    reinterpret_cast<int*>(out + 8)[threadIdx.x - 8] = flags[threadIdx.x - 8];
+  }
+  __threadfence_system();
+}
+
+cudaError_t relc_sums(Handle* h, int nb, double* out) {
+  k_relc_sums<<<1, 256, 0, h->stream>>>(h->red, nb, h->dev_flags, out);
+  return cudaGetLastError();
+}
+
 static constexpr int kRedBlocks = 256;
 
 cudaError_t reduce_dot(Handle* h, const float* a, const float* b, size_t len, double* dev_out) {

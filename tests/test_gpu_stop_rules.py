@@ -227,3 +227,48 @@ def test_multi_iteration_graph_matches_single_launches():
         ga, gb = a.get_state(), b.get_state()
     for k in "SZABCD":
         assert rel_err(ga[k], gb[k]) <= (6e-5 if k == "A" else 1e-5), k
+
+
+def test_rel_change_request_reads_the_iteration_it_follows():
+    """ps_rel_change_request after iteration k, then iteration k + 1, then ps_rel_change_result:
+    the relative change of iteration k, as a second handle in the same state reads it with
+    ps_get_rel_change right after its iteration k (the two handles differ only in the order of
+    the FP32 gridding atomics); after the last iteration the asynchronous and the synchronous
+    read agree bit for bit. Without a pending request the result call is PS_ESTATE, and a NaN
+    in the state comes back from the result as PS_ENONFINITE."""
+    n, levels, M = 32, 3, 900
+    pb = make_problem(n, M, levels, 2, seed=50)
+    st32 = {k: (v.astype(np.complex64) if k == "B" else v.astype(np.float32))
+            for k, v in inputs.random_state(n, M, 51, 0.05).items()}
+    a, b = _handle(pb, n, levels), _handle(pb, n, levels)
+    with a, b:
+        for s in (a, b):
+            s.set_sara_weights(None, 0.02)
+            s.set_state(st32)
+        with pytest.raises(B.PolsaraError) as e:
+            B.ps_rel_change_result(a.h)
+        assert e.value.status == B.PS_ESTATE
+        got = []
+        a.pd_iterate(1)
+        B.ps_rel_change_request(a.h)
+        for _ in range(4):
+            a.pd_iterate(1)
+            got.append(B.ps_rel_change_result(a.h))
+            B.ps_rel_change_request(a.h)
+        got.append(B.ps_rel_change_result(a.h))
+        assert np.array_equal(got[-1], B.ps_get_rel_change(a.h))
+        ref = []
+        for _ in range(5):
+            b.pd_iterate(1)
+            ref.append(B.ps_get_rel_change(b.h))
+        for k in range(5):
+            assert np.all(np.isfinite(got[k])) and np.all(got[k] > 0), k
+            assert np.allclose(got[k], ref[k], rtol=1e-4, atol=0.0), (k, got[k], ref[k])
+        x = np.zeros((4, n, n), np.float32)
+        x[2, 3, 4] = np.nan
+        a.set_state({"S": x})
+        a.pd_iterate(1)
+        B.ps_rel_change_request(a.h)
+        with pytest.raises(B.PolsaraError) as e:
+            B.ps_rel_change_result(a.h)
+        assert e.value.status == B.PS_ENONFINITE
