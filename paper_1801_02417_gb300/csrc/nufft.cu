@@ -1045,7 +1045,7 @@ cudaError_t nufft_forward_grid(Handle* h, const float* X) {
   const GridGeom& g = h->g;
   const size_t sm1 = fft_smem_bytes(g.K, 1);
   k_fwd_rows<<<h->n, 256, sm1, h->stream>>>(X, h->n, h->N, h->corr, h->tw, g.K, g.logK, h->T1, g.Wd, g.off, g.full);
-  k_fwd_cols<<<g.Wd, 256, sm1, h->stream>>>(h->T1, h->n, h->tw, g.K, g.logK, h->G, g.Wd, g.off, g.full);
+  k_fwd_cols<<<g.Wd, 512, sm1, h->stream>>>(h->T1, h->n, h->tw, g.K, g.logK, h->G, g.Wd, g.off, g.full);
   return cudaGetLastError();
 }
 
@@ -1153,7 +1153,7 @@ cudaError_t nufft_adjoint_image(Handle* h, float* out) {
   const GridGeom& g = h->g;
   const size_t sm2 = fft_smem_bytes(g.K, 2), sm1 = fft_smem_bytes(g.K, 1);
   const int ncols = g.full ? (g.K / 2 + 1) : (g.R + 1);
-  k_adj_cols<<<ncols, 256, sm2, h->stream>>>(h->Acc, h->n, h->tw, g.K, g.logK, h->T2, g.Wd, g.off, g.full);
+  k_adj_cols<<<ncols, 512, sm2, h->stream>>>(h->Acc, h->n, h->tw, g.K, g.logK, h->T2, g.Wd, g.off, g.full);
   k_adj_rows<<<h->n, 256, sm1, h->stream>>>(h->T2, h->n, h->N, h->corr, h->tw, g.K, g.logK, g.Wd, g.off, g.full, out);
   return cudaGetLastError();
 }
