@@ -685,20 +685,28 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   g.tilesX = (g.Wd + ps::kGridTile - 1) / ps::kGridTile;
   auto gi = [&](int k) { return g.full ? (k & (g.K - 1)) : k + g.off; };
 
-  // Storage order: rows sorted by gridding tile, then tap-centre cell (row-major in the
-  // tile), rows of one cell in the caller's order: two stable counting-sort passes
-  // (cell within the tile, then tile).
-  const int TS = ps::kGridTile;
+  // Storage order: rows sorted by degridding tile (TS x TS cells), then by gridding tile
+  // within it (TG x TG), then by tap-centre cell (row-major in the gridding tile), rows of
+  // one cell in the caller's order: three stable counting-sort passes, least significant
+  // first. The rows of every degridding tile, of every gridding tile and of every cell are
+  // then contiguous.
+  const int TS = ps::kGridTile, TG = ps::kGridTileG, NS = TS / TG;
   auto tile_of = [&](int32_t m) { return (int64_t)(gi(cy[m]) / TS) * g.tilesX + gi(cx[m]) / TS; };
-  auto cell_of = [&](int32_t m) { return (int64_t)((gi(cy[m]) % TS) * TS + gi(cx[m]) % TS); };
+  auto sub_of = [&](int32_t m) { return (int64_t)(((gi(cy[m]) % TS) / TG) * NS + (gi(cx[m]) % TS) / TG); };
+  auto cell_of = [&](int32_t m) { return (int64_t)((gi(cy[m]) % TG) * TG + gi(cx[m]) % TG); };
   std::vector<int32_t> perm(M), tmp(M);
   std::iota(tmp.begin(), tmp.end(), 0);
-  counting_sort(tmp, perm, (int64_t)TS * TS, parts, cell_of);
+  counting_sort(tmp, perm, (int64_t)TG * TG, parts, cell_of);
+  tmp.swap(perm);
+  counting_sort(tmp, perm, (int64_t)NS * NS, parts, sub_of);
   tmp.swap(perm);
   counting_sort(tmp, perm, (int64_t)g.tilesX * g.tilesX, parts, tile_of);
-  std::vector<int64_t> skey(M);   // sorted (tile, cell) keys
+  std::vector<int32_t> sgy(M), sgx(M);   // grid cell of each row, in storage order
   parallel_parts(M, parts, [&](int, int64_t b, int64_t e) {
-    for (int64_t i = b; i < e; ++i) skey[i] = tile_of(perm[i]) * TS * TS + cell_of(perm[i]);
+    for (int64_t i = b; i < e; ++i) {
+      sgy[i] = gi(cy[perm[i]]);
+      sgx[i] = gi(cx[perm[i]]);
+    }
   });
   if (M > 0) h->offsets_host.assign(block_offsets, block_offsets + nblocks + 1);
   else h->offsets_host.assign(1, 0);
@@ -726,26 +734,26 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
     part_psf[t] = acc;
   });
   h->psf_peak = std::accumulate(part_psf.begin(), part_psf.end(), 0.0);
-  // Work items (<= cap rows of one tile) and same-cell chunks (<= kBinChunk rows): kGridItem
-  // rows per degridding item, kGridItemG per gridding item.
-  auto make_items = [&](int cap, std::vector<ps::GridItem>& items, std::vector<int32_t>& gchunks) {
+  // Work items (<= cap rows of one tile of side tsz) and same-cell chunks (<= kBinChunk
+  // rows): kGridItem rows of a TS tile per degridding item, kGridItemG rows of a TG tile per
+  // gridding item; a chunk holds its cell's position in the item's tile.
+  auto make_items = [&](int cap, int tsz, std::vector<ps::GridItem>& items, std::vector<int32_t>& gchunks) {
     int j0 = 0;
     while (j0 < M) {
-      const int64_t tile = skey[j0] / (TS * TS);
+      const int ty = sgy[j0] / tsz, tx = sgx[j0] / tsz;
       int j1 = j0;
-      while (j1 < M && j1 - j0 < cap && skey[j1] / (TS * TS) == tile) ++j1;
+      while (j1 < M && j1 - j0 < cap && sgy[j1] / tsz == ty && sgx[j1] / tsz == tx) ++j1;
       ps::GridItem it{};
-      it.ty = (int32_t)(tile / g.tilesX);
-      it.tx = (int32_t)(tile % g.tilesX);
+      it.ty = ty;
+      it.tx = tx;
       it.vstart = j0;
       it.vend = j1;
       it.cstart = (int32_t)gchunks.size();
       int c0 = j0;
       while (c0 < j1) {
-        const int64_t cell = skey[c0];
         int c1 = c0;
-        while (c1 < j1 && c1 - c0 < ps::kBinChunk && skey[c1] == cell) ++c1;
-        const int ly = (int)(cell % (TS * TS)) / TS, lx = (int)(cell % TS);
+        while (c1 < j1 && c1 - c0 < ps::kBinChunk && sgy[c1] == sgy[c0] && sgx[c1] == sgx[c0]) ++c1;
+        const int ly = sgy[c0] - ty * tsz, lx = sgx[c0] - tx * tsz;
         gchunks.push_back((c0 - j0) | ((c1 - c0) << 10) | (ly << 16) | (lx << 24));
         c0 = c1;
       }
@@ -756,8 +764,8 @@ ps_status ps_set_measurements(ps_handle* h, int64_t M64, const double* uv, const
   };
   std::vector<ps::GridItem> items, items_g;
   std::vector<int32_t> gchunks, gchunks_g;
-  make_items(ps::kGridItem, items, gchunks);
-  make_items(ps::kGridItemG, items_g, gchunks_g);
+  make_items(ps::kGridItem, TS, items, gchunks);
+  make_items(ps::kGridItemG, TG, items_g, gchunks_g);
   h->M = M;
   h->nblocks = M > 0 ? nblocks : 0;
   h->nitems = (int)items.size();

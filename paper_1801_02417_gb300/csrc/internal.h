@@ -14,7 +14,9 @@ namespace ps {
 constexpr int kBases = 9;        // Dirac + db1..db8
 constexpr int kDb = 8;           // Daubechies bases
 constexpr int kMaxTaps = 16;     // db8 filter length
-constexpr int kGridTile = 16;    // gridding tile side (cells)
+constexpr int kGridTile = 16;    // degridding tile side (cells)
+constexpr int kGridTileG = 8;    // gridding tile side (cells): a quarter of a degridding tile
+static_assert(kGridTile % kGridTileG == 0, "gridding tiles subdivide degridding tiles");
 constexpr int kChunk = 1024;     // visibilities per reduction chunk
 constexpr int kGridItem = 768;   // visibilities per degridding work item
 constexpr int kGridItemG = 384;  // visibilities per gridding work item (smaller: 4 CTAs per SM)

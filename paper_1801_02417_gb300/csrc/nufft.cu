@@ -496,7 +496,7 @@ __global__ void k_block_scale(const double* __restrict__ block_sum, const double
 
 // Gridding (adjoint of the interpolation), Alg. 1 step 3's phi^dagger.
 // Rows are stored sorted by tap-centre cell. One CTA owns a work item:
-// up to kGridItemG visibilities whose centres lie in one kGridTile^2 tile.
+// up to kGridItemG visibilities whose centres lie in one kGridTileG^2 tile.
 //  1. Each thread stages one visibility in shared memory: the conj(L)-mixed
 //     values x_I = RR + LL, x_Q = RR - LL, x_U = RL + LR, x_V = i (LR - RL)
 //     scaled by c_b w_m (two float4), and its W x and W y kernel weights (planes
@@ -526,11 +526,11 @@ constexpr int kGridV = kGridItemG + 2;
 // FORM 3 (W <= 8): the chunk's block as a product of two small matrices on the tensor
 //   cores (mma.m16n8k8, TF32 with hi/lo operand splitting for FP32 accuracy); lanes load
 //   distinct words of the rows instead of broadcasts.
-// Stride of the 8 channel planes of a gridding tile: its (kGridTile + W - 1)^2 cells plus
+// Stride of the 8 channel planes of a gridding tile: its (kGridTileG + W - 1)^2 cells plus
 // one, odd modulo 32, so lanes adding to the same cell of different planes spread over banks.
 template <int W>
 __host__ __device__ constexpr int grid_plane() {
-  return (kGridTile + W - 1) * (kGridTile + W - 1) + 1;
+  return (kGridTileG + W - 1) * (kGridTileG + W - 1) + 1;
 }
 
 // FORM 3 keeps 8 y-weights and 8 x-weights per row for kGridItemG rows plus 8 spare
@@ -595,7 +595,7 @@ __device__ __forceinline__ void grid_chunks(const int32_t* __restrict__ chunks, 
                                             const float* __restrict__ wts, float* __restrict__ acc) {
   const float* wxs = wts;
   const float* wys = wts + W * kGridV;
-  constexpr int TS = kGridTile;
+  constexpr int TS = kGridTileG;
   constexpr int SS = TS + W - 1;
   constexpr int NP = grid_plane<W>();
   constexpr bool HALF = FORM == 1;
@@ -773,7 +773,7 @@ __device__ __forceinline__ void grid_chunks(const int32_t* __restrict__ chunks, 
 template <int W>
 __device__ __forceinline__ void grid_flush(const float* __restrict__ acc, int ty, int tx, int Wd, int full, int K,
                                            float4* __restrict__ Acc) {
-  constexpr int TS = kGridTile;
+  constexpr int TS = kGridTileG;
   constexpr int SS = TS + W - 1;
   constexpr int NC = SS * SS;
   constexpr int NP = grid_plane<W>();
