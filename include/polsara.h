@@ -388,7 +388,9 @@ enum {
                                the 8 bases, each basis' staged A and gamma W in flight during the previous
                                basis (levels >= 2 as 0),
                              3 as 2 with one CTA per (tile, 4 bases, map),
-                             4 as 3 with 512 threads per CTA (two columns per thread) */
+                             4 as 3 with 512 threads per CTA (two columns per thread),
+                             5 as 3 with one staging set, refilled for the next basis during its
+                               row pass (3 CTAs/SM) */
   PS_TUNE_COUNT = 4
 };
 

@@ -1345,7 +1345,7 @@ ps_status ps_profile_stages(ps_handle* h, int32_t n_iter, double* stage_ms) {
 
 // ---------------------------------------------------------------------------
 // Autotuner: candidates per PS_TUNE_* slot, each timed on the handle's own data.
-static const int kTuneCandidates[PS_TUNE_COUNT] = {3, 3, 5, 5};
+static const int kTuneCandidates[PS_TUNE_COUNT] = {3, 3, 5, 6};
 
 // Mean milliseconds of `reps` launches of f after one untimed launch.
 extern "C++" {

@@ -593,13 +593,17 @@ __device__ __forceinline__ void ana_cols2(const float* __restrict__ lo_s, const 
 // Level-1 analysis with the input tile shared by NB bases: one CTA per (tile, group of NB
 // bases, map). The 2 TO + 14 rows the db8 filter needs cover every shorter filter (same
 // origin), so the map's tile is copied once and each basis filters it from shared memory.
-// The staged A and gamma W rows of basis i + 1 (dual mode) are copied into the second of
-// two staging sets while basis i is filtered.
+// NSET = 2: the staged A and gamma W rows of basis i + 1 (dual mode) are copied into the
+// second of two staging sets while basis i is filtered (2 CTAs/SM). NSET = 1: one staging
+// set, refilled for basis i + 1 once basis i's columns have read it, so the copy overlaps the
+// next basis' row pass; the smaller footprint fits 3 CTAs/SM (256 threads).
 constexpr int kAnaMFloats = kAnaPre + 4 * kStage;
-static size_t multi_analysis_smem() { return (size_t)kAnaMFloats * sizeof(float) + 32; }
+static size_t multi_analysis_smem(int nset = 2) {
+  return (size_t)(kAnaPre + 2 * nset * kStage) * sizeof(float) + 32;
+}
 
-template <int NB, int THREADS>
-__global__ void __launch_bounds__(THREADS, 2) k_ana_l1m(const float* __restrict__ X, int n, int last,
+template <int NB, int THREADS, int NSET = 2>
+__global__ void __launch_bounds__(THREADS, NSET == 1 ? 3 : 2) k_ana_l1m(const float* __restrict__ X, int n, int last,
                                                     float* __restrict__ coef, float* __restrict__ thr,
                                                     float* __restrict__ approx_out, int mode, float scale,
                                                     float gamma, float delta, int* err,
@@ -608,8 +612,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_ana_l1m(const float* __restrict_
   float* in_s = reinterpret_cast<float*>(smm);
   float* lo_s = in_s + kA2In;
   float* hi_s = lo_s + kRSmax * kPlo;
-  float* st = in_s + kAnaPre;                                       // set s: A at st + 2 s kStage, gamma W after it
-  uint64_t* bar = reinterpret_cast<uint64_t*>(st + 4 * kStage);    // [0] input tile, [1 + s] stage set s
+  float* st = in_s + kAnaPre;                                          // set s: A at st + 2 s kStage, gamma W after it
+  uint64_t* bar = reinterpret_cast<uint64_t*>(st + 2 * NSET * kStage);    // [0] input tile, [1 + s] stage set s
   const int map = blockIdx.z, b0 = blockIdx.y * NB;
   const int hm = n >> 1, tilesx = hm / kTO;
   const int oy0 = (blockIdx.x / tilesx) * kTO, ox0 = (blockIdx.x % tilesx) * kTO;
@@ -619,7 +623,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_ana_l1m(const float* __restrict_
   auto set_a = [&](int s) { return st + 2 * s * kStage; };
   auto set_t = [&](int s) { return st + (2 * s + 1) * kStage; };
   if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) mbar_init(&bar[q], 1);
+    for (int q = 0; q < 1 + NSET; ++q) mbar_init(&bar[q], 1);
   __syncthreads();
   ana_issue_input_t(tm, map * n, X + (size_t)map * n * n, n, oy0, ox0, kRSmax, in_s, &bar[0]);
   if (staged) stage_epilogue_t(tm, coef, thr, plane(b0), prow(b0), n, hm, oy0, ox0, set_a(0), set_t(0), &bar[1]);
@@ -633,21 +637,24 @@ __global__ void __launch_bounds__(THREADS, 2) k_ana_l1m(const float* __restrict_
     return;   // the CTA's tiles are left unchanged (the host reports PS_ETIMEOUT)
   }
   for (int i = 0; i < NB; ++i) {
-    const int bi = b0 + i, s = i & 1;
-    // Set s ^ 1 was last read by basis i - 1, which ended at a barrier: refill it for basis i + 1.
-    if (staged && i + 1 < NB)
+    const int bi = b0 + i, s = NSET == 2 ? (i & 1) : 0;
+    // Phase of set s's barrier for basis i (each use completes one phase).
+    const uint32_t par = NSET == 2 ? (uint32_t)((i >> 1) & 1) : (uint32_t)(i & 1);
+    // NSET = 2: set s ^ 1 was last read by basis i - 1, which ended at a barrier: refill it
+    // for basis i + 1.
+    if (NSET == 2 && staged && i + 1 < NB)
       stage_epilogue_t(tm, coef, thr, plane(bi + 1), prow(bi + 1), n, hm, oy0, ox0, set_a(s ^ 1), set_t(s ^ 1),
                        &bar[1 + (s ^ 1)]);
 #define PS_MR(LFv) ana_rows<LFv>(in_s, lo_s, hi_s)
     PS_SWITCH_LF(bi, PS_MR)
 #undef PS_MR
     if (staged) {
-      const bool ok2 = mbar_wait(&bar[1 + s], (uint32_t)((i >> 1) & 1));
+      const bool ok2 = mbar_wait(&bar[1 + s], par);
       if (__syncthreads_or(!ok2)) {
         if (threadIdx.x == 0) {
           atomicExch(err, 1);
-          (void)mbar_drain(&bar[1 + s], (uint32_t)((i >> 1) & 1));
-          if (i + 1 < NB) (void)mbar_drain(&bar[1 + (s ^ 1)], (uint32_t)(((i + 1) >> 1) & 1));
+          (void)mbar_drain(&bar[1 + s], par);
+          if (NSET == 2 && i + 1 < NB) (void)mbar_drain(&bar[1 + (s ^ 1)], (uint32_t)(((i + 1) >> 1) & 1));
         }
         return;
       }
@@ -664,6 +671,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_ana_l1m(const float* __restrict_
     PS_SWITCH_LF(bi, PS_MC)
 #undef PS_MC
     __syncthreads();   // lo/hi and stage set s consumed before the next basis
+    // NSET = 1: the single set is free now: refill it for basis i + 1 (its rows run meanwhile).
+    if (NSET == 1 && staged && i + 1 < NB)
+      stage_epilogue_t(tm, coef, thr, plane(bi + 1), prow(bi + 1), n, hm, oy0, ox0, set_a(0), set_t(0), &bar[1]);
   }
 }
 
@@ -1496,7 +1506,7 @@ cudaError_t configure_kernels() {
     if (e != cudaSuccess) return e;
   }
   for (const void* f : {(const void*)k_ana_l1m<8, 256>, (const void*)k_ana_l1m<4, 256>,
-                        (const void*)k_ana_l1m<4, 512>}) {
+                        (const void*)k_ana_l1m<4, 512>, (const void*)k_ana_l1m<4, 256, 1>}) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)multi_analysis_smem());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -1542,9 +1552,12 @@ cudaError_t sara_analysis(Handle* h, const float* X, float* coef, float* thr, in
       else if (choice == 3)
         k_ana_l1m<4, 256><<<gm, 256, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
                                                                          scale, gamma, delta, h->dev_flags, tm);
-      else
+      else if (choice == 4)
         k_ana_l1m<4, 512><<<gm, 512, multi_analysis_smem(), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
                                                                          scale, gamma, delta, h->dev_flags, tm);
+      else
+        k_ana_l1m<4, 256, 1><<<gm, 256, multi_analysis_smem(1), h->stream>>>(X, n, l == L, coef, thr, buf[0], mode,
+                                                                            scale, gamma, delta, h->dev_flags, tm);
       if (fine_done) {
         const cudaError_t e = cudaEventRecord(fine_done, h->stream);
         if (e != cudaSuccess) return e;

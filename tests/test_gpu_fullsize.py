@@ -177,7 +177,7 @@ def test_sara_every_launch_choice_full_maps(big):
             B.ps_apply_psi(s.h, A, back)
             assert _rel(back[1], ref_syn) <= 1e-6, syn
             outs.append(back)
-        for ana in range(5):
+        for ana in range(6):
             B.ps_set_tuning(s.h, saved[:3] + [ana])
             C = np.empty((4, 9, WL.n, WL.n), np.float32)
             B.ps_apply_psi_adjoint(s.h, S, C)

@@ -156,14 +156,15 @@ def test_nonfinite_state_is_reported(plane):
         assert np.all(np.isfinite(B.ps_get_rel_change(s.h)))
 
 
-@pytest.mark.parametrize("tuning", [[0, 0, 3, 1], [1, 0, 0, 0]])
+@pytest.mark.parametrize("tuning", [[0, 0, 3, 1], [1, 0, 0, 0], [1, 0, 0, 5]])
 def test_bounded_wait_gives_up_then_recovers(tuning):
     """With a zero poll budget every bulk-copy wait gives up at once: the CTAs raise the flag,
     drain their copies with the full budget and return; ps_synchronize reports PS_ETIMEOUT.
-    With the budget restored the handle iterates like the oracle again. The two tunings cover
-    every kernel with such a wait (tiled and persistent analysis, both synthesis forms, the
-    tensor-core gridding; at 256^2 with 3 levels, levels 1-2 are tiled and level 2 of the
-    synthesis takes its own tiled kernel)."""
+    With the budget restored the handle iterates like the oracle again. The tunings cover
+    every kernel with such a wait (tiled and persistent analysis, the multi-basis level-1
+    analysis with one staging set, both synthesis forms, the tensor-core gridding; at 256^2
+    with 3 levels, levels 1-2 are tiled and level 2 of the synthesis takes its own tiled
+    kernel)."""
     n, M, levels = 256, 2000, 3
     pb = make_problem(n, M, levels, 2, seed=36)
     prob = pb["prob"]

@@ -42,7 +42,7 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
     Yr = (rng.normal(size=(M, 4)) + 1j * rng.normal(size=(M, 4))).astype(np.complex64)
     ref_adj = meas.phi_adjoint(Yr.astype(np.complex128), pb["uv"], pb["w"].astype(np.float64), n)
     with _solver(pb, n, levels) as s:
-        for syn, deg, grd, ana in itertools.product(range(3), range(3), range(5), range(5)):
+        for syn, deg, grd, ana in itertools.product(range(3), range(3), range(5), range(6)):
             B.ps_set_tuning(s.h, [syn, deg, grd, ana])
             assert B.ps_get_tuning(s.h) == [syn, deg, grd, ana]
             Sg = np.empty((4, n, n), np.float32)
@@ -63,7 +63,7 @@ def test_every_launch_choice_matches_oracle(n, M, levels):
 def test_set_tuning_rejects_unknown_choices():
     pb = make_problem(32, 500, 2, 1, seed=13)
     with _solver(pb, 32, 2) as s:
-        for bad in ([3, 0, 0, 0], [0, 3, 0, 0], [0, 0, 5, 0], [0, 0, 0, 5]):
+        for bad in ([3, 0, 0, 0], [0, 3, 0, 0], [0, 0, 5, 0], [0, 0, 0, 6]):
             with pytest.raises(B.PolsaraError) as e:
                 B.ps_set_tuning(s.h, bad)
             assert e.value.status == B.PS_EINVAL
@@ -101,7 +101,7 @@ def test_autotune_keeps_the_state_and_the_iteration():
 
 
 @pytest.mark.parametrize("tuning", [[0, 0, 0, 1], [0, 1, 3, 0], [0, 0, 0, 2], [1, 0, 0, 3], [2, 0, 4, 2],
-                                    [1, 0, 3, 4], [0, 2, 1, 0]])
+                                    [1, 0, 3, 4], [0, 2, 1, 0], [1, 2, 3, 5]])
 def test_forced_launch_choices_iterate_like_oracle(tuning):
     """Forced launch choices inside the iteration against Algorithm 1 of the FP64 oracle
     from a random state: [0, 0, 0, 1] the persistent analysis form (dual update with
@@ -110,7 +110,8 @@ def test_forced_launch_choices_iterate_like_oracle(tuning):
     [0, 0, 0, 2] and [1, 0, 0, 3] the level-1 analysis with the input tile shared by 8 or 4
     bases (both staging sets in use), [2, 0, 4, 2] the persistent finest synthesis level and the
     tensor-core gridding with in-kernel weights, [1, 0, 3, 4] the 512-thread multi-basis analysis,
-    [0, 2, 1, 0] the register-capped degridding beside the per-tap gridding."""
+    [0, 2, 1, 0] the register-capped degridding beside the per-tap gridding, [1, 2, 3, 5] the
+    multi-basis analysis with one staging set refilled between bases."""
     from oracle import primal_dual as opd
     from paper_1801_02417_gb300 import inputs
     n, M, levels = 128, 1500, 3
